@@ -1,0 +1,447 @@
+#!/usr/bin/env python
+"""Benchmark: Moore-Penrose inverse of a 4096 x 2048 rank-1536 matrix on GB300.
+
+One step = one complete pseudoinverse (Gram, pivot tolerance, full-rank
+Cholesky, compaction, inverse of L'L, chain) of one synthetic input,
+G = A B with A 4096 x 1536 and B 1536 x 2048 i.i.d. N(0,1).
+
+Metric: pinv TFLOP/s = algorithmic flops of one pseudoinverse (fixed formula,
+symmetric products counted at half) / device time per step, plus pinvs/s, for
+the fastest arithmetic mode and for plain FP64; the relative Frobenius error
+of G+ against the CPU oracle is reported beside each.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode best|fp64|exact|bf16x3]
+  python bench.py --impl reference ...   (the CPU oracle, timed on the host cores)
+
+Under torchrun (N > 1) every rank solves its own copy of the workload on its
+own GPU (independent problems: no collective on the data path); the time is
+the maximum over ranks and the value the total over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+M, N, R = 4096, 2048, 1536
+WORKLOAD = "rank-deficient G = A(4096x1536) B(1536x2048), N(0,1), seed 1"
+
+
+def pinv_flops(m: int, n: int, r: int) -> float:
+    """Algorithmic flops of one pseudoinverse: Gram m n^2, full-rank Cholesky
+    n r^2 - 2/3 r^3 + r (n - r)^2, L'L n r^2, inverse r^3, chain 2 n r^2 +
+    n^2 r + 2 n^2 m."""
+    chol = n * r * r - 2.0 / 3.0 * r ** 3 + r * (n - r) ** 2
+    return float(m * n * n + chol + n * r * r + r ** 3 + 2 * n * r * r + n * n * r + 2 * n * n * m)
+
+
+# ---------------------------------------------------------------------------
+# GPU clock sampling (nvidia-smi) during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        under_load = [x for x in sm if x > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(under_load), "sm_max_mhz": max(smax),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# FP64 pipe of GB300: 152 SMs x 2 DFMA/clock x 2 flop x 2.07 GHz (maximum SM
+# clock).  A measured DFMA loop on this part reached 1.20 TFLOP/s at 1.995 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle legs (subprocess with a known thread count)
+# ---------------------------------------------------------------------------
+
+def _oracle_worker(argv):
+    """Runs inside a fresh interpreter: times oracle.geninv on the workload."""
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--reps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=0)
+    ap.add_argument("--save", default="")
+    ap.add_argument("--budget-s", type=float, default=25.0)
+    a = ap.parse_args(argv)
+    import numpy as np
+
+    import oracle
+    from paper_0804_4809_gb300 import inputs
+    G = inputs.workload_large_rank_deficient()
+    for _ in range(a.warmup):
+        oracle.geninv(G)
+    times = []
+    Y = None
+    t_start = time.perf_counter()
+    for i in range(a.reps):
+        t0 = time.perf_counter()
+        Y, fac = oracle.geninv(G, return_factors=True)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start > a.budget_s and i + 1 >= 1:
+            break
+    threads = len(os.listdir("/proc/self/task")) if os.path.isdir("/proc/self/task") else None
+    if a.save:
+        np.save(a.save, Y)
+    print(json.dumps({"times": times, "rank": int(fac["rank"]), "threads": threads}))
+
+
+def run_oracle_subprocess(reps: int, warmup: int, save: str = "", budget_s: float = 25.0) -> dict:
+    cores = os.cpu_count() or 1
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(cores)
+    env.pop("CUDA_VISIBLE_DEVICES", None)
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-worker", "--reps", str(reps),
+           "--warmup", str(warmup), "--budget-s", str(budget_s)]
+    if save:
+        cmd += ["--save", save]
+    out = subprocess.run(cmd, env=env, capture_output=True, text=True, cwd=ROOT)
+    if out.returncode != 0:
+        raise RuntimeError("oracle worker failed:\n" + out.stderr[-2000:])
+    res = json.loads(out.stdout.strip().splitlines()[-1])
+    res["cores"] = cores
+    return res
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def time_steps(fn, steps, flush, stream):
+    import torch
+    evs = []
+    for _ in range(steps):
+        flush()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def run_mode(mode, G, out, steps, warmup, flush, stream, device):
+    import torch
+
+    from paper_0804_4809_gb300 import cpinv
+    plan = cpinv.PinvPlan(M, N, device, mode=mode)
+    sid = stream.cuda_stream
+    with torch.cuda.stream(stream):
+        r = plan(G, out, sync_rank=True, stream=sid)
+        for _ in range(max(0, warmup - 1)):
+            plan(G, out, stream=sid)
+        torch.cuda.synchronize()
+        l0 = cpinv.launch_count()
+        ms = time_steps(lambda: plan(G, out, stream=sid), steps, flush, stream)
+        launches = cpinv.launch_count() - l0
+        # profiled pass: events around each library launch (same stream)
+        cpinv.profile_enable(True)
+        prof_ms = time_steps(lambda: plan(G, out, stream=sid), steps, flush, stream)
+        prof = cpinv.profile_read()
+        cpinv.profile_enable(False)
+        r2 = plan(G, out, sync_rank=True, stream=sid)
+    torch.cuda.synchronize()
+    return {"rank": r, "rank_after": r2, "ms": ms, "launches": launches, "profile": prof,
+            "profiled_ms": prof_ms}
+
+
+def run_e2e(mode, G_host, steps, device):
+    """Same metric through the public API with host buffers: pinned H2D of G,
+    the pseudoinverse, D2H of G+, synchronised, per step."""
+    import torch
+
+    from paper_0804_4809_gb300 import cpinv
+    plan = cpinv.PinvPlan(M, N, device, mode=mode)
+    Gh = torch.from_numpy(G_host).pin_memory()
+    Yh = torch.empty((N, M), dtype=torch.float64).pin_memory()
+    Gd = torch.empty((M, N), dtype=torch.float64, device=device)
+    Yd = torch.empty((N, M), dtype=torch.float64, device=device)
+    s = torch.cuda.current_stream(device)
+
+    def step():
+        Gd.copy_(Gh, non_blocking=True)
+        plan(Gd, Yd, stream=s.cuda_stream)
+        Yh.copy_(Yd, non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        step()
+        s.synchronize()
+        ts.append(time.perf_counter() - t0)
+    return {"s": ts, "h2d": Gh.numel() * 8, "d2h": Yh.numel() * 8}
+
+
+def ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    from paper_0804_4809_gb300 import build, inputs
+    if rank == 0 or ws == 1:
+        build.build()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        build.build()
+
+    G_host = inputs.workload_large_rank_deficient()
+    G = torch.from_numpy(G_host).to(device)
+    out = torch.empty((N, M), dtype=torch.float64, device=device)
+    flushbuf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+
+    def flush():
+        flushbuf.zero_()
+
+    stream = torch.cuda.Stream(device)
+    modes = ["fp64"] if args.mode in ("best", "fp64") else [args.mode, "fp64"]
+    if args.mode == "best":
+        modes = best_modes()
+    results = {}
+    outs = {}
+    sampler = ClockSampler(local)
+    sampler.start()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    for md in modes:
+        o = torch.empty_like(out)
+        results[md] = run_mode(md, G, o, args.steps, args.warmup, flush, stream, device)
+        outs[md] = o
+    clocks = sampler.stop()
+    e2e = run_e2e(modes[0], G_host, args.steps, device)
+
+    # max over ranks of the timed total
+    head = modes[0]
+    t_sum = sum(results[head]["ms"]) / 1e3
+    t_fp64 = sum(results["fp64"]["ms"]) / 1e3
+    t_e2e = sum(e2e["s"])
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_sum, t_fp64, t_e2e], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_sum, t_fp64, t_e2e = (float(x) for x in t.tolist())
+    if rank != 0:
+        return
+
+    flops = pinv_flops(M, N, R)
+    K = args.steps
+    value = flops * K * ws / t_sum / 1e12
+    line = {
+        "metric": "pinv TFLOP/s (algorithmic flops / device time), 4096x2048 rank 1536",
+        "value": round(value, 4),
+        "unit": "TFLOP/s",
+        "n_gpus": ws,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": round(t_sum / K * 1e3, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if head == "fp64" else ("bf16-slices->f64" if head == "exact" else "bf16x3"),
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": M, "n": N, "rank": R, "mode": head,
+                   "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+        "pinvs_per_s": round(K * ws / t_sum, 4),
+        "gpu_launches": int(results[head]["launches"]),
+        "clocks": clocks,
+    }
+    # modes side by side
+    line["modes"] = {}
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        with tempfile.TemporaryDirectory() as td:
+            path = os.path.join(td, "Yo.npy")
+            cpu = run_oracle_subprocess(reps=args.cpu_reps, warmup=0, save=path,
+                                        budget_s=args.cpu_budget_s)
+            Yo = np.load(path)
+        nYo = np.linalg.norm(Yo)
+        for md in modes:
+            Y = outs[md].cpu().numpy()
+            line["modes"][md] = {"rel_err_vs_oracle": float(np.linalg.norm(Y - Yo) / nYo)}
+        line["rank_oracle"] = cpu["rank"]
+    for md in modes:
+        rs = results[md]
+        t = sum(rs["ms"]) / 1e3
+        d = line["modes"].setdefault(md, {})
+        d.update({"tflops": round(flops * K / t / 1e12, 4), "pinvs_per_s": round(K / t, 4),
+                  "ms_per_step": round(t / K * 1e3, 4), "rank": rs["rank"],
+                  "launches_per_step": rs["launches"] / K,
+                  "profile": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                                  "gflop": round(v["flops"] / 1e9, 3)}
+                              for k, v in rs["profile"].items()},
+                  "profiled_ms_per_step": round(sum(rs["profiled_ms"]) / K, 4)})
+    line["vs_plain_fp64"] = round(t_fp64 / t_sum, 4) if head != "fp64" else 1.0
+    line["rel_err_vs_oracle"] = line["modes"].get(head, {}).get("rel_err_vs_oracle")
+
+    # roofline of the dominant kernel (from the profiled pass, events on the launch stream)
+    prof = results[head]["profile"]
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])[0] if prof else None
+    peaks = measured_peaks()
+    if dom is not None:
+        p = prof[dom]
+        achieved = p["flops"] / (p["ms"] / 1e3) / 1e12 if p["ms"] > 0 else 0.0
+        if dom == "gemm_fp64":
+            bound, peak, src = "alu", FP64_PEAK_TFLOPS, "FP64 pipe: 152 SM x 2 DFMA/clk x 2.07 GHz"
+        else:
+            bound = "tensor"
+            peak = peaks.get("bf16_tflops_sustained") or 1700.0
+            src = "measured bf16 sustained" if peaks else "fallback"
+        line["roofline"] = {"kernel": dom, "bound": bound, "achieved": round(achieved, 4),
+                            "peak": round(peak, 4), "unit": "TFLOP/s",
+                            "frac": round(achieved / peak, 4), "traffic": None,
+                            "peak_source": src,
+                            "share_of_step": round(p["ms"] / sum(v["ms"] for v in prof.values()), 4)}
+    line["e2e"] = {"value": round(flops * K * ws / t_e2e / 1e12, 4), "unit": "TFLOP/s",
+                   "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+                   "mode": modes[0]}
+    if cpu is not None:
+        t_cpu = statistics.median(cpu["times"])
+        line["cpu_baseline"] = {"value": round(flops / t_cpu / 1e12, 6), "unit": "TFLOP/s",
+                                "cores": cpu["cores"], "threads_seen": cpu.get("threads"),
+                                "kind": "oracle",
+                                "sample": f"{len(cpu['times'])} full pseudoinverse(s) of the same "
+                                          f"4096x2048 input, median {t_cpu:.2f} s"}
+    print(json.dumps(line), flush=True)
+
+
+def best_modes():
+    """Modes to run: the fastest implemented mode first, plain FP64 beside it."""
+    from paper_0804_4809_gb300 import cpinv
+    import ctypes
+    avail = []
+    for md in ("exact",):
+        o = cpinv.make_opts(md)
+        if cpinv.lib().cpinv_pinv_workspace_size(M, N, ctypes.byref(o)) > 0:
+            avail.append(md)
+    return avail + ["fp64"]
+
+
+def reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1 and rank != 0:
+        return
+    res = run_oracle_subprocess(reps=args.steps, warmup=args.warmup, budget_s=1e9)
+    flops = pinv_flops(M, N, R)
+    t = sum(res["times"])
+    K = len(res["times"])
+    value = flops * K / t / 1e12
+    line = {
+        "impl": "reference",
+        "metric": "pinv TFLOP/s (algorithmic flops / device time), 4096x2048 rank 1536",
+        "value": round(value, 6), "unit": "TFLOP/s", "n_gpus": ws, "steps": K,
+        "warmup": args.warmup, "ms_per_step": round(t / K * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": M, "n": N, "rank": R, "mode": "cpu oracle"},
+        "cpu_baseline": {"value": round(value, 6), "unit": "TFLOP/s", "kind": "oracle",
+                         "cores": res["cores"], "threads_seen": res.get("threads"),
+                         "sample": f"{K} full pseudoinverse(s) of the 4096x2048 input per run"},
+        "e2e": {"value": round(value, 6), "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "rank_oracle": res["rank"],
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    if "--oracle-worker" in sys.argv:
+        argv = [a for a in sys.argv[1:] if a != "--oracle-worker"]
+        return _oracle_worker(argv)
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="best", choices=["best", "fp64", "exact", "bf16x3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-reps", type=int, default=3)
+    ap.add_argument("--cpu-budget-s", type=float, default=25.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference(args)
+    return ours(args)
+
+
+if __name__ == "__main__":
+    main()

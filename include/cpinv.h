@@ -1,0 +1,149 @@
+/*
+ * cpinv -- Moore-Penrose inverse by full-rank Cholesky factorisation, on one
+ * NVIDIA GB300 (sm_103a).  C ABI.
+ *
+ * Method (P. Courrieu, "Fast Computation of Moore-Penrose Inverse Matrices"):
+ *   Sec. 1       G+ is the unique n x m matrix satisfying the four Penrose
+ *                conditions; W = G+ F solves min |G W - F|^2 with minimum norm.
+ *   Sec. 2 Eq.(1) G'G = L L', L (n x r) of full column rank r.
+ *   Theorem 1    G+ = L (L'L)^-1 (L'L)^-1 L' G'.
+ *   Appendix     A = G'G (A = G G' and a transposed result when m < n);
+ *                tol = rel_tol * min{A_jj : A_jj > 0}; full-rank Cholesky in
+ *                natural column order keeping column k iff its updated pivot
+ *                is > tol; M = inv(L'L); G+ = L M M L' G'.
+ *
+ * Conventions for every entry point below:
+ *   - Matrices are dense, ROW-MAJOR, FP64, with an explicit leading dimension
+ *     (elements between the starts of two consecutive rows), ld >= #columns.
+ *   - Every matrix pointer is a DEVICE pointer (cudaMalloc'd or equivalent)
+ *     on the current CUDA device.  The caller owns all buffers; the library
+ *     never frees or keeps them past the call.
+ *   - `workspace` is a device buffer of at least the size returned by the
+ *     matching *_workspace_size function, aligned to 256 bytes; the call
+ *     uses it as scratch and keeps nothing in it.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All work is
+ *     enqueued on it.  If `rank_out` is non-NULL the call synchronizes that
+ *     stream, writes the numerical rank r to *rank_out and returns the status
+ *     the kernels recorded (non-finite input, failed inverse); if it is NULL
+ *     the call returns after enqueueing, and only argument errors are
+ *     reported.
+ *   - Return value: a CPINV_* status.  On error the outputs are unspecified
+ *     and *rank_out (if given) is -1.
+ *   - m = 0 or n = 0 gives an empty result and r = 0.  A G with no positive
+ *     diagonal entry in its Gram matrix (e.g. G = 0) gives G+ = 0 and r = 0,
+ *     like the Appendix listing (min over an empty set makes every test false).
+ */
+#ifndef CPINV_H
+#define CPINV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define CPINV_OK                  0
+#define CPINV_ERR_INVALID_ARG     1  /* NULL pointer, negative size, ld too small, bad option */
+#define CPINV_ERR_NONFINITE_INPUT 2  /* G holds a NaN or an Inf */
+#define CPINV_ERR_WORKSPACE       3  /* workspace NULL, misaligned or too small */
+#define CPINV_ERR_CUDA            4  /* a CUDA runtime call failed */
+#define CPINV_ERR_NUMERICAL       5  /* L'L was not positive definite in FP64 */
+#define CPINV_ERR_UNSUPPORTED     6  /* mode or size not supported by this build */
+
+/* Arithmetic of the dense contractions (Gram, L'L, inverse, chain).
+ * The pivot decisions, square roots and the small diagonal-block solves are
+ * FP64 in every mode. */
+#define CPINV_MODE_FP64         0  /* FP64 fused multiply-add everywhere */
+#define CPINV_MODE_EXACT_SLICE  1  /* tcgen05 BF16 tensor cores on integer slices of the
+                                      FP64 operands with exact FP32/INT32 sums
+                                      (Ozaki scheme), FP64-accurate products */
+#define CPINV_MODE_SPLIT_BF16X3 2  /* tcgen05 BF16 tensor cores, hi/lo split, three
+                                      products accumulated in FP32 (reduced accuracy) */
+
+typedef struct cpinv_opts {
+  int32_t mode;      /* CPINV_MODE_* (default CPINV_MODE_FP64) */
+  int32_t slices;    /* exact-slice mode: number of 8-bit slices per operand,
+                        0 = default (7); ignored by the other modes */
+  int32_t panel;     /* Cholesky panel width, 0 = default; 16, 32 or 64 */
+  int32_t reserved;  /* must be 0 */
+  double rel_tol;    /* pivot threshold factor; default 1e-9 (Appendix) */
+} cpinv_opts;
+
+/* Fills *o with the defaults (FP64 mode, rel_tol = 1e-9). */
+void cpinv_default_opts(cpinv_opts* o);
+
+/* Human-readable name of a status code (static string). */
+const char* cpinv_status_string(int status);
+
+/* Library version, as major*10000 + minor*100 + patch. */
+int cpinv_version(void);
+
+/* ---------------------------------------------------------------------------
+ * Moore-Penrose inverse (Theorem 1, Appendix `geninv`).
+ *   G   : m x n, row-major, leading dimension ldg >= n.
+ *   Gp  : n x m output G+, row-major, leading dimension ldgp >= m.
+ * For m < n the Appendix's transposed branch is taken (A = G G', m x m).
+ * ------------------------------------------------------------------------- */
+size_t cpinv_pinv_workspace_size(int64_t m, int64_t n, const cpinv_opts* o);
+int cpinv_pinv(const double* G, int64_t m, int64_t n, int64_t ldg,
+               double* Gp, int64_t ldgp,
+               void* workspace, size_t workspace_bytes,
+               const cpinv_opts* o, int64_t* rank_out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Minimum-norm least squares W = G+ F (Sec. 1; the printed "W = G+ W" is
+ * read as W = G+ F).  G+ is never formed: W = L (M (M (L' (G'F)))).
+ *   F : m x k, row-major, ldf >= k.     W : n x k output, ldw >= k.
+ * ------------------------------------------------------------------------- */
+size_t cpinv_lstsq_workspace_size(int64_t m, int64_t n, int64_t k, const cpinv_opts* o);
+int cpinv_lstsq(const double* G, int64_t m, int64_t n, int64_t ldg,
+                const double* F, int64_t k, int64_t ldf,
+                double* W, int64_t ldw,
+                void* workspace, size_t workspace_bytes,
+                const cpinv_opts* o, int64_t* rank_out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Numerical rank and kept-pivot mask (Appendix: tol rule and full-rank
+ * Cholesky).  accepted_out (device, may be NULL) receives one byte per
+ * column of the factored Gram matrix -- min(m, n) bytes: columns of G when
+ * m >= n, rows of G when m < n -- 1 if that pivot was kept, else 0.
+ * ------------------------------------------------------------------------- */
+size_t cpinv_rank_workspace_size(int64_t m, int64_t n, const cpinv_opts* o);
+int cpinv_rank(const double* G, int64_t m, int64_t n, int64_t ldg,
+               uint8_t* accepted_out,
+               void* workspace, size_t workspace_bytes,
+               const cpinv_opts* o, int64_t* rank_out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Tracing.  When enabled, every kernel the library launches is bracketed by
+ * two CUDA events recorded on the stream it is launched on; reading the
+ * profile synchronizes the device and returns, per kernel class, the number
+ * of launches, the summed event-to-event device time and the algorithmic
+ * floating-point operations of those launches (a symmetric product that
+ * computes one triangle counts n(n+1)K, a full one 2MNK).  Off by default;
+ * the records are process-global and not thread-safe.
+ * ------------------------------------------------------------------------- */
+typedef struct cpinv_profile_entry {
+  char name[32];     /* kernel class: "gemm_fp64", "gemm_slice", "diag_factor", "aux", ... */
+  int64_t launches;
+  double ms;         /* summed device time of those launches */
+  double flops;      /* algorithmic flops (0 for non-contractions) */
+} cpinv_profile_entry;
+
+/* Enables (on != 0) or disables tracing and clears the records.  Returns the
+ * previous state. */
+int cpinv_profile_enable(int on);
+/* Writes up to max_entries classes to out, returns how many classes there
+ * are (may exceed max_entries), and clears the records.  Returns -1 on a CUDA
+ * error. */
+int cpinv_profile_read(cpinv_profile_entry* out, int max_entries);
+/* Number of kernels the library has launched in this process. */
+int64_t cpinv_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPINV_H */

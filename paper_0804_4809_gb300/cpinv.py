@@ -1,0 +1,229 @@
+"""Thin PyTorch binding of libcpinv.so (argument marshalling only).
+
+Every step of the computation runs in the library's CUDA kernels; this module
+only checks tensors, allocates outputs and the workspace through PyTorch's
+caching allocator, and passes raw device pointers and the current CUDA stream
+through the C ABI (``include/cpinv.h``).  There is no CPU fallback: if the
+library is missing or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcpinv.so")
+
+MODE_FP64 = 0
+MODE_EXACT_SLICE = 1
+MODE_SPLIT_BF16X3 = 2
+_MODES = {"fp64": MODE_FP64, "exact": MODE_EXACT_SLICE, "exact_slice": MODE_EXACT_SLICE,
+          "bf16x3": MODE_SPLIT_BF16X3, "split": MODE_SPLIT_BF16X3}
+
+_c_i64 = ctypes.c_int64
+_c_vp = ctypes.c_void_p
+_c_sz = ctypes.c_size_t
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("slices", ctypes.c_int32),
+                ("panel", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("rel_tol", ctypes.c_double)]
+
+
+class ProfileEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64),
+                ("ms", ctypes.c_double), ("flops", ctypes.c_double)]
+
+
+class CpinvError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"cpinv status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+#: Every C symbol ``include/cpinv.h`` declares, with (restype, argtypes).
+SIGNATURES = {
+    "cpinv_default_opts": (None, [ctypes.POINTER(Opts)]),
+    "cpinv_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "cpinv_version": (ctypes.c_int, []),
+    "cpinv_pinv_workspace_size": (_c_sz, [_c_i64, _c_i64, ctypes.POINTER(Opts)]),
+    "cpinv_pinv": (ctypes.c_int, [_c_vp, _c_i64, _c_i64, _c_i64, _c_vp, _c_i64, _c_vp, _c_sz,
+                                  ctypes.POINTER(Opts), ctypes.POINTER(_c_i64), _c_vp]),
+    "cpinv_lstsq_workspace_size": (_c_sz, [_c_i64, _c_i64, _c_i64, ctypes.POINTER(Opts)]),
+    "cpinv_lstsq": (ctypes.c_int, [_c_vp, _c_i64, _c_i64, _c_i64, _c_vp, _c_i64, _c_i64, _c_vp,
+                                   _c_i64, _c_vp, _c_sz, ctypes.POINTER(Opts),
+                                   ctypes.POINTER(_c_i64), _c_vp]),
+    "cpinv_rank_workspace_size": (_c_sz, [_c_i64, _c_i64, ctypes.POINTER(Opts)]),
+    "cpinv_rank": (ctypes.c_int, [_c_vp, _c_i64, _c_i64, _c_i64, _c_vp, _c_vp, _c_sz,
+                                  ctypes.POINTER(Opts), ctypes.POINTER(_c_i64), _c_vp]),
+    "cpinv_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "cpinv_profile_read": (ctypes.c_int, [ctypes.POINTER(ProfileEntry), ctypes.c_int]),
+    "cpinv_launch_count": (ctypes.c_int64, []),
+}
+
+
+def lib():
+    """Load libcpinv.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def make_opts(mode="fp64", rel_tol: float = 1e-9, panel: int = 0, slices: int = 0) -> Opts:
+    o = Opts()
+    lib().cpinv_default_opts(ctypes.byref(o))
+    o.mode = _MODES[mode] if isinstance(mode, str) else int(mode)
+    o.rel_tol = float(rel_tol)
+    o.panel = int(panel)
+    o.slices = int(slices)
+    return o
+
+
+def _check(status: int):
+    if status != 0:
+        raise CpinvError(status, lib().cpinv_status_string(status).decode())
+
+
+def _mat(x: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(x, torch.Tensor) or x.dim() != 2:
+        raise TypeError(f"{name} must be a 2-D torch tensor")
+    if x.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    if not x.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor (no CPU path)")
+    if x.shape[1] > 1 and x.stride(1) != 1 or x.shape[0] > 1 and x.stride(0) < x.shape[1]:
+        x = x.contiguous()
+    return x
+
+
+def _ld(x: torch.Tensor) -> int:
+    return max(int(x.stride(0)), int(x.shape[1]), 1) if x.shape[0] > 1 else max(int(x.shape[1]), 1)
+
+
+def _stream(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def pinv(G: torch.Tensor, mode="fp64", rel_tol: float = 1e-9, panel: int = 0, slices: int = 0,
+         out: torch.Tensor | None = None, sync_rank: bool = True):
+    """G+ of a CUDA float64 matrix.  Returns (G+, rank); rank is None when
+    ``sync_rank`` is False (no host synchronisation)."""
+    G = _mat(G, "G")
+    m, n = G.shape
+    o = make_opts(mode, rel_tol, panel, slices)
+    if out is None:
+        out = torch.empty((n, m), dtype=torch.float64, device=G.device)
+    ws_bytes = lib().cpinv_pinv_workspace_size(m, n, ctypes.byref(o))
+    if ws_bytes == 0:
+        raise CpinvError(1, "invalid options or sizes")
+    ws = _workspace(ws_bytes, G.device)
+    r = _c_i64(-1)
+    st = lib().cpinv_pinv(G.data_ptr(), m, n, _ld(G), out.data_ptr(), _ld(out), ws.data_ptr(),
+                          ws.numel(), ctypes.byref(o), ctypes.byref(r) if sync_rank else None,
+                          _stream(G.device))
+    _check(st)
+    return out, (int(r.value) if sync_rank else None)
+
+
+def lstsq(G: torch.Tensor, F: torch.Tensor, mode="fp64", rel_tol: float = 1e-9, panel: int = 0,
+          slices: int = 0, out: torch.Tensor | None = None, sync_rank: bool = True):
+    """Minimum-norm least squares W = G+ F.  Returns (W, rank)."""
+    G = _mat(G, "G")
+    F = _mat(F, "F")
+    m, n = G.shape
+    if F.shape[0] != m:
+        raise ValueError("F must have as many rows as G")
+    k = F.shape[1]
+    o = make_opts(mode, rel_tol, panel, slices)
+    if out is None:
+        out = torch.empty((n, k), dtype=torch.float64, device=G.device)
+    ws_bytes = lib().cpinv_lstsq_workspace_size(m, n, k, ctypes.byref(o))
+    if ws_bytes == 0:
+        raise CpinvError(1, "invalid options or sizes")
+    ws = _workspace(ws_bytes, G.device)
+    r = _c_i64(-1)
+    st = lib().cpinv_lstsq(G.data_ptr(), m, n, _ld(G), F.data_ptr(), k, _ld(F), out.data_ptr(),
+                           _ld(out), ws.data_ptr(), ws.numel(), ctypes.byref(o),
+                           ctypes.byref(r) if sync_rank else None, _stream(G.device))
+    _check(st)
+    return out, (int(r.value) if sync_rank else None)
+
+
+def rank(G: torch.Tensor, mode="fp64", rel_tol: float = 1e-9, panel: int = 0, slices: int = 0):
+    """Numerical rank and kept-pivot mask (uint8, min(m, n) entries)."""
+    G = _mat(G, "G")
+    m, n = G.shape
+    o = make_opts(mode, rel_tol, panel, slices)
+    mask = torch.empty((min(m, n),), dtype=torch.uint8, device=G.device)
+    ws_bytes = lib().cpinv_rank_workspace_size(m, n, ctypes.byref(o))
+    if ws_bytes == 0:
+        raise CpinvError(1, "invalid options or sizes")
+    ws = _workspace(ws_bytes, G.device)
+    r = _c_i64(-1)
+    st = lib().cpinv_rank(G.data_ptr(), m, n, _ld(G), mask.data_ptr() if mask.numel() else None,
+                          ws.data_ptr(), ws.numel(), ctypes.byref(o), ctypes.byref(r),
+                          _stream(G.device))
+    _check(st)
+    return int(r.value), mask
+
+
+def profile_enable(on: bool = True) -> bool:
+    """Turn the library's per-launch CUDA-event tracing on or off (clears it)."""
+    return bool(lib().cpinv_profile_enable(1 if on else 0))
+
+
+def profile_read() -> dict:
+    """Per kernel class: {'launches', 'ms', 'flops'} since the last read."""
+    arr = (ProfileEntry * 16)()
+    n = lib().cpinv_profile_read(arr, 16)
+    if n < 0:
+        raise CpinvError(4, "profile read failed")
+    return {arr[i].name.decode(): {"launches": int(arr[i].launches), "ms": float(arr[i].ms),
+                                   "flops": float(arr[i].flops)} for i in range(min(n, 16))}
+
+
+def launch_count() -> int:
+    """Kernels launched by the library in this process."""
+    return int(lib().cpinv_launch_count())
+
+
+class PinvPlan:
+    """Pre-sized G+ call for repeated use: the workspace is allocated once."""
+
+    def __init__(self, m: int, n: int, device, mode="fp64", rel_tol: float = 1e-9,
+                 panel: int = 0, slices: int = 0):
+        self.m, self.n = int(m), int(n)
+        self.device = torch.device(device)
+        self.opts = make_opts(mode, rel_tol, panel, slices)
+        nbytes = lib().cpinv_pinv_workspace_size(self.m, self.n, ctypes.byref(self.opts))
+        if nbytes == 0:
+            raise CpinvError(1, "invalid options or sizes")
+        self.ws = _workspace(nbytes, self.device)
+
+    def __call__(self, G: torch.Tensor, out: torch.Tensor, sync_rank: bool = False,
+                 stream: int | None = None):
+        r = _c_i64(-1)
+        st = lib().cpinv_pinv(G.data_ptr(), self.m, self.n, _ld(G), out.data_ptr(), _ld(out),
+                              self.ws.data_ptr(), self.ws.numel(), ctypes.byref(self.opts),
+                              ctypes.byref(r) if sync_rank else None,
+                              _stream(self.device) if stream is None else stream)
+        _check(st)
+        return int(r.value) if sync_rank else None

@@ -1,0 +1,529 @@
+// C ABI of cpinv (declared in include/cpinv.h) and the host-side pipeline.
+//
+// Pipeline of one call (Appendix `geninv`, Theorem 1), all on one stream:
+//   Gram        A = G'G (or G G' when m < n), lower triangle        [matmul]
+//   tol         rel_tol * min positive diagonal entry, NaN/Inf flag  [tol_kernel]
+//   Cholesky    panels: diag block (pivot tests) / panel solve / trailing update
+//   compaction  prefix sum of the kept-pivot mask, gather of the kept columns
+//   N = L'L     lower triangle                                        [matmul]
+//   N = U U'    Cholesky with every pivot required (SPD)
+//   W = U^-1    block rows: W_p. = -U_pp^-1 (U_p,<p W_<p,<p)        [matmul]
+//   M = W'W     = N^-1 = (L'L)^-1                                     [matmul]
+//   pinv:  X = L M, K = X X', G+ = K G'   (G+ = G' K when m < n)
+//   lstsq: W = L (M (M (L' (G'F))))       (G' (L (M (M (L'F))))) when m < n)
+// The numerical rank r never leaves the device until the optional read-back
+// at the end: every launch after the pivot tests is sized for the largest
+// possible r and reads r from device memory.
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "../../include/cpinv.h"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace cpinv {
+namespace {
+
+struct Arena {
+  char* base;
+  size_t off;
+  void* take(size_t bytes) {
+    off = (off + 255) & ~(size_t)255;
+    void* p = base ? base + off : nullptr;
+    off += bytes;
+    return p;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Tracing: events around every launch (when enabled) and a launch counter.
+// ---------------------------------------------------------------------------
+enum Kind { K_GEMM_FP64 = 0, K_GEMM_SLICE = 1, K_DIAG = 2, K_AUX = 3, K_SPLIT = 4, K_COUNT = 5 };
+const char* const kKindName[K_COUNT] = {"gemm_fp64", "gemm_slice", "diag_factor", "aux",
+                                        "slice_split"};
+
+struct TraceRec {
+  cudaEvent_t e0, e1;
+  int kind;
+  bool resolved;
+  double flops;
+  Dim M, N, K;
+  int lower;
+  const int64_t* rdev;
+};
+
+struct Tracer {
+  bool on = false;
+  std::vector<TraceRec> recs;
+};
+Tracer g_tr;
+std::atomic<int64_t> g_launches{0};
+
+int64_t eval_host(const Dim& d, int64_t r) {
+  int64_t v = d.off + (d.sel ? r : 0);
+  v = v < 0 ? 0 : v;
+  return v > d.max ? d.max : v;
+}
+
+double gemm_flops(const Dim& Md, const Dim& Nd, const Dim& Kd, int lower, int64_t r) {
+  const double M = (double)eval_host(Md, r), N = (double)eval_host(Nd, r), K = (double)eval_host(Kd, r);
+  double elems = M * N;
+  if (lower) elems = (M <= N) ? M * (M + 1) / 2 : N * (N + 1) / 2 + (M - N) * N;
+  return 2.0 * elems * K;
+}
+
+template <class F>
+cudaError_t traced(cudaStream_t s, int kind, F&& f, const GemmParams* g = nullptr) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (!g_tr.on) return f();
+  TraceRec r{};
+  r.kind = kind;
+  if (cudaEventCreate(&r.e0) != cudaSuccess || cudaEventCreate(&r.e1) != cudaSuccess)
+    return cudaErrorUnknown;
+  cudaEventRecord(r.e0, s);
+  cudaError_t e = f();
+  cudaEventRecord(r.e1, s);
+  if (g) {
+    r.M = g->M;
+    r.N = g->N;
+    r.K = g->K;
+    r.lower = g->lower;
+    r.rdev = g->rdev;
+    r.resolved = false;
+  } else {
+    r.resolved = true;
+    r.flops = 0.0;
+  }
+  g_tr.recs.push_back(r);
+  return e;
+}
+
+// Resolves the flop counts of the records that depend on the device rank
+// (called at the end of each traced call, while the workspace is alive).
+cudaError_t trace_resolve(cudaStream_t s, const int64_t* rdev) {
+  if (!g_tr.on) return cudaSuccess;
+  int64_t r = 0;
+  cudaError_t e = cudaMemcpyAsync(&r, rdev, sizeof(r), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  for (auto& t : g_tr.recs)
+    if (!t.resolved) {
+      t.flops = gemm_flops(t.M, t.N, t.K, t.lower, r);
+      t.resolved = true;
+    }
+  return cudaSuccess;
+}
+
+enum Job { JOB_RANK = 0, JOB_PINV = 1, JOB_LSTSQ = 2 };
+
+struct Plan {
+  int64_t m, n, nA, k;
+  bool trans;
+  int b;
+  int mode;
+  double rel_tol;
+  DevState* st;
+  uint8_t* acc;
+  int32_t* colidx;
+  double* Z;
+  double* Tinv;
+  double* bufA;  // A -> L_full -> N -> U -> K
+  double* bufL;  // compact L (nA x nA, r columns used)
+  double* bufW;  // W = U^-1 -> X
+  double* bufM;  // M
+  double* Tmp;   // b x nA
+  double* c1;    // lstsq: nA x k (also G'F)
+  double* c2;
+  double* c3;
+};
+
+void carve(Plan& p, Arena& a, Job job) {
+  const int64_t nA = p.nA, b = p.b;
+  const int64_t nb = (nA + b - 1) / b;
+  p.st = (DevState*)a.take(sizeof(DevState));
+  p.acc = (uint8_t*)a.take((size_t)(nA > 0 ? nA : 1));
+  p.colidx = (int32_t*)a.take(sizeof(int32_t) * (size_t)(nA > 0 ? nA : 1));
+  p.Z = (double*)a.take(sizeof(double) * (size_t)(b * b));
+  p.bufA = (double*)a.take(sizeof(double) * (size_t)(nA * nA));
+  if (job == JOB_RANK) return;
+  p.Tinv = (double*)a.take(sizeof(double) * (size_t)(nb * b * b));
+  p.bufL = (double*)a.take(sizeof(double) * (size_t)(nA * nA));
+  p.bufW = (double*)a.take(sizeof(double) * (size_t)(nA * nA));
+  p.bufM = (double*)a.take(sizeof(double) * (size_t)(nA * nA));
+  p.Tmp = (double*)a.take(sizeof(double) * (size_t)(b * nA));
+  if (job == JOB_LSTSQ) {
+    const int64_t rows = p.n > p.m ? p.n : p.m;
+    p.c1 = (double*)a.take(sizeof(double) * (size_t)(rows * p.k));
+    p.c2 = (double*)a.take(sizeof(double) * (size_t)(nA * p.k));
+    p.c3 = (double*)a.take(sizeof(double) * (size_t)(nA * p.k));
+  }
+}
+
+bool make_plan(Plan& p, int64_t m, int64_t n, int64_t k, const cpinv_opts* o) {
+  cpinv_opts d;
+  cpinv_default_opts(&d);
+  if (!o) o = &d;
+  p.m = m;
+  p.n = n;
+  p.k = k;
+  p.trans = m < n;
+  p.nA = p.trans ? m : n;
+  p.b = o->panel ? o->panel : 32;
+  p.mode = o->mode;
+  p.rel_tol = o->rel_tol;
+  if (p.b < 1 || p.b > 64) return false;
+  if (!(p.rel_tol >= 0.0) || !std::isfinite(p.rel_tol)) return false;
+  if (o->mode != CPINV_MODE_FP64) return false;
+  return true;
+}
+
+size_t plan_bytes(Plan& p, Job job) {
+  Arena a{nullptr, 0};
+  carve(p, a, job);
+  return a.off + 256;
+}
+
+struct Ctx {
+  cudaStream_t s;
+  const Plan* p;
+  const int64_t* rdev() const { return &p->st->rank; }
+};
+
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t _e = (x);                       \
+    if (_e != cudaSuccess) return CPINV_ERR_CUDA; \
+  } while (0)
+
+// C = alpha op(A) op(B) + beta C  in the plan's arithmetic.
+cudaError_t matmul(const Ctx& c, const double* A, int64_t lda, bool ta, const double* B,
+                   int64_t ldb, bool tb, double* C, int64_t ldc, Dim M, Dim N, Dim K,
+                   double alpha, double beta, int lower) {
+  GemmParams g;
+  g.A = A;
+  g.B = B;
+  g.C = C;
+  g.lda = lda;
+  g.ldb = ldb;
+  g.ldc = ldc;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.alpha = alpha;
+  g.beta = beta;
+  g.rdev = c.rdev();
+  g.lower = lower;
+  g.pad = 0;
+  return traced(c.s, K_GEMM_FP64, [&] { return launch_dgemm(g, ta, tb, c.s); }, &g);
+}
+
+// Blocked full-rank Cholesky, in place on the lower triangle of a (ld = lda).
+// spd = 0: order nA (host), pivot test against the Appendix tolerance, mask
+//          written to acc.  spd = 1: order r (device), tolerance 0, block
+//          inverses stored in Tinv.
+int factor(const Ctx& c, double* a, int64_t lda, int spd) {
+  const Plan& p = *c.p;
+  const int64_t nA = p.nA;
+  const int b = p.b;
+  for (int64_t k0 = 0, blk = 0; k0 < nA; k0 += b, ++blk) {
+    const Dim nd = spd ? rdim(0, nA) : hdim(nA);
+    CK(traced(c.s, K_DIAG, [&] {
+      return launch_diag_factor(a, lda, nd, k0, b, p.st, c.rdev(), spd ? nullptr : p.acc, p.Z,
+                                spd ? p.Tinv + blk * b * b : nullptr, spd, c.s);
+    }));
+    if (k0 + b >= nA) continue;
+    double* panel = a + (k0 + b) * lda + k0;
+    double* trail = a + (k0 + b) * lda + (k0 + b);
+    Dim below, bw;
+    if (spd) {
+      below = rdim(-(k0 + b), nA - k0 - b);
+      bw = rdim(-k0, b);
+    } else {
+      below = hdim(nA - k0 - b);
+      bw = hdim(b);
+    }
+    // panel below the block: L = A Z (in place; one column tile covers the panel)
+    CK(matmul(c, panel, lda, false, p.Z, b, false, panel, lda, below, bw, bw, 1.0, 0.0, 0));
+    // trailing update, lower triangle
+    CK(matmul(c, panel, lda, false, panel, lda, true, trail, lda, below, below, bw, -1.0, 1.0, 1));
+  }
+  return CPINV_OK;
+}
+
+// Gram, tolerance, full-rank Cholesky, compaction.  Leaves L in bufL (JOB_PINV
+// / JOB_LSTSQ) and r in st->rank.
+int front_rank(const Ctx& c, const double* G, int64_t ldg, bool compact) {
+  const Plan& p = *c.p;
+  const int64_t nA = p.nA;
+  if (!p.trans)  // A = G'G
+    CK(matmul(c, G, ldg, true, G, ldg, false, p.bufA, nA, hdim(nA), hdim(nA), hdim(p.m), 1.0,
+              0.0, 1));
+  else  // A = G G'
+    CK(matmul(c, G, ldg, false, G, ldg, true, p.bufA, nA, hdim(nA), hdim(nA), hdim(p.n), 1.0,
+              0.0, 1));
+  CK(traced(c.s, K_AUX, [&] { return launch_tol(p.bufA, nA, nA, p.rel_tol, p.st, c.s); }));
+  int rc = factor(c, p.bufA, nA, 0);
+  if (rc) return rc;
+  CK(traced(c.s, K_AUX, [&] { return launch_scan(p.acc, nA, p.colidx, p.st, c.s); }));
+  if (compact)
+    CK(traced(c.s, K_AUX,
+              [&] { return launch_gather(p.bufA, nA, nA, p.colidx, p.bufL, nA, c.s); }));
+  return CPINV_OK;
+}
+
+// M = (L'L)^-1 into bufM (after front_rank with compaction).
+int front_inverse(const Ctx& c) {
+  const Plan& p = *c.p;
+  const int64_t nA = p.nA;
+  const int b = p.b;
+  const Dim R = rdim(0, nA);
+  // N = L'L (lower), into bufA
+  CK(matmul(c, p.bufL, nA, true, p.bufL, nA, false, p.bufA, nA, R, R, hdim(nA), 1.0, 0.0, 1));
+  int rc = factor(c, p.bufA, nA, 1);
+  if (rc) return rc;
+  // W = U^-1 by block rows
+  CK(traced(c.s, K_AUX,
+            [&] { return launch_tri_inv_init(p.bufW, nA, nA, c.rdev(), p.Tinv, b, c.s); }));
+  for (int64_t ib = b, blk = 1; ib < nA; ib += b, ++blk) {
+    const Dim rows = rdim(-ib, b);
+    CK(matmul(c, p.bufA + ib * nA, nA, false, p.bufW, nA, false, p.Tmp, nA, rows, hdim(ib),
+              hdim(ib), 1.0, 0.0, 0));
+    CK(matmul(c, p.Tinv + blk * b * b, b, false, p.Tmp, nA, false, p.bufW + ib * nA, nA, rows,
+              hdim(ib), rows, -1.0, 0.0, 0));
+  }
+  // M = W'W (full, symmetric)
+  CK(matmul(c, p.bufW, nA, true, p.bufW, nA, false, p.bufM, nA, R, R, R, 1.0, 0.0, 0));
+  return CPINV_OK;
+}
+
+int finish(const Ctx& c, int64_t* rank_out) {
+  CK(trace_resolve(c.s, c.rdev()));
+  if (!rank_out) return CPINV_OK;
+  DevState h;
+  CK(cudaMemcpyAsync(&h, c.p->st, sizeof(DevState), cudaMemcpyDeviceToHost, c.s));
+  CK(cudaStreamSynchronize(c.s));
+  if (h.status & ST_NONFINITE) return CPINV_ERR_NONFINITE_INPUT;
+  if (h.status & ST_NUMERICAL) return CPINV_ERR_NUMERICAL;
+  *rank_out = h.rank;
+  return CPINV_OK;
+}
+
+int begin(Plan& p, Job job, void* ws, size_t ws_bytes) {
+  if (!ws || ((uintptr_t)ws & 255u)) return CPINV_ERR_WORKSPACE;
+  if (ws_bytes < plan_bytes(p, job)) return CPINV_ERR_WORKSPACE;
+  Arena a{(char*)ws, 0};
+  carve(p, a, job);
+  return CPINV_OK;
+}
+
+}  // namespace
+}  // namespace cpinv
+
+using namespace cpinv;
+
+extern "C" {
+
+void cpinv_default_opts(cpinv_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->mode = CPINV_MODE_FP64;
+  o->slices = 0;
+  o->panel = 0;
+  o->rel_tol = 1e-9;
+}
+
+const char* cpinv_status_string(int status) {
+  switch (status) {
+    case CPINV_OK: return "ok";
+    case CPINV_ERR_INVALID_ARG: return "invalid argument";
+    case CPINV_ERR_NONFINITE_INPUT: return "non-finite input";
+    case CPINV_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case CPINV_ERR_CUDA: return "CUDA error";
+    case CPINV_ERR_NUMERICAL: return "L'L not positive definite in FP64";
+    case CPINV_ERR_UNSUPPORTED: return "unsupported mode or size";
+    default: return "unknown status";
+  }
+}
+
+int cpinv_version(void) { return 100; }
+
+size_t cpinv_rank_workspace_size(int64_t m, int64_t n, const cpinv_opts* o) {
+  Plan p{};
+  if (m < 0 || n < 0 || !make_plan(p, m, n, 0, o)) return 0;
+  return plan_bytes(p, JOB_RANK);
+}
+
+size_t cpinv_pinv_workspace_size(int64_t m, int64_t n, const cpinv_opts* o) {
+  Plan p{};
+  if (m < 0 || n < 0 || !make_plan(p, m, n, 0, o)) return 0;
+  return plan_bytes(p, JOB_PINV);
+}
+
+size_t cpinv_lstsq_workspace_size(int64_t m, int64_t n, int64_t k, const cpinv_opts* o) {
+  Plan p{};
+  if (m < 0 || n < 0 || k < 0 || !make_plan(p, m, n, k, o)) return 0;
+  return plan_bytes(p, JOB_LSTSQ);
+}
+
+static int check_opts(const cpinv_opts* o) {
+  if (!o) return CPINV_OK;
+  if (o->mode != CPINV_MODE_FP64 && o->mode != CPINV_MODE_EXACT_SLICE &&
+      o->mode != CPINV_MODE_SPLIT_BF16X3)
+    return CPINV_ERR_INVALID_ARG;
+  if (o->mode != CPINV_MODE_FP64) return CPINV_ERR_UNSUPPORTED;
+  if (o->panel < 0 || o->panel > 64 || o->reserved != 0) return CPINV_ERR_INVALID_ARG;
+  if (!(o->rel_tol >= 0.0) || !std::isfinite(o->rel_tol)) return CPINV_ERR_INVALID_ARG;
+  return CPINV_OK;
+}
+
+int cpinv_rank(const double* G, int64_t m, int64_t n, int64_t ldg, uint8_t* accepted_out,
+               void* workspace, size_t workspace_bytes, const cpinv_opts* o, int64_t* rank_out,
+               void* stream) {
+  if (rank_out) *rank_out = -1;
+  if (int rc = check_opts(o)) return rc;
+  if (m < 0 || n < 0 || ldg < n) return CPINV_ERR_INVALID_ARG;
+  if (m == 0 || n == 0) {
+    if (rank_out) *rank_out = 0;
+    return CPINV_OK;
+  }
+  if (!G) return CPINV_ERR_INVALID_ARG;
+  Plan p{};
+  if (!make_plan(p, m, n, 0, o)) return CPINV_ERR_INVALID_ARG;
+  if (int rc = begin(p, JOB_RANK, workspace, workspace_bytes)) return rc;
+  Ctx c{(cudaStream_t)stream, &p};
+  CK(cudaMemsetAsync(p.st, 0, sizeof(DevState), c.s));
+  if (int rc = front_rank(c, G, ldg, false)) return rc;
+  if (accepted_out)
+    CK(traced(c.s, K_AUX, [&] { return launch_copy_mask(p.acc, accepted_out, p.nA, c.s); }));
+  return finish(c, rank_out);
+}
+
+int cpinv_pinv(const double* G, int64_t m, int64_t n, int64_t ldg, double* Gp, int64_t ldgp,
+               void* workspace, size_t workspace_bytes, const cpinv_opts* o, int64_t* rank_out,
+               void* stream) {
+  if (rank_out) *rank_out = -1;
+  if (int rc = check_opts(o)) return rc;
+  if (m < 0 || n < 0 || ldg < n || ldgp < m) return CPINV_ERR_INVALID_ARG;
+  if (m == 0 || n == 0) {
+    if (rank_out) *rank_out = 0;
+    return CPINV_OK;
+  }
+  if (!G || !Gp) return CPINV_ERR_INVALID_ARG;
+  Plan p{};
+  if (!make_plan(p, m, n, 0, o)) return CPINV_ERR_INVALID_ARG;
+  if (int rc = begin(p, JOB_PINV, workspace, workspace_bytes)) return rc;
+  Ctx c{(cudaStream_t)stream, &p};
+  CK(cudaMemsetAsync(p.st, 0, sizeof(DevState), c.s));
+  if (int rc = front_rank(c, G, ldg, true)) return rc;
+  if (int rc = front_inverse(c)) return rc;
+  const int64_t nA = p.nA;
+  const Dim R = rdim(0, nA);
+  // X = L M  (bufW),  K = X X'  (bufA)
+  CK(matmul(c, p.bufL, nA, false, p.bufM, nA, false, p.bufW, nA, hdim(nA), R, R, 1.0, 0.0, 0));
+  CK(matmul(c, p.bufW, nA, false, p.bufW, nA, true, p.bufA, nA, hdim(nA), hdim(nA), R, 1.0, 0.0,
+            0));
+  if (!p.trans)  // G+ = K G'   (n x n)(n x m)
+    CK(matmul(c, p.bufA, nA, false, G, ldg, true, Gp, ldgp, hdim(n), hdim(m), hdim(n), 1.0, 0.0,
+              0));
+  else  // G+ = G' K   (n x m)(m x m)
+    CK(matmul(c, G, ldg, true, p.bufA, nA, false, Gp, ldgp, hdim(n), hdim(m), hdim(m), 1.0, 0.0,
+              0));
+  return finish(c, rank_out);
+}
+
+int cpinv_lstsq(const double* G, int64_t m, int64_t n, int64_t ldg, const double* F, int64_t k,
+                int64_t ldf, double* W, int64_t ldw, void* workspace, size_t workspace_bytes,
+                const cpinv_opts* o, int64_t* rank_out, void* stream) {
+  if (rank_out) *rank_out = -1;
+  if (int rc = check_opts(o)) return rc;
+  if (m < 0 || n < 0 || k < 0 || ldg < n || ldf < k || ldw < k) return CPINV_ERR_INVALID_ARG;
+  if (m == 0 || n == 0 || k == 0) {
+    // W (n x k) = 0 when m == 0; nothing to write when n == 0 or k == 0.
+    if (m == 0 && n > 0 && k > 0) {
+      if (!W) return CPINV_ERR_INVALID_ARG;
+      CK(cudaMemset2DAsync(W, (size_t)ldw * sizeof(double), 0, (size_t)k * sizeof(double),
+                           (size_t)n, (cudaStream_t)stream));
+    }
+    if (rank_out && (m == 0 || n == 0)) *rank_out = 0;
+    if (k == 0 && m > 0 && n > 0 && rank_out) {
+      // rank still defined: run the rank query path
+      return cpinv_rank(G, m, n, ldg, nullptr, workspace, workspace_bytes, o, rank_out, stream);
+    }
+    return CPINV_OK;
+  }
+  if (!G || !F || !W) return CPINV_ERR_INVALID_ARG;
+  Plan p{};
+  if (!make_plan(p, m, n, k, o)) return CPINV_ERR_INVALID_ARG;
+  if (int rc = begin(p, JOB_LSTSQ, workspace, workspace_bytes)) return rc;
+  Ctx c{(cudaStream_t)stream, &p};
+  CK(cudaMemsetAsync(p.st, 0, sizeof(DevState), c.s));
+  if (int rc = front_rank(c, G, ldg, true)) return rc;
+  if (int rc = front_inverse(c)) return rc;
+  const int64_t nA = p.nA;
+  const Dim R = rdim(0, nA);
+  if (!p.trans) {
+    // c1 <- G'F (n x k);  c2 <- L' c1 (r x k)
+    CK(matmul(c, G, ldg, true, F, ldf, false, p.c1, k, hdim(n), hdim(k), hdim(m), 1.0, 0.0, 0));
+    CK(matmul(c, p.bufL, nA, true, p.c1, k, false, p.c2, k, R, hdim(k), hdim(nA), 1.0, 0.0, 0));
+  } else {
+    // c2 <- L' F (r x k)
+    CK(matmul(c, p.bufL, nA, true, F, ldf, false, p.c2, k, R, hdim(k), hdim(nA), 1.0, 0.0, 0));
+  }
+  CK(matmul(c, p.bufM, nA, false, p.c2, k, false, p.c3, k, R, hdim(k), R, 1.0, 0.0, 0));
+  CK(matmul(c, p.bufM, nA, false, p.c3, k, false, p.c2, k, R, hdim(k), R, 1.0, 0.0, 0));
+  if (!p.trans) {
+    CK(matmul(c, p.bufL, nA, false, p.c2, k, false, W, ldw, hdim(n), hdim(k), R, 1.0, 0.0, 0));
+  } else {
+    // t = L c (m x k) into c1, W = G' t
+    CK(matmul(c, p.bufL, nA, false, p.c2, k, false, p.c1, k, hdim(m), hdim(k), R, 1.0, 0.0, 0));
+    CK(matmul(c, G, ldg, true, p.c1, k, false, W, ldw, hdim(n), hdim(k), hdim(m), 1.0, 0.0, 0));
+  }
+  return finish(c, rank_out);
+}
+
+int cpinv_profile_enable(int on) {
+  const int prev = g_tr.on ? 1 : 0;
+  for (auto& t : g_tr.recs) {
+    cudaEventDestroy(t.e0);
+    cudaEventDestroy(t.e1);
+  }
+  g_tr.recs.clear();
+  g_tr.on = on != 0;
+  return prev;
+}
+
+int cpinv_profile_read(cpinv_profile_entry* out, int max_entries) {
+  if (cudaDeviceSynchronize() != cudaSuccess) return -1;
+  int64_t launches[K_COUNT] = {0};
+  double ms[K_COUNT] = {0}, flops[K_COUNT] = {0};
+  for (auto& t : g_tr.recs) {
+    float e = 0.f;
+    if (cudaEventElapsedTime(&e, t.e0, t.e1) != cudaSuccess) return -1;
+    launches[t.kind] += 1;
+    ms[t.kind] += e;
+    flops[t.kind] += t.resolved ? t.flops : 0.0;
+    cudaEventDestroy(t.e0);
+    cudaEventDestroy(t.e1);
+  }
+  g_tr.recs.clear();
+  int n = 0;
+  for (int k = 0; k < K_COUNT; ++k) {
+    if (!launches[k]) continue;
+    if (out && n < max_entries) {
+      std::memset(&out[n], 0, sizeof(out[n]));
+      std::strncpy(out[n].name, kKindName[k], sizeof(out[n].name) - 1);
+      out[n].launches = launches[k];
+      out[n].ms = ms[k];
+      out[n].flops = flops[k];
+    }
+    ++n;
+  }
+  return n;
+}
+
+int64_t cpinv_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

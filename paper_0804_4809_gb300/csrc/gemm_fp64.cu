@@ -1,0 +1,108 @@
+// FP64 matrix product on the CUDA cores (DFMA), the "plain FP64" arithmetic.
+//
+// C = alpha * op(A) op(B) + beta * C, row-major operands, optional lower-only
+// output (for the symmetric products G'G, L'L, A - L L').  On GB300 the FP64
+// pipe issues about two DFMA per clock per SM (1.2 TFLOP/s over 152 SMs), so
+// this kernel is bound by that pipe at any reasonable tile shape: a 64 x 64
+// tile per 256-thread CTA with 4 x 4 outputs per thread keeps the shared-memory
+// and DRAM traffic far below what the DFMA rate can consume.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace cpinv {
+
+namespace {
+
+constexpr int TM = 64, TN = 64, TK = 16;
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) dgemm_kernel(GemmParams p) {
+  const int64_t M = eval_dim(p.M, p.rdev);
+  const int64_t N = eval_dim(p.N, p.rdev);
+  const int64_t K = eval_dim(p.K, p.rdev);
+  const int64_t i0 = (int64_t)blockIdx.y * TM;
+  const int64_t j0 = (int64_t)blockIdx.x * TN;
+  if (i0 >= M || j0 >= N) return;
+  if (p.lower && j0 > i0 + TM - 1) return;  // tile strictly above the diagonal
+
+  __shared__ double As[TK][TM + 1];
+  __shared__ double Bs[TK][TN + 1];
+
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+
+  for (int64_t k0 = 0; k0 < K; k0 += TK) {
+    // A tile: TM x TK elements of op(A)
+#pragma unroll
+    for (int q = 0; q < (TM * TK) / 256; ++q) {
+      const int e = tid + 256 * q;
+      int i, k;
+      if (TA) { k = e / TM; i = e % TM; } else { i = e / TK; k = e % TK; }
+      const int64_t gi = i0 + i, gk = k0 + k;
+      double v = 0.0;
+      if (gi < M && gk < K) v = TA ? p.A[gk * p.lda + gi] : p.A[gi * p.lda + gk];
+      As[k][i] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < (TN * TK) / 256; ++q) {
+      const int e = tid + 256 * q;
+      int j, k;
+      if (TB) { j = e / TK; k = e % TK; } else { k = e / TN; j = e % TN; }
+      const int64_t gj = j0 + j, gk = k0 + k;
+      double v = 0.0;
+      if (gj < N && gk < K) v = TB ? p.B[gj * p.ldb + gk] : p.B[gk * p.ldb + gj];
+      Bs[k][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < TK; ++k) {
+      double a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = As[k][ty + 16 * u];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) b[u] = Bs[k][tx + 16 * u];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t gi = i0 + ty + 16 * u;
+    if (gi >= M) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int64_t gj = j0 + tx + 16 * v;
+      if (gj >= N) continue;
+      if (p.lower && gj > gi) continue;
+      double* c = p.C + gi * p.ldc + gj;
+      double out = p.alpha * acc[u][v];
+      if (p.beta != 0.0) out = fma(p.beta, *c, out);
+      *c = out;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_dgemm(const GemmParams& p, bool transA, bool transB, cudaStream_t s) {
+  const int64_t Mmax = p.M.max, Nmax = p.N.max;
+  if (Mmax <= 0 || Nmax <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((Nmax + TN - 1) / TN), (unsigned)((Mmax + TM - 1) / TM));
+  if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+  if (!transA && !transB) dgemm_kernel<false, false><<<grid, 256, 0, s>>>(p);
+  else if (!transA && transB) dgemm_kernel<false, true><<<grid, 256, 0, s>>>(p);
+  else if (transA && !transB) dgemm_kernel<true, false><<<grid, 256, 0, s>>>(p);
+  else dgemm_kernel<true, true><<<grid, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace cpinv

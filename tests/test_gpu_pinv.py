@@ -1,0 +1,165 @@
+"""GPU parity of pinv / lstsq / rank against the CPU oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0804_4809_gb300 import inputs
+
+from gpu_util import TOL, dev, penrose_normwise, rel, to_dev
+
+pytestmark = pytest.mark.gpu
+
+MODES = ["fp64"]
+
+
+@pytest.fixture(scope="module")
+def cp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0804_4809_gb300 import build
+    build.build()
+    from paper_0804_4809_gb300 import cpinv
+    return cpinv
+
+
+def _pinv(cp, G, mode, **kw):
+    import torch
+    Y, r = cp.pinv(to_dev(G), mode=mode, **kw)
+    torch.cuda.synchronize()
+    return Y.cpu().numpy(), r
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_small_workload(cp, mode):
+    """200 x 100, rank 80: rank, kept mask, G+ and the four Penrose conditions."""
+    G = inputs.workload_small()
+    Yo, fac = oracle.geninv(G, return_factors=True)
+    Y, r = _pinv(cp, G, mode)
+    assert r == fac["rank"] == 80
+    rk, mask = cp.rank(to_dev(G), mode=mode)
+    assert rk == 80
+    assert np.array_equal(mask.cpu().numpy().astype(bool), fac["accepted"])
+    assert rel(Y, Yo) <= TOL[mode]
+    assert penrose_normwise(G, Y) < 1e-9
+
+
+SHAPES = [
+    (200, 100, 80), (130, 70, 70), (64, 200, 31), (1, 1, 1), (17, 1, 1), (1, 17, 1),
+    (300, 257, 100), (500, 129, 128), (40, 40, 40), (333, 65, 64), (90, 33, 0),
+]
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("panel", [16, 32, 64])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_shapes_and_panels(cp, mode, panel, shape):
+    m, n, r = shape
+    G = inputs.rank_deficient(m, n, r, seed=m * 7 + n)
+    Yo, fac = oracle.geninv(G, return_factors=True)
+    Y, rk = _pinv(cp, G, mode, panel=panel)
+    assert rk == fac["rank"] == r
+    assert Y.shape == (n, m)
+    if r == 0:
+        assert not Y.any()
+    else:
+        assert rel(Y, Yo) <= TOL[mode]
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_lstsq(cp, mode):
+    import torch
+    for (m, n, r, k) in [(200, 100, 80, 3), (64, 150, 40, 5), (257, 129, 129, 1)]:
+        G = inputs.rank_deficient(m, n, r, seed=m + n + k)
+        F = inputs.normal((m, k), seed=k)
+        Wo = oracle.lstsq(G, F)
+        W, rk = cp.lstsq(to_dev(G), to_dev(F), mode=mode)
+        torch.cuda.synchronize()
+        assert rk == r
+        assert rel(W.cpu().numpy(), Wo) <= TOL[mode]
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_special_cases(cp, mode):
+    # zero column -> zero row of G+
+    G = inputs.normal((50, 9), seed=3)
+    G[:, 4] = 0.0
+    Y, r = _pinv(cp, G, mode)
+    assert r == 8 and not Y[4].any()
+    # duplicate columns
+    g = inputs.normal((31, 1), seed=4)
+    Y, r = _pinv(cp, np.hstack([g, g, g]), mode)
+    assert r == 1
+    assert rel(Y, np.vstack([g.T] * 3) / (3 * float(g[:, 0] @ g[:, 0]))) < 1e-14
+    # G = 0
+    Y, r = _pinv(cp, np.zeros((12, 7)), mode)
+    assert r == 0 and not Y.any()
+    # rectangular diagonal
+    G = np.zeros((9, 6))
+    for i, x in enumerate([2.0, 0.0, -4.0, 0.5, 0.0, 8.0]):
+        G[i, i] = x
+    Y, r = _pinv(cp, G, mode)
+    assert r == 4
+    assert np.max(np.abs(Y - oracle.geninv(G))) < 1e-15
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_leading_dimensions_and_stream(cp, mode):
+    import torch
+    m, n, r = 150, 70, 50
+    G = inputs.rank_deficient(m, n, r, seed=9)
+    big = torch.zeros((m, n + 13), dtype=torch.float64, device=dev())
+    big[:, 5:5 + n] = to_dev(G)
+    view = big[:, 5:5 + n]            # ldg = n + 13
+    outbig = torch.full((n, m + 7), 7.0, dtype=torch.float64, device=dev())
+    out = outbig[:, :m]               # ldgp = m + 7
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        Y, rk = cp.pinv(view, mode=mode, out=out)
+    s.synchronize()
+    assert rk == r
+    assert rel(out.cpu().numpy(), oracle.geninv(G)) <= TOL[mode]
+    assert torch.all(outbig[:, m:] == 7.0)   # nothing written past the row length
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_nonfinite_input_is_reported(cp, mode):
+    G = inputs.normal((40, 10), seed=5)
+    G[7, 3] = np.nan
+    with pytest.raises(cp.CpinvError) as e:
+        _pinv(cp, G, mode)
+    assert e.value.status == 2
+    G[7, 3] = np.inf
+    with pytest.raises(cp.CpinvError):
+        _pinv(cp, G, mode)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_deterministic(cp, mode):
+    G = inputs.rank_deficient(300, 200, 150, seed=12)
+    Y1, _ = _pinv(cp, G, mode)
+    Y2, _ = _pinv(cp, G, mode)
+    assert np.array_equal(Y1, Y2)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_large_rank_deficient_full_size(cp, mode):
+    """4096 x 2048, rank 1536 -- the benchmark workload, element by element."""
+    G = inputs.workload_large_rank_deficient()
+    Yo, fac = oracle.geninv(G, return_factors=True)
+    Y, r = _pinv(cp, G, mode)
+    assert r == fac["rank"] == 1536
+    e = rel(Y, Yo)
+    print(f"4096x2048 r=1536 {mode}: rel err {e:.3e}")
+    assert e <= TOL[mode]
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_large_full_rank_full_size(cp, mode):
+    G = inputs.workload_large_full_rank()
+    Yo, fac = oracle.geninv(G, return_factors=True)
+    Y, r = _pinv(cp, G, mode)
+    assert r == fac["rank"] == 2048
+    e = rel(Y, Yo)
+    print(f"4096x2048 full rank {mode}: rel err {e:.3e}")
+    assert e <= TOL[mode]
