@@ -117,6 +117,37 @@ int cpinv_rank(const double* G, int64_t m, int64_t n, int64_t ldg,
                const cpinv_opts* o, int64_t* rank_out, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Allocation-free pseudoinverse of small matrices.  The paper has no
+ * counterpart to this entry point; it serves callers that cannot allocate
+ * device memory at all -- for instance a real-time loop where cudaMalloc or
+ * cudaFree would block the host or synchronize the device, or a plugin inside
+ * a host application that owns all GPU memory and offers no allocator.
+ *
+ * Same computation, arguments and results as cpinv_pinv, minus the workspace:
+ * the scratch is a fixed array of CPINV_STATIC_SCRATCH_BYTES (1 MiB) compiled
+ * into the library as device memory, which every GPU that loads the library
+ * keeps until the process exits.  No cudaMalloc, cudaFree or other allocating
+ * routine is called.
+ *   Limit: min(m, n) <= CPINV_STATIC_MAX_ORDER (128) and a workspace that fits
+ *          in the array (cpinv_pinv_workspace_size(m, n, o) <= 1 MiB, true for
+ *          every panel width at that order); larger inputs return
+ *          CPINV_ERR_UNSUPPORTED before any GPU work.
+ *   Set-up: the first call on each device looks up the array's device address
+ *          (cudaGetSymbolAddress) with that device current; make that first
+ *          call before any stream capture begins.
+ *   Sharing: all calls on a device use the same array, which keeps whatever
+ *          the last call left in it (each call clears the state it needs).
+ *          Calls that overlap on the GPU -- on different streams, or from
+ *          several host threads -- race on the array and give wrong results;
+ *          order them on one stream or serialize them.
+ * ------------------------------------------------------------------------- */
+#define CPINV_STATIC_SCRATCH_BYTES (1u << 20)
+#define CPINV_STATIC_MAX_ORDER 128
+int cpinv_pinv_static(const double* G, int64_t m, int64_t n, int64_t ldg,
+                      double* Gp, int64_t ldgp,
+                      const cpinv_opts* o, int64_t* rank_out, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Tracing.  When enabled, every kernel the library launches is bracketed by
  * two CUDA events recorded on the stream it is launched on; reading the
  * profile synchronizes the device and returns, per kernel class, the number

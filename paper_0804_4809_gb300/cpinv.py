@@ -61,6 +61,8 @@ SIGNATURES = {
     "cpinv_rank_workspace_size": (_c_sz, [_c_i64, _c_i64, ctypes.POINTER(Opts)]),
     "cpinv_rank": (ctypes.c_int, [_c_vp, _c_i64, _c_i64, _c_i64, _c_vp, _c_vp, _c_sz,
                                   ctypes.POINTER(Opts), ctypes.POINTER(_c_i64), _c_vp]),
+    "cpinv_pinv_static": (ctypes.c_int, [_c_vp, _c_i64, _c_i64, _c_i64, _c_vp, _c_i64,
+                                         ctypes.POINTER(Opts), ctypes.POINTER(_c_i64), _c_vp]),
     "cpinv_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "cpinv_profile_read": (ctypes.c_int, [ctypes.POINTER(ProfileEntry), ctypes.c_int]),
     "cpinv_launch_count": (ctypes.c_int64, []),
