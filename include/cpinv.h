@@ -51,6 +51,7 @@ extern "C" {
 #define CPINV_ERR_CUDA            4  /* a CUDA runtime call failed */
 #define CPINV_ERR_NUMERICAL       5  /* L'L was not positive definite in FP64 */
 #define CPINV_ERR_UNSUPPORTED     6  /* mode or size not supported by this build */
+#define CPINV_ERR_TIMEOUT         7  /* a bounded device-side wait expired (kernels exited early) */
 
 /* Arithmetic of the dense contractions (Gram, L'L, inverse, chain).
  * The pivot decisions, square roots and the small diagonal-block solves are
@@ -115,6 +116,30 @@ int cpinv_rank(const double* G, int64_t m, int64_t n, int64_t ldg,
                uint8_t* accepted_out,
                void* workspace, size_t workspace_bytes,
                const cpinv_opts* o, int64_t* rank_out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * The dense contraction of the library on its own:
+ *   C = alpha op(A) op(B) + beta C,   op(X) = X or X' (transX != 0),
+ * op(A) M x K, op(B) K x N, C M x N, all row-major FP64 device matrices.
+ * This is the product the pipeline uses for G'G, L'L, the inverse and the
+ * chain (Theorem 1); exposed for callers who want the same arithmetic.
+ *   mode CPINV_MODE_FP64: FP64 fused multiply-adds.
+ *   mode CPINV_MODE_EXACT_SLICE: each row of op(A) and column of op(B) is
+ *     scaled by a power of two and rounded to a signed integer of `bits`
+ *     bits (1..62, 0 = 53); the integer products are computed exactly by
+ *     residue arithmetic on the BF16 tensor cores and each entry of the result
+ *     is rounded once to FP64 (when K > 4096, per 4096-wide chunk of K).
+ * Workspace: cpinv_matmul_workspace_size(M, N, K, mode, bits, symmetric)
+ * bytes, 256-byte aligned (`symmetric` != 0 if B == A and op(B) = op(A)').
+ * `check` != 0 synchronizes the stream and reports device-side errors
+ * (non-finite input, timeout).
+ * ------------------------------------------------------------------------- */
+size_t cpinv_matmul_workspace_size(int64_t M, int64_t N, int64_t K, int32_t mode,
+                                   int32_t bits, int32_t symmetric);
+int cpinv_matmul(int32_t transA, int32_t transB, int64_t M, int64_t N, int64_t K,
+                 double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+                 double beta, double* C, int64_t ldc, int32_t mode, int32_t bits,
+                 void* workspace, size_t workspace_bytes, int32_t check, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free pseudoinverse of small matrices.  The paper has no

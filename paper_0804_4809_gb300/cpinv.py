@@ -63,6 +63,12 @@ SIGNATURES = {
                                   ctypes.POINTER(Opts), ctypes.POINTER(_c_i64), _c_vp]),
     "cpinv_pinv_static": (ctypes.c_int, [_c_vp, _c_i64, _c_i64, _c_i64, _c_vp, _c_i64,
                                          ctypes.POINTER(Opts), ctypes.POINTER(_c_i64), _c_vp]),
+    "cpinv_matmul_workspace_size": (_c_sz, [_c_i64, _c_i64, _c_i64, ctypes.c_int32,
+                                            ctypes.c_int32, ctypes.c_int32]),
+    "cpinv_matmul": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _c_i64, _c_i64, _c_i64,
+                                    ctypes.c_double, _c_vp, _c_i64, _c_vp, _c_i64, ctypes.c_double,
+                                    _c_vp, _c_i64, ctypes.c_int32, ctypes.c_int32, _c_vp, _c_sz,
+                                    ctypes.c_int32, _c_vp]),
     "cpinv_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "cpinv_profile_read": (ctypes.c_int, [ctypes.POINTER(ProfileEntry), ctypes.c_int]),
     "cpinv_launch_count": (ctypes.c_int64, []),
@@ -229,3 +235,29 @@ class PinvPlan:
                               _stream(self.device) if stream is None else stream)
         _check(st)
         return int(r.value) if sync_rank else None
+
+
+def matmul(A: torch.Tensor, B: torch.Tensor, transA: bool = False, transB: bool = False,
+           mode="fp64", bits: int = 0, alpha: float = 1.0, beta: float = 0.0,
+           C: torch.Tensor | None = None, check: bool = True) -> torch.Tensor:
+    """C = alpha op(A) op(B) + beta C in the library's arithmetic (FP64 or
+    exact-slice residue products on the tensor cores)."""
+    A = _mat(A, "A")
+    B = _mat(B, "B")
+    M, K = (A.shape[1], A.shape[0]) if transA else (A.shape[0], A.shape[1])
+    K2, N = (B.shape[1], B.shape[0]) if transB else (B.shape[0], B.shape[1])
+    if K != K2:
+        raise ValueError("inner dimensions differ")
+    if C is None:
+        C = torch.zeros((M, N), dtype=torch.float64, device=A.device)
+    md = _MODES[mode] if isinstance(mode, str) else int(mode)
+    sym = int(A.data_ptr() == B.data_ptr() and transA != transB and M == N)
+    nbytes = lib().cpinv_matmul_workspace_size(M, N, K, md, bits, sym)
+    if nbytes == 0:
+        raise CpinvError(1, "invalid sizes or options")
+    ws = _workspace(nbytes, A.device)
+    st = lib().cpinv_matmul(int(transA), int(transB), M, N, K, float(alpha), A.data_ptr(), _ld(A),
+                            B.data_ptr(), _ld(B), float(beta), C.data_ptr(), _ld(C), md, int(bits),
+                            ws.data_ptr(), ws.numel(), int(check), _stream(A.device))
+    _check(st)
+    return C

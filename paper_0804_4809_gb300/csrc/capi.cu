@@ -38,30 +38,6 @@ struct Arena {
   }
 };
 
-// ---------------------------------------------------------------------------
-// Tracing: events around every launch (when enabled) and a launch counter.
-// ---------------------------------------------------------------------------
-enum Kind { K_GEMM_FP64 = 0, K_GEMM_SLICE = 1, K_DIAG = 2, K_AUX = 3, K_SPLIT = 4, K_COUNT = 5 };
-const char* const kKindName[K_COUNT] = {"gemm_fp64", "gemm_slice", "diag_factor", "aux",
-                                        "slice_split"};
-
-struct TraceRec {
-  cudaEvent_t e0, e1;
-  int kind;
-  bool resolved;
-  double flops;
-  Dim M, N, K;
-  int lower;
-  const int64_t* rdev;
-};
-
-struct Tracer {
-  bool on = false;
-  std::vector<TraceRec> recs;
-};
-Tracer g_tr;
-std::atomic<int64_t> g_launches{0};
-
 int64_t eval_host(const Dim& d, int64_t r) {
   int64_t v = d.off + (d.sel ? r : 0);
   v = v < 0 ? 0 : v;
@@ -75,31 +51,28 @@ double gemm_flops(const Dim& Md, const Dim& Nd, const Dim& Kd, int lower, int64_
   return 2.0 * elems * K;
 }
 
-template <class F>
-cudaError_t traced(cudaStream_t s, int kind, F&& f, const GemmParams* g = nullptr) {
-  g_launches.fetch_add(1, std::memory_order_relaxed);
-  if (!g_tr.on) return f();
-  TraceRec r{};
-  r.kind = kind;
-  if (cudaEventCreate(&r.e0) != cudaSuccess || cudaEventCreate(&r.e1) != cudaSuccess)
-    return cudaErrorUnknown;
-  cudaEventRecord(r.e0, s);
-  cudaError_t e = f();
-  cudaEventRecord(r.e1, s);
-  if (g) {
-    r.M = g->M;
-    r.N = g->N;
-    r.K = g->K;
-    r.lower = g->lower;
-    r.rdev = g->rdev;
-    r.resolved = false;
-  } else {
-    r.resolved = true;
-    r.flops = 0.0;
-  }
-  g_tr.recs.push_back(r);
-  return e;
-}
+// ---------------------------------------------------------------------------
+// Tracing: events around every launch (when enabled) and a launch counter.
+// ---------------------------------------------------------------------------
+const char* const kKindName[KT_COUNT] = {"gemm_fp64", "tc_mma", "diag_factor",
+                                         "aux",       "split",  "crt_reconstruct"};
+
+struct TraceRec {
+  cudaEvent_t e0, e1;
+  int kind;
+  bool resolved;
+  double flops;
+  double mult;
+  Dim M, N, K;
+  int lower;
+};
+
+struct Tracer {
+  bool on = false;
+  std::vector<TraceRec> recs;
+};
+Tracer g_tr;
+std::atomic<int64_t> g_launches{0};
 
 // Resolves the flop counts of the records that depend on the device rank
 // (called at the end of each traced call, while the workspace is alive).
@@ -111,11 +84,42 @@ cudaError_t trace_resolve(cudaStream_t s, const int64_t* rdev) {
   if (e != cudaSuccess) return e;
   for (auto& t : g_tr.recs)
     if (!t.resolved) {
-      t.flops = gemm_flops(t.M, t.N, t.K, t.lower, r);
+      t.flops = t.mult * gemm_flops(t.M, t.N, t.K, t.lower, r);
       t.resolved = true;
     }
   return cudaSuccess;
 }
+
+}  // namespace
+
+void trace_count() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+bool trace_on() { return g_tr.on; }
+int trace_begin(cudaStream_t s) {
+  TraceRec r{};
+  if (cudaEventCreate(&r.e0) != cudaSuccess || cudaEventCreate(&r.e1) != cudaSuccess) return -1;
+  cudaEventRecord(r.e0, s);
+  g_tr.recs.push_back(r);
+  return (int)g_tr.recs.size() - 1;
+}
+void trace_end(int rec, cudaStream_t s, int kind, const GemmParams* g, double mult) {
+  if (rec < 0) return;
+  TraceRec& r = g_tr.recs[(size_t)rec];
+  cudaEventRecord(r.e1, s);
+  r.kind = kind;
+  r.mult = mult;
+  if (g) {
+    r.M = g->M;
+    r.N = g->N;
+    r.K = g->K;
+    r.lower = g->lower;
+    r.resolved = false;
+  } else {
+    r.resolved = true;
+    r.flops = 0.0;
+  }
+}
+
+namespace {
 
 enum Job { JOB_RANK = 0, JOB_PINV = 1, JOB_LSTSQ = 2 };
 
@@ -138,12 +142,53 @@ struct Plan {
   double* c1;    // lstsq: nA x k (also G'F)
   double* c2;
   double* c3;
+  void* crt;     // exact-slice scratch (residues, exponents)
+  size_t crt_bytes;
 };
+
+// Where a product sits in the pipeline decides its arithmetic in exact-slice
+// mode: the Gram matrix is formed from 62-bit integers (an exactly summed,
+// once-rounded G'G), the other large products from 53-bit integers (FP64
+// accuracy); the Cholesky panel operations stay on the FP64 pipe.
+enum Site { S_FP64 = 0, S_GRAM = 1, S_PROD = 2 };
+
+constexpr int64_t kCrtMaxK = 4096;  // exactness bound of one residue product
+
+bool use_exact(const Plan& p, Site site, int64_t Mmax, int64_t Nmax, int64_t Kmax) {
+  if (p.mode != CPINV_MODE_EXACT_SLICE || site == S_FP64) return false;
+  return Kmax >= 64 && Mmax >= 16 && Nmax >= 1;
+}
+
+size_t crt_need(const Plan& p, Site site, int64_t M, int64_t N, int64_t K, bool same) {
+  if (!use_exact(p, site, M, N, K)) return 0;
+  const int beta = site == S_GRAM ? 62 : 53;
+  const int64_t Kc = K < kCrtMaxK ? K : kCrtMaxK;
+  const int nm = crt_moduli_for(Kc, beta, beta);
+  if (nm < 0) return 0;
+  return crt_workspace_bytes(M, N, Kc, nm, same);
+}
+
+size_t crt_plan_bytes(const Plan& p, Job job) {
+  const int64_t nA = p.nA, m = p.m, n = p.n;
+  size_t need = crt_need(p, S_GRAM, nA, nA, p.trans ? n : m, true);
+  if (job == JOB_RANK) return need;
+  auto mx = [&](size_t v) { need = v > need ? v : need; };
+  mx(crt_need(p, S_PROD, nA, nA, nA, true));    // L'L, W'W, X X'
+  mx(crt_need(p, S_PROD, nA, nA, nA, false));   // L M, inverse blocks
+  if (job == JOB_PINV) mx(crt_need(p, S_PROD, n, m, nA, false));  // G+ = K G' or G' K
+  if (job == JOB_LSTSQ) {
+    mx(crt_need(p, S_PROD, n, p.k, m, false));   // G'F (or G't)
+    mx(crt_need(p, S_PROD, nA, p.k, nA, false)); // L'c, M c, L c
+  }
+  return need;
+}
 
 void carve(Plan& p, Arena& a, Job job) {
   const int64_t nA = p.nA, b = p.b;
   const int64_t nb = (nA + b - 1) / b;
   p.st = (DevState*)a.take(sizeof(DevState));
+  p.crt_bytes = crt_plan_bytes(p, job);
+  p.crt = p.crt_bytes ? a.take(p.crt_bytes) : nullptr;
   p.acc = (uint8_t*)a.take((size_t)(nA > 0 ? nA : 1));
   p.colidx = (int32_t*)a.take(sizeof(int32_t) * (size_t)(nA > 0 ? nA : 1));
   p.Z = (double*)a.take(sizeof(double) * (size_t)(b * b));
@@ -176,7 +221,7 @@ bool make_plan(Plan& p, int64_t m, int64_t n, int64_t k, const cpinv_opts* o) {
   p.rel_tol = o->rel_tol;
   if (p.b < 1 || p.b > 64) return false;
   if (!(p.rel_tol >= 0.0) || !std::isfinite(p.rel_tol)) return false;
-  if (o->mode != CPINV_MODE_FP64) return false;
+  if (o->mode != CPINV_MODE_FP64 && o->mode != CPINV_MODE_EXACT_SLICE) return false;
   return true;
 }
 
@@ -198,8 +243,35 @@ struct Ctx {
     if (_e != cudaSuccess) return CPINV_ERR_CUDA; \
   } while (0)
 
-// C = alpha op(A) op(B) + beta C  in the plan's arithmetic.
-cudaError_t matmul(const Ctx& c, const double* A, int64_t lda, bool ta, const double* B,
+// Exact-slice product; K beyond the exactness bound of one residue product is
+// cut into chunks whose results are added in FP64 (beta = 1 after the first).
+cudaError_t crt_product(const GemmParams& g, bool ta, bool tb, int bits, bool same, void* ws,
+                        size_t ws_bytes, DevState* st, cudaStream_t s) {
+  const Dim K = g.K;
+  for (int64_t k0 = 0; k0 < (K.max > 0 ? K.max : 1); k0 += kCrtMaxK) {
+    CrtGemm cg;
+    cg.p = g;
+    const int64_t kmax = K.max - k0 < kCrtMaxK ? K.max - k0 : kCrtMaxK;
+    cg.p.K = K.sel ? Dim{K.off - k0, kmax, 1, 0} : hdim(kmax < K.off - k0 ? kmax : K.off - k0);
+    cg.p.A = ta ? g.A + k0 * g.lda : g.A + k0;
+    cg.p.B = tb ? g.B + k0 : g.B + k0 * g.ldb;
+    cg.p.beta = k0 == 0 ? g.beta : 1.0;
+    cg.transA = ta;
+    cg.transB = tb;
+    cg.same_operand = same;
+    cg.betaA = cg.betaB = bits;
+    cg.ws = ws;
+    cg.ws_bytes = ws_bytes;
+    cg.st = st;
+    KernelTimer t;
+    cudaError_t e = launch_crt_gemm(cg, s, &t);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// C = alpha op(A) op(B) + beta C  in the plan's arithmetic (see Site).
+cudaError_t matmul(const Ctx& c, Site site, const double* A, int64_t lda, bool ta, const double* B,
                    int64_t ldb, bool tb, double* C, int64_t ldc, Dim M, Dim N, Dim K,
                    double alpha, double beta, int lower) {
   GemmParams g;
@@ -217,7 +289,14 @@ cudaError_t matmul(const Ctx& c, const double* A, int64_t lda, bool ta, const do
   g.rdev = c.rdev();
   g.lower = lower;
   g.pad = 0;
-  return traced(c.s, K_GEMM_FP64, [&] { return launch_dgemm(g, ta, tb, c.s); }, &g);
+  const Plan& p = *c.p;
+  if (!use_exact(p, site, M.max, N.max, K.max)) {
+    KernelTimer t;
+    t.gemm = &g;
+    return t.run(KT_GEMM_FP64, c.s, [&] { return launch_dgemm(g, ta, tb, c.s); });
+  }
+  const bool same = A == B && lda == ldb && ta != tb;
+  return crt_product(g, ta, tb, site == S_GRAM ? 62 : 53, same, p.crt, p.crt_bytes, p.st, c.s);
 }
 
 // Blocked full-rank Cholesky, in place on the lower triangle of a (ld = lda).
@@ -230,7 +309,7 @@ int factor(const Ctx& c, double* a, int64_t lda, int spd) {
   const int b = p.b;
   for (int64_t k0 = 0, blk = 0; k0 < nA; k0 += b, ++blk) {
     const Dim nd = spd ? rdim(0, nA) : hdim(nA);
-    CK(traced(c.s, K_DIAG, [&] {
+    CK(KernelTimer().run(KT_DIAG, c.s, [&] {
       return launch_diag_factor(a, lda, nd, k0, b, p.st, c.rdev(), spd ? nullptr : p.acc, p.Z,
                                 spd ? p.Tinv + blk * b * b : nullptr, spd, c.s);
     }));
@@ -246,9 +325,11 @@ int factor(const Ctx& c, double* a, int64_t lda, int spd) {
       bw = hdim(b);
     }
     // panel below the block: L = A Z (in place; one column tile covers the panel)
-    CK(matmul(c, panel, lda, false, p.Z, b, false, panel, lda, below, bw, bw, 1.0, 0.0, 0));
+    CK(matmul(c, S_FP64, panel, lda, false, p.Z, b, false, panel, lda, below, bw, bw, 1.0, 0.0,
+              0));
     // trailing update, lower triangle
-    CK(matmul(c, panel, lda, false, panel, lda, true, trail, lda, below, below, bw, -1.0, 1.0, 1));
+    CK(matmul(c, S_FP64, panel, lda, false, panel, lda, true, trail, lda, below, below, bw, -1.0,
+              1.0, 1));
   }
   return CPINV_OK;
 }
@@ -259,18 +340,42 @@ int front_rank(const Ctx& c, const double* G, int64_t ldg, bool compact) {
   const Plan& p = *c.p;
   const int64_t nA = p.nA;
   if (!p.trans)  // A = G'G
-    CK(matmul(c, G, ldg, true, G, ldg, false, p.bufA, nA, hdim(nA), hdim(nA), hdim(p.m), 1.0,
-              0.0, 1));
+    CK(matmul(c, S_GRAM, G, ldg, true, G, ldg, false, p.bufA, nA, hdim(nA), hdim(nA), hdim(p.m),
+              1.0, 0.0, 1));
   else  // A = G G'
-    CK(matmul(c, G, ldg, false, G, ldg, true, p.bufA, nA, hdim(nA), hdim(nA), hdim(p.n), 1.0,
-              0.0, 1));
-  CK(traced(c.s, K_AUX, [&] { return launch_tol(p.bufA, nA, nA, p.rel_tol, p.st, c.s); }));
+    CK(matmul(c, S_GRAM, G, ldg, false, G, ldg, true, p.bufA, nA, hdim(nA), hdim(nA), hdim(p.n),
+              1.0, 0.0, 1));
+  CK(KernelTimer().run(KT_AUX, c.s,
+                       [&] { return launch_tol(p.bufA, nA, nA, p.rel_tol, p.st, c.s); }));
   int rc = factor(c, p.bufA, nA, 0);
   if (rc) return rc;
-  CK(traced(c.s, K_AUX, [&] { return launch_scan(p.acc, nA, p.colidx, p.st, c.s); }));
+  CK(KernelTimer().run(KT_AUX, c.s,
+                       [&] { return launch_scan(p.acc, nA, p.colidx, p.st, c.s); }));
   if (compact)
-    CK(traced(c.s, K_AUX,
-              [&] { return launch_gather(p.bufA, nA, nA, p.colidx, p.bufL, nA, c.s); }));
+    CK(KernelTimer().run(KT_AUX, c.s, [&] {
+      return launch_gather(p.bufA, nA, nA, p.colidx, p.bufL, nA, c.s);
+    }));
+  return CPINV_OK;
+}
+
+// W[lo:hi, lo:hi] = U[lo:hi, lo:hi]^-1 for the lower-triangular U in bufA,
+// given the inverted diagonal blocks already in W:  split at mid,
+//   W21 = -W22 (U21 W11)     (bufM holds U21 W11)
+int tri_inverse(const Ctx& c, int64_t lo, int64_t hi) {
+  const Plan& p = *c.p;
+  const int64_t nA = p.nA, b = p.b;
+  if (hi - lo <= b) return CPINV_OK;
+  const int64_t blocks = (hi - lo + b - 1) / b;  // >= 2
+  const int64_t mid = lo + (blocks / 2) * b;      // lo < mid < hi
+  int rc = tri_inverse(c, lo, mid);
+  if (rc) return rc;
+  rc = tri_inverse(c, mid, hi);
+  if (rc) return rc;
+  const Dim rows = rdim(-mid, hi - mid), cols = rdim(-lo, mid - lo);
+  CK(matmul(c, S_PROD, p.bufA + mid * nA + lo, nA, false, p.bufW + lo * nA + lo, nA, false,
+            p.bufM + mid * nA + lo, nA, rows, cols, cols, 1.0, 0.0, 0));
+  CK(matmul(c, S_PROD, p.bufW + mid * nA + mid, nA, false, p.bufM + mid * nA + lo, nA, false,
+            p.bufW + mid * nA + lo, nA, rows, cols, rows, -1.0, 0.0, 0));
   return CPINV_OK;
 }
 
@@ -281,21 +386,18 @@ int front_inverse(const Ctx& c) {
   const int b = p.b;
   const Dim R = rdim(0, nA);
   // N = L'L (lower), into bufA
-  CK(matmul(c, p.bufL, nA, true, p.bufL, nA, false, p.bufA, nA, R, R, hdim(nA), 1.0, 0.0, 1));
+  CK(matmul(c, S_PROD, p.bufL, nA, true, p.bufL, nA, false, p.bufA, nA, R, R, hdim(nA), 1.0, 0.0,
+            1));
   int rc = factor(c, p.bufA, nA, 1);
   if (rc) return rc;
-  // W = U^-1 by block rows
-  CK(traced(c.s, K_AUX,
-            [&] { return launch_tri_inv_init(p.bufW, nA, nA, c.rdev(), p.Tinv, b, c.s); }));
-  for (int64_t ib = b, blk = 1; ib < nA; ib += b, ++blk) {
-    const Dim rows = rdim(-ib, b);
-    CK(matmul(c, p.bufA + ib * nA, nA, false, p.bufW, nA, false, p.Tmp, nA, rows, hdim(ib),
-              hdim(ib), 1.0, 0.0, 0));
-    CK(matmul(c, p.Tinv + blk * b * b, b, false, p.Tmp, nA, false, p.bufW + ib * nA, nA, rows,
-              hdim(ib), rows, -1.0, 0.0, 0));
-  }
+  // W = U^-1: diagonal blocks from the factorisation, the rest by recursion
+  CK(KernelTimer().run(KT_AUX, c.s, [&] {
+    return launch_tri_inv_init(p.bufW, nA, nA, c.rdev(), p.Tinv, b, c.s);
+  }));
+  rc = tri_inverse(c, 0, nA);
+  if (rc) return rc;
   // M = W'W (full, symmetric)
-  CK(matmul(c, p.bufW, nA, true, p.bufW, nA, false, p.bufM, nA, R, R, R, 1.0, 0.0, 0));
+  CK(matmul(c, S_PROD, p.bufW, nA, true, p.bufW, nA, false, p.bufM, nA, R, R, R, 1.0, 0.0, 0));
   return CPINV_OK;
 }
 
@@ -307,6 +409,7 @@ int finish(const Ctx& c, int64_t* rank_out) {
   CK(cudaStreamSynchronize(c.s));
   if (h.status & ST_NONFINITE) return CPINV_ERR_NONFINITE_INPUT;
   if (h.status & ST_NUMERICAL) return CPINV_ERR_NUMERICAL;
+  if (h.status & ST_TIMEOUT) return CPINV_ERR_TIMEOUT;
   *rank_out = h.rank;
   return CPINV_OK;
 }
@@ -344,6 +447,7 @@ const char* cpinv_status_string(int status) {
     case CPINV_ERR_CUDA: return "CUDA error";
     case CPINV_ERR_NUMERICAL: return "L'L not positive definite in FP64";
     case CPINV_ERR_UNSUPPORTED: return "unsupported mode or size";
+    case CPINV_ERR_TIMEOUT: return "a device-side wait timed out";
     default: return "unknown status";
   }
 }
@@ -373,7 +477,7 @@ static int check_opts(const cpinv_opts* o) {
   if (o->mode != CPINV_MODE_FP64 && o->mode != CPINV_MODE_EXACT_SLICE &&
       o->mode != CPINV_MODE_SPLIT_BF16X3)
     return CPINV_ERR_INVALID_ARG;
-  if (o->mode != CPINV_MODE_FP64) return CPINV_ERR_UNSUPPORTED;
+  if (o->mode == CPINV_MODE_SPLIT_BF16X3) return CPINV_ERR_UNSUPPORTED;
   if (o->panel < 0 || o->panel > 64 || o->reserved != 0) return CPINV_ERR_INVALID_ARG;
   if (!(o->rel_tol >= 0.0) || !std::isfinite(o->rel_tol)) return CPINV_ERR_INVALID_ARG;
   return CPINV_OK;
@@ -397,7 +501,8 @@ int cpinv_rank(const double* G, int64_t m, int64_t n, int64_t ldg, uint8_t* acce
   CK(cudaMemsetAsync(p.st, 0, sizeof(DevState), c.s));
   if (int rc = front_rank(c, G, ldg, false)) return rc;
   if (accepted_out)
-    CK(traced(c.s, K_AUX, [&] { return launch_copy_mask(p.acc, accepted_out, p.nA, c.s); }));
+    CK(KernelTimer().run(KT_AUX, c.s,
+                         [&] { return launch_copy_mask(p.acc, accepted_out, p.nA, c.s); }));
   return finish(c, rank_out);
 }
 
@@ -422,15 +527,16 @@ int cpinv_pinv(const double* G, int64_t m, int64_t n, int64_t ldg, double* Gp, i
   const int64_t nA = p.nA;
   const Dim R = rdim(0, nA);
   // X = L M  (bufW),  K = X X'  (bufA)
-  CK(matmul(c, p.bufL, nA, false, p.bufM, nA, false, p.bufW, nA, hdim(nA), R, R, 1.0, 0.0, 0));
-  CK(matmul(c, p.bufW, nA, false, p.bufW, nA, true, p.bufA, nA, hdim(nA), hdim(nA), R, 1.0, 0.0,
+  CK(matmul(c, S_PROD, p.bufL, nA, false, p.bufM, nA, false, p.bufW, nA, hdim(nA), R, R, 1.0, 0.0,
             0));
+  CK(matmul(c, S_PROD, p.bufW, nA, false, p.bufW, nA, true, p.bufA, nA, hdim(nA), hdim(nA), R,
+            1.0, 0.0, 0));
   if (!p.trans)  // G+ = K G'   (n x n)(n x m)
-    CK(matmul(c, p.bufA, nA, false, G, ldg, true, Gp, ldgp, hdim(n), hdim(m), hdim(n), 1.0, 0.0,
-              0));
+    CK(matmul(c, S_PROD, p.bufA, nA, false, G, ldg, true, Gp, ldgp, hdim(n), hdim(m), hdim(n), 1.0,
+              0.0, 0));
   else  // G+ = G' K   (n x m)(m x m)
-    CK(matmul(c, G, ldg, true, p.bufA, nA, false, Gp, ldgp, hdim(n), hdim(m), hdim(m), 1.0, 0.0,
-              0));
+    CK(matmul(c, S_PROD, G, ldg, true, p.bufA, nA, false, Gp, ldgp, hdim(n), hdim(m), hdim(m), 1.0,
+              0.0, 0));
   return finish(c, rank_out);
 }
 
@@ -466,22 +572,97 @@ int cpinv_lstsq(const double* G, int64_t m, int64_t n, int64_t ldg, const double
   const Dim R = rdim(0, nA);
   if (!p.trans) {
     // c1 <- G'F (n x k);  c2 <- L' c1 (r x k)
-    CK(matmul(c, G, ldg, true, F, ldf, false, p.c1, k, hdim(n), hdim(k), hdim(m), 1.0, 0.0, 0));
-    CK(matmul(c, p.bufL, nA, true, p.c1, k, false, p.c2, k, R, hdim(k), hdim(nA), 1.0, 0.0, 0));
+    CK(matmul(c, S_PROD, G, ldg, true, F, ldf, false, p.c1, k, hdim(n), hdim(k), hdim(m), 1.0,
+              0.0, 0));
+    CK(matmul(c, S_PROD, p.bufL, nA, true, p.c1, k, false, p.c2, k, R, hdim(k), hdim(nA), 1.0, 0.0,
+              0));
   } else {
     // c2 <- L' F (r x k)
-    CK(matmul(c, p.bufL, nA, true, F, ldf, false, p.c2, k, R, hdim(k), hdim(nA), 1.0, 0.0, 0));
+    CK(matmul(c, S_PROD, p.bufL, nA, true, F, ldf, false, p.c2, k, R, hdim(k), hdim(nA), 1.0, 0.0,
+              0));
   }
-  CK(matmul(c, p.bufM, nA, false, p.c2, k, false, p.c3, k, R, hdim(k), R, 1.0, 0.0, 0));
-  CK(matmul(c, p.bufM, nA, false, p.c3, k, false, p.c2, k, R, hdim(k), R, 1.0, 0.0, 0));
+  CK(matmul(c, S_PROD, p.bufM, nA, false, p.c2, k, false, p.c3, k, R, hdim(k), R, 1.0, 0.0, 0));
+  CK(matmul(c, S_PROD, p.bufM, nA, false, p.c3, k, false, p.c2, k, R, hdim(k), R, 1.0, 0.0, 0));
   if (!p.trans) {
-    CK(matmul(c, p.bufL, nA, false, p.c2, k, false, W, ldw, hdim(n), hdim(k), R, 1.0, 0.0, 0));
+    CK(matmul(c, S_PROD, p.bufL, nA, false, p.c2, k, false, W, ldw, hdim(n), hdim(k), R, 1.0, 0.0,
+              0));
   } else {
     // t = L c (m x k) into c1, W = G' t
-    CK(matmul(c, p.bufL, nA, false, p.c2, k, false, p.c1, k, hdim(m), hdim(k), R, 1.0, 0.0, 0));
-    CK(matmul(c, G, ldg, true, p.c1, k, false, W, ldw, hdim(n), hdim(k), hdim(m), 1.0, 0.0, 0));
+    CK(matmul(c, S_PROD, p.bufL, nA, false, p.c2, k, false, p.c1, k, hdim(m), hdim(k), R, 1.0,
+              0.0, 0));
+    CK(matmul(c, S_PROD, G, ldg, true, p.c1, k, false, W, ldw, hdim(n), hdim(k), hdim(m), 1.0, 0.0,
+              0));
   }
   return finish(c, rank_out);
+}
+
+size_t cpinv_matmul_workspace_size(int64_t M, int64_t N, int64_t K, int32_t mode, int32_t bits,
+                                   int32_t symmetric) {
+  if (M < 0 || N < 0 || K < 0) return 0;
+  if (mode == CPINV_MODE_FP64) return 256;
+  if (mode != CPINV_MODE_EXACT_SLICE) return 0;
+  const int beta = bits ? bits : 53;
+  if (beta < 1 || beta > 62) return 0;
+  const int64_t Kc = K < kCrtMaxK ? (K > 0 ? K : 1) : kCrtMaxK;
+  const int nm = crt_moduli_for(Kc, beta, beta);
+  if (nm < 0) return 0;
+  return 1024 + crt_workspace_bytes(M, N, Kc, nm, symmetric != 0);
+}
+
+int cpinv_matmul(int32_t transA, int32_t transB, int64_t M, int64_t N, int64_t K, double alpha,
+                 const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                 int64_t ldc, int32_t mode, int32_t bits, void* workspace, size_t workspace_bytes,
+                 int32_t check, void* stream) {
+  if (M < 0 || N < 0 || K < 0) return CPINV_ERR_INVALID_ARG;
+  if (mode != CPINV_MODE_FP64 && mode != CPINV_MODE_EXACT_SLICE) {
+    return mode == CPINV_MODE_SPLIT_BF16X3 ? CPINV_ERR_UNSUPPORTED : CPINV_ERR_INVALID_ARG;
+  }
+  const int64_t arows = transA ? K : M, acols = transA ? M : K;
+  const int64_t brows = transB ? N : K, bcols = transB ? K : N;
+  if ((arows > 0 && lda < acols) || (brows > 0 && ldb < bcols) || ldc < N)
+    return CPINV_ERR_INVALID_ARG;
+  if (M == 0 || N == 0) return CPINV_OK;
+  if (!C || (K > 0 && (!A || !B))) return CPINV_ERR_INVALID_ARG;
+  if (!std::isfinite(alpha) || !std::isfinite(beta)) return CPINV_ERR_INVALID_ARG;
+  const int beta_bits = bits ? bits : 53;
+  if (mode == CPINV_MODE_EXACT_SLICE && (beta_bits < 1 || beta_bits > 62)) return CPINV_ERR_INVALID_ARG;
+  const bool same = A == B && lda == ldb && (transA != 0) != (transB != 0) && M == N;
+  const size_t need = cpinv_matmul_workspace_size(M, N, K, mode, bits, same ? 1 : 0);
+  if (!workspace || ((uintptr_t)workspace & 255u) || workspace_bytes < need)
+    return CPINV_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevState* st = (DevState*)workspace;
+  CK(cudaMemsetAsync(st, 0, sizeof(DevState), s));
+  GemmParams g;
+  std::memset(&g, 0, sizeof(g));
+  g.A = A;
+  g.B = B;
+  g.C = C;
+  g.lda = lda;
+  g.ldb = ldb;
+  g.ldc = ldc;
+  g.M = hdim(M);
+  g.N = hdim(N);
+  g.K = hdim(K);
+  g.alpha = alpha;
+  g.beta = beta;
+  g.rdev = &st->rank;
+  if (mode == CPINV_MODE_FP64 || K == 0) {
+    KernelTimer t;
+    t.gemm = &g;
+    CK(t.run(KT_GEMM_FP64, s, [&] { return launch_dgemm(g, transA != 0, transB != 0, s); }));
+  } else {
+    CK(crt_product(g, transA != 0, transB != 0, beta_bits, same, (char*)workspace + 1024,
+                   workspace_bytes - 1024, st, s));
+  }
+  CK(trace_resolve(s, &st->rank));
+  if (!check) return CPINV_OK;
+  DevState h;
+  CK(cudaMemcpyAsync(&h, st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h.status & ST_NONFINITE) return CPINV_ERR_NONFINITE_INPUT;
+  if (h.status & ST_TIMEOUT) return CPINV_ERR_TIMEOUT;
+  return CPINV_OK;
 }
 
 int cpinv_profile_enable(int on) {
@@ -497,8 +678,8 @@ int cpinv_profile_enable(int on) {
 
 int cpinv_profile_read(cpinv_profile_entry* out, int max_entries) {
   if (cudaDeviceSynchronize() != cudaSuccess) return -1;
-  int64_t launches[K_COUNT] = {0};
-  double ms[K_COUNT] = {0}, flops[K_COUNT] = {0};
+  int64_t launches[KT_COUNT] = {0};
+  double ms[KT_COUNT] = {0}, flops[KT_COUNT] = {0};
   for (auto& t : g_tr.recs) {
     float e = 0.f;
     if (cudaEventElapsedTime(&e, t.e0, t.e1) != cudaSuccess) return -1;
@@ -510,7 +691,7 @@ int cpinv_profile_read(cpinv_profile_entry* out, int max_entries) {
   }
   g_tr.recs.clear();
   int n = 0;
-  for (int k = 0; k < K_COUNT; ++k) {
+  for (int k = 0; k < KT_COUNT; ++k) {
     if (!launches[k]) continue;
     if (out && n < max_entries) {
       std::memset(&out[n], 0, sizeof(out[n]));

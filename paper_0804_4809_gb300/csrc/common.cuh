@@ -28,7 +28,7 @@ __device__ __forceinline__ int64_t eval_dim(const Dim& d, const int64_t* rdev) {
 }
 
 // Status bits recorded by kernels (OR-ed into DevState::status).
-enum : int32_t { ST_NONFINITE = 1, ST_NUMERICAL = 2 };
+enum : int32_t { ST_NONFINITE = 1, ST_NUMERICAL = 2, ST_TIMEOUT = 4 };
 
 // Per-call device state, at the start of the workspace.
 struct DevState {

@@ -1,0 +1,909 @@
+// FP64-accurate matrix products on the BF16 tensor cores (tcgen05) by residue
+// arithmetic -- the "exact-slice" arithmetic of the library (see crt.h).
+//
+//   split_kernel        FP64 operand -> per-row power-of-two scale, integer of
+//                       <= beta bits, balanced residues mod p_j as BF16,
+//                       stored K-major: S[j][row][k]            (HBM-bound)
+//   crt_mma_kernel      per (output tile, modulus): C_j = A_j B_j' on tcgen05,
+//                       TMA-fed 4..6-stage pipeline, FP32 accumulators in
+//                       TMEM (double-buffered over moduli), epilogue reduces
+//                       each exact integer sum mod p_j to one byte  (tensor)
+//   reconstruct_kernel  CRT of the n residues -> exact integer -> FP64
+//                       (one rounding) x 2^(scale_i + scale_j), then
+//                       alpha * . + beta * C                       (integer ALU)
+//
+// Every spin-wait on an mbarrier has an iteration limit; on expiry the CTA
+// records ST_TIMEOUT in the call's status word, stops issuing work, waits (with
+// a limit) for the copies it has in flight, frees its tensor memory and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+#include "crt.h"
+#include "kernels.h"
+
+namespace cpinv {
+
+// ---------------------------------------------------------------------------
+// host: CRT constants
+// ---------------------------------------------------------------------------
+namespace crt {
+
+namespace {
+// little-endian 32-bit limbs, fixed width
+struct Big {
+  uint32_t w[kLimbs];
+};
+Big big_from(uint64_t v) {
+  Big b{};
+  b.w[0] = (uint32_t)v;
+  b.w[1] = (uint32_t)(v >> 32);
+  return b;
+}
+Big big_mul_small(const Big& a, uint32_t m) {
+  Big r{};
+  uint64_t carry = 0;
+  for (int i = 0; i < kLimbs; ++i) {
+    uint64_t t = (uint64_t)a.w[i] * m + carry;
+    r.w[i] = (uint32_t)t;
+    carry = t >> 32;
+  }
+  return r;
+}
+Big big_div_small(const Big& a, uint32_t d, uint32_t* rem) {
+  Big q{};
+  uint64_t r = 0;
+  for (int i = kLimbs - 1; i >= 0; --i) {
+    uint64_t cur = (r << 32) | a.w[i];
+    q.w[i] = (uint32_t)(cur / d);
+    r = cur % d;
+  }
+  if (rem) *rem = (uint32_t)r;
+  return q;
+}
+int big_bitlen(const Big& a) {
+  for (int i = kLimbs - 1; i >= 0; --i)
+    if (a.w[i]) return 32 * i + 32 - __builtin_clz(a.w[i]);
+  return 0;
+}
+uint64_t big_shr64(const Big& a, int sh) {  // low 64 bits of a >> sh
+  uint64_t r = 0;
+  for (int b = 0; b < 64; ++b) {
+    const int pos = sh + b;
+    if (pos < 32 * kLimbs && ((a.w[pos / 32] >> (pos % 32)) & 1u)) r |= (uint64_t)1 << b;
+  }
+  return r;
+}
+}  // namespace
+
+int moduli_for_bits(int bits) {
+  double acc = 0.0;
+  for (int n = 1; n <= kMaxMod; ++n) {
+    acc += std::log2((double)kModuli[n - 1]);
+    if (acc > (double)bits + 0.01) return n;
+  }
+  return -1;
+}
+
+void make_consts(int n, Consts* c) {
+  std::memset(c, 0, sizeof(*c));
+  c->n = n;
+  Big P = big_from(1);
+  for (int j = 0; j < n; ++j) P = big_mul_small(P, (uint32_t)kModuli[j]);
+  std::memcpy(c->P, P.w, sizeof(P.w));
+  uint32_t rem;
+  Big half = big_div_small(P, 2, &rem);
+  std::memcpy(c->halfP, half.w, sizeof(half.w));
+  for (int j = 0; j < n; ++j) {
+    const uint32_t p = (uint32_t)kModuli[j];
+    Big Mj = big_div_small(P, p, &rem);
+    std::memcpy(c->Mj[j], Mj.w, sizeof(Mj.w));
+    uint32_t mm;
+    big_div_small(Mj, p, &mm);  // Mj mod p
+    uint32_t y = 0;
+    for (uint32_t t = 1; t < p; ++t)
+      if ((mm * t) % p == 1) {
+        y = t;
+        break;
+      }
+    for (uint32_t r = 0; r < 128; ++r) c->tab[j][r] = (uint8_t)((r * y) % p);
+  }
+  const int bl = big_bitlen(P);
+  c->shift = bl > 58 ? bl - 58 : 0;
+  const uint64_t ptop = big_shr64(P, c->shift);
+  c->inv_ptop = (float)(1.0 / (double)ptop);
+}
+
+}  // namespace crt
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int BM = 128;       // rows of an output tile (TMEM lanes)
+constexpr int BK = 64;        // K per pipeline stage: 64 BF16 = one 128-byte swizzle row
+constexpr uint32_t kSpinLimit = 1u << 26;
+
+// ---------------------------------------------------------------------------
+// split: op(X) (rows x K, FP64) -> residues
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ bool nonfinite_bits(uint64_t b) { return ((b >> 52) & 0x7FF) == 0x7FF; }
+
+// Row exponents: E[i] = max biased exponent over row i of op(X) (0 if the row
+// is 0), accumulated with atomicMax into a zeroed array.
+// trans = 0: row i is contiguous (X[i*ld + k]); one warp per row.
+// trans = 1: row i of op(X) is column i of X; a 32-row x 8-chunk block,
+//            coalesced over i, each thread scanning a slice of k.
+__global__ void row_expo_kernel(const double* X, int64_t ld, int trans, Dim rowsd, Dim colsd,
+                                const int64_t* rdev, int32_t* E, DevState* st) {
+  const int64_t rows = eval_dim(rowsd, rdev), cols = eval_dim(colsd, rdev);
+  int emax = 0, bad = 0;
+  int64_t i;
+  if (!trans) {
+    i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i < rows) {
+      const uint64_t* row = reinterpret_cast<const uint64_t*>(X + i * ld);
+      for (int64_t k = lane; k < cols; k += 32) {
+        const uint64_t b = row[k];
+        const int e = (int)((b >> 52) & 0x7FF);
+        if (e == 0x7FF) bad = 1;
+        else if ((b << 1) != 0 && e > emax) emax = e;
+      }
+    }
+    for (int o = 16; o; o >>= 1) {
+      emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+      bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if (lane != 0) return;
+  } else {
+    i = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
+    const int64_t kc = (cols + gridDim.y * 8 - 1) / (gridDim.y * 8);
+    const int64_t kb = ((int64_t)blockIdx.y * 8 + (threadIdx.x >> 5)) * kc;
+    const int64_t ke = kb + kc < cols ? kb + kc : cols;
+    if (i < rows)
+      for (int64_t k = kb; k < ke; ++k) {
+        const uint64_t b = reinterpret_cast<const uint64_t*>(X)[k * ld + i];
+        const int e = (int)((b >> 52) & 0x7FF);
+        if (e == 0x7FF) bad = 1;
+        else if ((b << 1) != 0 && e > emax) emax = e;
+      }
+  }
+  if (i < rows && emax > 0) atomicMax(&E[i], emax);
+  if (bad) atomicOr(&st->status, ST_NONFINITE);
+}
+
+// |x| * 2^(beta - e_row) rounded to nearest, as an unsigned magnitude, where
+// e_row = Emax - 1022 (so |x| < 2^e_row):  a = m * 2^(E - Emax + beta - 53).
+__device__ __forceinline__ uint64_t integerize(uint64_t b, int Emax, int beta) {
+  const int E = (int)((b >> 52) & 0x7FF);
+  if ((b << 1) == 0 || Emax == 0) return 0;
+  uint64_t m = b & 0xFFFFFFFFFFFFFull;
+  int Eeff = E;
+  if (E == 0) Eeff = 1;
+  else m |= 0x10000000000000ull;
+  const int sh = Eeff - Emax + beta - 53;
+  if (sh >= 0) return m << sh;  // beta <= 62 keeps this below 2^63
+  const int rs = -sh;
+  if (rs > 63) return 0;
+  const uint64_t half = (uint64_t)1 << (rs - 1);
+  return (m + half) >> rs;
+}
+
+// residues of the 32x32 tile (rows i0.., k0..) of op(X); one thread per element
+__global__ void __launch_bounds__(256) split_kernel(const double* X, int64_t ld, int trans,
+                                                    Dim rowsd, Dim colsd, int64_t rows_max,
+                                                    int64_t kpad, const int64_t* rdev,
+                                                    const int32_t* E, int n_mod, int beta,
+                                                    bf16* out) {
+  __shared__ uint64_t tile[32][33];
+  const int64_t rows = eval_dim(rowsd, rdev), cols = eval_dim(colsd, rdev);
+  const int64_t i0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  // load: element (i, k) of op(X)
+  for (int q = ty; q < 32; q += 8) {
+    uint64_t v = 0;
+    if (!trans) {
+      const int64_t i = i0 + q, k = k0 + tx;
+      if (i < rows && k < cols) v = reinterpret_cast<const uint64_t*>(X)[i * ld + k];
+      tile[q][tx] = v;
+    } else {
+      const int64_t k = k0 + q, i = i0 + tx;
+      if (i < rows && k < cols) v = reinterpret_cast<const uint64_t*>(X)[k * ld + i];
+      tile[tx][q] = v;
+    }
+  }
+  __syncthreads();
+  const size_t plane = (size_t)rows_max * (size_t)kpad;
+  for (int q = ty; q < 32; q += 8) {
+    const int64_t i = i0 + q, k = k0 + tx;
+    if (i >= rows_max || k >= kpad) continue;
+    const uint64_t b = tile[q][tx];
+    uint64_t a = 0;
+    bool neg = false;
+    if (i < rows && k < cols && !nonfinite_bits(b)) {
+      a = integerize(b, E[i], beta);
+      neg = (b >> 63) != 0;
+    }
+    const uint32_t ahi = (uint32_t)(a >> 32), alo = (uint32_t)a;
+    bf16* o = out + (size_t)i * kpad + k;
+#pragma unroll
+    for (int j = 0; j < crt::kMaxMod; ++j) {
+      if (j >= n_mod) break;
+      const uint32_t p = (uint32_t)crt::modulus(j);
+      const uint32_t two32 = (uint32_t)((((uint64_t)1) << 32) % p);
+      uint32_t r = ((ahi % p) * two32 + (alo % p)) % p;
+      if (neg && r) r = p - r;
+      const int v = (int)r > (int)(p / 2) ? (int)r - (int)p : (int)r;
+      o[j * plane] = __float2bfloat16_rn((float)v);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tcgen05 / TMA / mbarrier helpers (inline PTX)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: false on timeout (or if another role already gave up)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 1023u) == 1023u && *abort) return false;
+    if (it > 4096) __nanosleep(64);
+  }
+  *abort = 1;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                     // leading byte offset (unused, K-major SW128)
+  d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                     // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;                     // layout: 128-byte swizzle
+  return d;
+}
+
+template <int BN>
+__device__ __forceinline__ constexpr uint32_t idesc_bf16() {
+  return (1u << 4)                 // D: FP32
+         | (1u << 7)               // A: BF16
+         | (1u << 10)              // B: BF16
+         | ((uint32_t)(BN >> 3) << 17)
+         | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// the tensor-core kernel
+// ---------------------------------------------------------------------------
+
+struct MmaParams {
+  Dim M, N;                 // output size (may depend on the device rank)
+  const int64_t* rdev;
+  int32_t nk;               // K / BK (K padded)
+  int32_t n_mod;
+  int32_t mods_per_cta;
+  int32_t lower;            // skip tiles strictly above the diagonal
+  uint8_t* R;               // residues [n_mod][Mpad][Npad]
+  int64_t Mpad, Npad;
+  int32_t* status;          // DevState::status
+};
+
+template <int BN, int STAGES>
+struct __align__(1024) MmaSmem {
+  bf16 A[STAGES][BM * BK];
+  bf16 B[STAGES][BN * BK];
+  uint64_t full[STAGES];
+  uint64_t empty[STAGES];
+  uint64_t accfull[2];
+  uint64_t accempty[2];
+  uint64_t done;
+  uint32_t tmem_base;
+  int abort;
+};
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(192, 1)
+    crt_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   MmaParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  MmaSmem<BN, STAGES>& sm = *reinterpret_cast<MmaSmem<BN, STAGES>*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  const int64_t M = eval_dim(p.M, p.rdev), N = eval_dim(p.N, p.rdev);
+  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+  const int jbeg = blockIdx.z * p.mods_per_cta;
+  const int jend = min(p.n_mod, jbeg + p.mods_per_cta);
+  if (m0 >= M || n0 >= N || jbeg >= jend) return;
+  if (p.lower && n0 > m0 + BM - 1) return;
+  const int nmods = jend - jbeg;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&sm.full[s], 1);
+      mbar_init(&sm.empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&sm.accfull[a], 1);
+      mbar_init(&sm.accempty[a], 4);
+    }
+    mbar_init(&sm.done, 1);
+    sm.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&sm.tmem_base)),
+                 "r"(2 * BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sm.tmem_base;
+  volatile int* abort = &sm.abort;
+  constexpr uint32_t kStageBytes = (BM + BN) * BK * sizeof(bf16);
+  const int nk = p.nk;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      uint32_t it = 0;
+      for (int jj = 0; jj < nmods && !*abort; ++jj) {
+        const int j = jbeg + jj;
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = (int)(it % STAGES);
+          const uint32_t ph = (it / STAGES) & 1u;
+          if (!mbar_wait(&sm.empty[s], ph ^ 1u, abort)) break;
+          mbar_expect_tx(&sm.full[s], kStageBytes);
+          tma_load_3d(sm.A[s], &tmA, &sm.full[s], kb * BK, (int)m0, j);
+          tma_load_3d(sm.B[s], &tmB, &sm.full[s], kb * BK, (int)n0, j);
+        }
+      }
+      // drain: every issued stage must have landed before the CTA exits
+      const uint32_t issued = it;
+      for (uint32_t q = issued > STAGES ? issued - STAGES : 0; q < issued; ++q) {
+        const int s = (int)(q % STAGES);
+        for (uint32_t t = 0; t < kSpinLimit && !mbar_try(&sm.full[s], (q / STAGES) & 1u); ++t) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16<BN>();
+      uint32_t it = 0;
+      for (int jj = 0; jj < nmods && !*abort; ++jj) {
+        const int acc = jj & 1;
+        if (!mbar_wait(&sm.accempty[acc], ((jj >> 1) & 1u) ^ 1u, abort)) break;
+        tc_fence_after();
+        const uint32_t dtm = tmem + (uint32_t)(acc * BN);
+        bool ok = true;
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = (int)(it % STAGES);
+          if (!mbar_wait(&sm.full[s], (it / STAGES) & 1u, abort)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(sm.A[s]), b0 = smem_u32(sm.B[s]);
+#pragma unroll
+          for (int ks = 0; ks < BK / 16; ++ks) {
+            umma_bf16(dtm, umma_desc_sw128(a0 + ks * 32), umma_desc_sw128(b0 + ks * 32), idesc,
+                      (kb | ks) != 0);
+          }
+          umma_commit(&sm.empty[s]);  // stage reusable once these MMAs are done
+        }
+        if (!ok) break;
+        umma_commit(&sm.accfull[acc]);
+      }
+      // every MMA issued by this thread has finished once `done` completes
+      umma_commit(&sm.done);
+      for (uint32_t t = 0; t < kSpinLimit && !mbar_try(&sm.done, 0); ++t) {
+      }
+    }
+  } else {
+    // ---------------- epilogue: 4 warps, warp w reads TMEM lanes 32*(w%4).. ----------------
+    const int q = warp & 3;
+    const int64_t row = m0 + q * 32 + lane;
+    for (int jj = 0; jj < nmods; ++jj) {
+      const int acc = jj & 1;
+      const int j = jbeg + jj;
+      if (!mbar_wait(&sm.accfull[acc], (jj >> 1) & 1u, abort)) break;
+      tc_fence_after();
+      int pj = 0;
+#pragma unroll
+      for (int t = 0; t < crt::kMaxMod; ++t)
+        if (t == j) pj = crt::modulus(t);
+      const float pfl = (float)pj, inv = 1.0f / (float)pj;
+      uint8_t* out = p.R + ((size_t)j * p.Mpad + row) * p.Npad + n0;
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 32) {
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c), v);
+        uint32_t packed[8];
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+          // exact integer |x| <= 2^24: x mod p in [0, p)
+          const float x = __uint_as_float(v[e]);
+          float qf = floorf(x * inv);
+          float r = fmaf(-qf, pfl, x);
+          if (r < 0.f) r += pfl;
+          if (r >= pfl) r -= pfl;
+          const uint32_t rb = __float_as_uint(r + 8388608.0f) & 0xFFu;  // 2^23 trick
+          if ((e & 3) == 0) packed[e >> 2] = 0;
+          packed[e >> 2] |= rb << (8 * (e & 3));
+        }
+        uint4* dst = reinterpret_cast<uint4*>(out + c);
+        dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm.accempty[acc]);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN));
+  }
+  if (threadIdx.x == 0 && sm.abort) atomicOr(p.status, ST_TIMEOUT);
+}
+
+// ---------------------------------------------------------------------------
+// reconstruction
+// ---------------------------------------------------------------------------
+
+struct ReconParams {
+  const uint8_t* R;
+  int64_t Mpad, Npad;
+  Dim M, N;
+  const int64_t* rdev;
+  const int32_t* EA;  // biased exponent maxima of the rows of op(A)
+  const int32_t* EB;  // ... of the columns of op(B)
+  int32_t betaA, betaB;
+  double alpha, beta;
+  double* C;
+  int64_t ldc;
+  int32_t lower;
+  int32_t pad;
+};
+
+__device__ __forceinline__ double compose_double(bool neg, const uint32_t (&mag)[crt::kLimbs],
+                                                 int scale) {
+  // correctly rounded mag * 2^scale (mag < 2^160), via integer operations
+  int top = -1;
+#pragma unroll
+  for (int i = crt::kLimbs - 1; i >= 0; --i)
+    if (top < 0 && mag[i]) top = 32 * i + 31 - __clz(mag[i]);
+  if (top < 0) return neg ? -0.0 : 0.0;
+  // 64 bits starting at bit (top - 63), sticky below
+  const int lo_bit = top - 63;
+  uint64_t t = 0;
+  bool sticky = false;
+#pragma unroll
+  for (int i = 0; i < crt::kLimbs; ++i) {
+    const int base = 32 * i;  // bits base .. base+31 of mag
+    const uint64_t w = mag[i];
+    const int off = base - lo_bit;  // where bit `base` lands in t
+    if (off >= 64 || off <= -32) {
+      if (off <= -32 && w) sticky = true;
+      continue;
+    }
+    if (off >= 0) t |= w << off;
+    else {
+      t |= w >> (-off);
+      if (w & ((1ull << (-off)) - 1ull)) sticky = true;
+    }
+  }
+  uint64_t mant = t >> 11;
+  const uint64_t rem = t & 0x7FFull;
+  if (rem > 0x400ull || (rem == 0x400ull && (sticky || (mant & 1ull)))) ++mant;
+  int e = top;  // value = mant * 2^(top - 52)
+  if (mant >> 53) {
+    mant >>= 1;
+    ++e;
+  }
+  const int biased = e + scale + 1023;
+  if (biased <= 0 || biased >= 2047) {
+    // out of the normal range: let the FP64 unit handle under/overflow
+    const double d = ldexp((double)mant, e - 52 + scale);
+    return neg ? -d : d;
+  }
+  const uint64_t bits = ((uint64_t)neg << 63) | ((uint64_t)biased << 52) | (mant & 0xFFFFFFFFFFFFFull);
+  return __longlong_as_double((long long)bits);
+}
+
+__global__ void __launch_bounds__(256) reconstruct_kernel(ReconParams p,
+                                                          const __grid_constant__ crt::Consts c) {
+  __shared__ uint8_t tab[crt::kMaxMod][128];
+  for (int e = threadIdx.x; e < c.n * 128; e += blockDim.x) tab[e / 128][e % 128] = c.tab[e / 128][e % 128];
+  __syncthreads();
+  const int64_t M = eval_dim(p.M, p.rdev), N = eval_dim(p.N, p.rdev);
+  const int64_t total = M * N;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / N, j = idx % N;
+    if (p.lower && j > i) continue;
+    uint64_t acc[crt::kLimbs] = {0, 0, 0, 0, 0};
+    const uint8_t* r = p.R + i * p.Npad + j;
+    const size_t plane = (size_t)p.Mpad * (size_t)p.Npad;
+    for (int m = 0; m < c.n; ++m) {
+      const uint32_t t = tab[m][r[m * plane]];
+#pragma unroll
+      for (int l = 0; l < crt::kLimbs; ++l) acc[l] += (uint64_t)t * c.Mj[m][l];
+    }
+    uint32_t S[crt::kLimbs];
+    uint64_t carry = 0;
+#pragma unroll
+    for (int l = 0; l < crt::kLimbs; ++l) {
+      const uint64_t v = acc[l] + carry;
+      S[l] = (uint32_t)v;
+      carry = v >> 32;
+    }
+    // q = floor(S / P) in [0, n): estimate from the top bits, then correct
+    uint64_t stop = 0;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int pos = c.shift + 32 * b;  // 32-bit chunk of S >> shift
+      const int li = pos >> 5, off = pos & 31;
+      uint32_t w = 0;
+      if (li < crt::kLimbs) w = S[li] >> off;
+      if (off && li + 1 < crt::kLimbs) w |= S[li + 1] << (32 - off);
+      stop |= (uint64_t)w << (32 * b);
+    }
+    int qe = (int)floorf((float)stop * c.inv_ptop);
+    qe = qe < 0 ? 0 : qe;
+    // X = S - qe * P  (signed, two's complement over the limbs)
+    int64_t borrow = 0;
+    uint32_t X[crt::kLimbs];
+#pragma unroll
+    for (int l = 0; l < crt::kLimbs; ++l) {
+      const int64_t v = (int64_t)S[l] - (int64_t)((uint64_t)qe * c.P[l]) + borrow;
+      X[l] = (uint32_t)v;
+      borrow = v >> 32;  // arithmetic
+    }
+    // fix-up: bring X into [0, P)
+    for (int pass = 0; pass < 2; ++pass) {
+      if ((int32_t)X[crt::kLimbs - 1] < 0) {  // X < 0: X += P
+        uint64_t cc = 0;
+#pragma unroll
+        for (int l = 0; l < crt::kLimbs; ++l) {
+          const uint64_t v = (uint64_t)X[l] + c.P[l] + cc;
+          X[l] = (uint32_t)v;
+          cc = v >> 32;
+        }
+      } else {
+        // X >= P ?
+        bool ge = true;
+#pragma unroll
+        for (int l = crt::kLimbs - 1; l >= 0; --l) {
+          if (X[l] != c.P[l]) {
+            ge = X[l] > c.P[l];
+            break;
+          }
+        }
+        if (ge) {
+          int64_t bb = 0;
+#pragma unroll
+          for (int l = 0; l < crt::kLimbs; ++l) {
+            const int64_t v = (int64_t)X[l] - (int64_t)c.P[l] + bb;
+            X[l] = (uint32_t)v;
+            bb = v >> 32;
+          }
+        }
+      }
+    }
+    // centre: X > P/2 -> X - P (negative); magnitude and sign
+    bool gt = false;
+#pragma unroll
+    for (int l = crt::kLimbs - 1; l >= 0; --l) {
+      if (X[l] != c.halfP[l]) {
+        gt = X[l] > c.halfP[l];
+        break;
+      }
+    }
+    uint32_t mag[crt::kLimbs];
+    if (gt) {  // |X - P| = P - X
+      int64_t bb = 0;
+#pragma unroll
+      for (int l = 0; l < crt::kLimbs; ++l) {
+        const int64_t v = (int64_t)c.P[l] - (int64_t)X[l] + bb;
+        mag[l] = (uint32_t)v;
+        bb = v >> 32;
+      }
+    } else {
+#pragma unroll
+      for (int l = 0; l < crt::kLimbs; ++l) mag[l] = X[l];
+    }
+    const int scale = (p.EA[i] - 1022 - p.betaA) + (p.EB[j] - 1022 - p.betaB);
+    double v = compose_double(gt, mag, scale);
+    double* cp = p.C + i * p.ldc + j;
+    if (p.alpha != 1.0) v *= p.alpha;
+    if (p.beta != 0.0) v = fma(p.beta, *cp, v);
+    *cp = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap* map, const bf16* base, int64_t kpad, int64_t rows, int n_mod,
+              int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)rows, (cuuint64_t)n_mod};
+  cuuint64_t strides[2] = {(cuuint64_t)(kpad * sizeof(bf16)),
+                           (cuuint64_t)(kpad * rows * sizeof(bf16))};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(base), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BN, int STAGES>
+cudaError_t launch_mma(const CUtensorMap& ta, const CUtensorMap& tb, const MmaParams& mp,
+                       int64_t Mmax, int64_t Nmax, cudaStream_t s) {
+  const size_t smem = sizeof(MmaSmem<BN, STAGES>) + 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(crt_mma_kernel<BN, STAGES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int groups = (mp.n_mod + mp.mods_per_cta - 1) / mp.mods_per_cta;
+  dim3 grid((unsigned)((Nmax + BN - 1) / BN), (unsigned)((Mmax + BM - 1) / BM), (unsigned)groups);
+  crt_mma_kernel<BN, STAGES><<<grid, 192, smem, s>>>(ta, tb, mp);
+  return cudaGetLastError();
+}
+
+inline unsigned grid1d(int64_t total, int threads) {
+  int64_t g = (total + threads - 1) / threads;
+  if (g > 152 * 32) g = 152 * 32;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+// Moduli needed so that 2 K 2^(betaA + betaB) < prod p_j (one bit of margin).
+int crt_moduli_for(int64_t Kmax, int betaA, int betaB) {
+  const int bits = 1 + (int)std::ceil(std::log2((double)(Kmax > 1 ? Kmax : 2))) + betaA + betaB + 1;
+  return crt::moduli_for_bits(bits);
+}
+
+// Workspace needed by one exact product (see launch_crt_gemm).
+size_t crt_workspace_bytes(int64_t Mmax, int64_t Nmax, int64_t Kmax, int n_mod, bool same_operand) {
+  const int64_t kpad = round_up(Kmax > 0 ? Kmax : 1, BK);
+  const int64_t mpad = round_up(Mmax > 0 ? Mmax : 1, BM);
+  const int64_t npad = round_up(Nmax > 0 ? Nmax : 1, 256);
+  size_t b = 0;
+  auto add = [&](size_t x) { b = (b + 1023) / 1024 * 1024 + x; };
+  add(sizeof(bf16) * (size_t)n_mod * (size_t)mpad * (size_t)kpad);  // A slices
+  if (!same_operand) add(sizeof(bf16) * (size_t)n_mod * (size_t)npad * (size_t)kpad);
+  add((size_t)n_mod * (size_t)mpad * (size_t)npad);  // residues
+  add(sizeof(int32_t) * (size_t)(mpad + npad));      // exponents
+  return b + 1024;
+}
+
+cudaError_t launch_crt_gemm(const CrtGemm& g, cudaStream_t s, KernelTimer* timer) {
+  const GemmParams& p = g.p;
+  const int64_t Mmax = p.M.max, Nmax = p.N.max, Kmax = p.K.max;
+  if (Mmax <= 0 || Nmax <= 0) return cudaSuccess;
+  if (Kmax > 4096) return cudaErrorInvalidValue;  // exactness bound of the FP32 sums
+  const int n_mod = crt_moduli_for(Kmax, g.betaA, g.betaB);
+  if (n_mod < 0) return cudaErrorInvalidValue;
+  const int64_t kpad = round_up(Kmax > 0 ? Kmax : 1, BK);
+  const int64_t mpad = round_up(Mmax, BM);
+  const int BN = (Nmax >= 2048) ? 256 : 128;
+  const int64_t npad = round_up(Nmax, 256);
+  const bool same = g.same_operand;
+  // carve the workspace
+  char* w = (char*)g.ws;
+  size_t off = 0;
+  auto take = [&](size_t x) {
+    off = (off + 1023) / 1024 * 1024;
+    char* q = w + off;
+    off += x;
+    return q;
+  };
+  bf16* SA = (bf16*)take(sizeof(bf16) * (size_t)n_mod * (size_t)mpad * (size_t)kpad);
+  bf16* SB = same ? SA : (bf16*)take(sizeof(bf16) * (size_t)n_mod * (size_t)npad * (size_t)kpad);
+  uint8_t* R = (uint8_t*)take((size_t)n_mod * (size_t)mpad * (size_t)npad);
+  int32_t* EA = (int32_t*)take(sizeof(int32_t) * (size_t)(mpad + npad));
+  int32_t* EB = same ? EA : EA + mpad;
+  if (off > g.ws_bytes) return cudaErrorInvalidValue;
+
+  // ---- split the operands ----
+  const int betaA = g.betaA, betaB = g.betaB;
+  cudaError_t e = cudaMemsetAsync(EA, 0, sizeof(int32_t) * (size_t)(mpad + npad), s);
+  if (e != cudaSuccess) return e;
+  // op(A): rows x K; transA: element (i,k) at A[k*lda + i].  op(B) is K x N;
+  // its N x K view: element (j,k) = transB ? B[j*ldb + k] : B[k*ldb + j].
+  auto split = [&](const double* X, int64_t ld, int tview, Dim rows, int64_t rows_max, int beta,
+                   int32_t* E, bf16* S) -> cudaError_t {
+    cudaError_t err = timer->run(KT_SPLIT, s, [&] {
+      if (!tview)
+        row_expo_kernel<<<(unsigned)((rows_max * 32 + 255) / 256), 256, 0, s>>>(X, ld, 0, rows,
+                                                                               p.K, p.rdev, E, g.st);
+      else
+        row_expo_kernel<<<dim3((unsigned)(rows_max / 32), 16), 256, 0, s>>>(X, ld, 1, rows, p.K,
+                                                                           p.rdev, E, g.st);
+      return cudaGetLastError();
+    });
+    if (err != cudaSuccess) return err;
+    dim3 grid((unsigned)(kpad / 32), (unsigned)(rows_max / 32));
+    return timer->run(KT_SPLIT, s, [&] {
+      split_kernel<<<grid, 256, 0, s>>>(X, ld, tview, rows, p.K, rows_max, kpad, p.rdev, E, n_mod,
+                                        beta, S);
+      return cudaGetLastError();
+    });
+  };
+  e = split(p.A, p.lda, g.transA ? 1 : 0, p.M, mpad, betaA, EA, SA);
+  if (e != cudaSuccess) return e;
+  if (!same) {
+    e = split(p.B, p.ldb, g.transB ? 0 : 1, p.N, npad, betaB, EB, SB);
+    if (e != cudaSuccess) return e;
+  }
+
+  // ---- tensor-core products, one per modulus ----
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, SA, kpad, mpad, n_mod, BM)) return cudaErrorInvalidValue;
+  if (!make_map(&tb, SB, kpad, same ? mpad : npad, n_mod, BN)) return cudaErrorInvalidValue;
+  MmaParams mp;
+  mp.M = p.M;
+  mp.N = p.N;
+  mp.rdev = p.rdev;
+  mp.nk = (int)(kpad / BK);
+  mp.n_mod = n_mod;
+  mp.lower = p.lower;
+  mp.R = R;
+  mp.Mpad = mpad;
+  mp.Npad = npad;
+  mp.status = &g.st->status;
+  // moduli per CTA: enough CTAs to fill the GPU about twice
+  const int64_t tiles = ((Mmax + BM - 1) / BM) * ((Nmax + BN - 1) / BN) / (p.lower ? 2 : 1);
+  int mpc = n_mod;
+  while (mpc > 1 && tiles * ((n_mod + mpc - 1) / mpc) < 2 * 152) mpc = (mpc + 1) / 2;
+  mp.mods_per_cta = mpc;
+  KernelTimer mt = *timer;
+  mt.gemm = &g.p;
+  mt.flops_mult = (double)n_mod;
+  e = mt.run(KT_MMA, s, [&] {
+    return BN == 256 ? launch_mma<256, 4>(ta, tb, mp, Mmax, Nmax, s)
+                     : launch_mma<128, 6>(ta, tb, mp, Mmax, Nmax, s);
+  });
+  if (e != cudaSuccess) return e;
+
+  // ---- reconstruction ----
+  static crt::Consts consts[crt::kMaxMod + 1];
+  static bool have[crt::kMaxMod + 1] = {false};
+  static std::mutex mu;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!have[n_mod]) {
+      crt::make_consts(n_mod, &consts[n_mod]);
+      have[n_mod] = true;
+    }
+  }
+  ReconParams rp;
+  rp.R = R;
+  rp.Mpad = mpad;
+  rp.Npad = npad;
+  rp.M = p.M;
+  rp.N = p.N;
+  rp.rdev = p.rdev;
+  rp.EA = EA;
+  rp.EB = EB;
+  rp.betaA = betaA;
+  rp.betaB = same ? betaA : betaB;
+  rp.alpha = p.alpha;
+  rp.beta = p.beta;
+  rp.C = p.C;
+  rp.ldc = p.ldc;
+  rp.lower = p.lower;
+  rp.pad = 0;
+  return timer->run(KT_RECON, s, [&] {
+    reconstruct_kernel<<<grid1d(Mmax * Nmax, 256), 256, 0, s>>>(rp, consts[n_mod]);
+    return cudaGetLastError();
+  });
+}
+
+}  // namespace cpinv

@@ -8,6 +8,53 @@
 
 namespace cpinv {
 
+// ---------------------------------------------------------------------------
+// Kernel classes for tracing, and the hook every launcher goes through
+// (implemented in capi.cu).
+// ---------------------------------------------------------------------------
+enum : int {
+  KT_GEMM_FP64 = 0,  // dgemm_kernel
+  KT_MMA = 1,        // crt_mma_kernel (tcgen05)
+  KT_DIAG = 2,       // diag_factor_kernel
+  KT_AUX = 3,        // small O(n^2) kernels
+  KT_SPLIT = 4,      // residue split of the operands
+  KT_RECON = 5,      // CRT reconstruction
+  KT_COUNT = 6
+};
+
+void trace_count();
+bool trace_on();
+int trace_begin(cudaStream_t s);
+void trace_end(int rec, cudaStream_t s, int kind, const GemmParams* g, double flops_mult);
+
+struct KernelTimer {
+  const GemmParams* gemm = nullptr;  // flops of the MMA launches come from its dims
+  double flops_mult = 1.0;           // e.g. the number of moduli
+  template <class F>
+  cudaError_t run(int kind, cudaStream_t s, F&& f) {
+    trace_count();
+    if (!trace_on()) return f();
+    const int rec = trace_begin(s);
+    cudaError_t e = f();
+    trace_end(rec, s, kind, kind == KT_MMA || kind == KT_GEMM_FP64 ? gemm : nullptr, flops_mult);
+    return e;
+  }
+};
+
+// One FP64-accurate product in the residue (exact-slice) arithmetic.
+struct CrtGemm {
+  GemmParams p;       // C = alpha op(A) op(B) + beta C  (dims may depend on the device rank)
+  bool transA, transB;
+  bool same_operand;  // op(B) is op(A)' (symmetric products): split once
+  int betaA, betaB;   // integer bits of the scaled operands (<= 62)
+  void* ws;           // scratch, crt_workspace_bytes() bytes, 1024-aligned
+  size_t ws_bytes;
+  DevState* st;
+};
+size_t crt_workspace_bytes(int64_t Mmax, int64_t Nmax, int64_t Kmax, int n_mod, bool same_operand);
+cudaError_t launch_crt_gemm(const CrtGemm& g, cudaStream_t s, KernelTimer* timer);
+int crt_moduli_for(int64_t Kmax, int betaA, int betaB);
+
 // gemm_fp64.cu
 cudaError_t launch_dgemm(const GemmParams& p, bool transA, bool transB, cudaStream_t s);
 

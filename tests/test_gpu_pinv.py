@@ -9,7 +9,7 @@ from gpu_util import TOL, dev, penrose_normwise, rel, to_dev
 
 pytestmark = pytest.mark.gpu
 
-MODES = ["fp64"]
+MODES = ["fp64", "exact"]
 
 
 @pytest.fixture(scope="module")
