@@ -120,7 +120,8 @@ int cpinv_rank(const double* G, int64_t m, int64_t n, int64_t ldg,
 /* ---------------------------------------------------------------------------
  * The dense contraction of the library on its own:
  *   C = alpha op(A) op(B) + beta C,   op(X) = X or X' (transX != 0),
- * op(A) M x K, op(B) K x N, C M x N, all row-major FP64 device matrices.
+ * op(A) M x K, op(B) K x N, C M x N, all row-major FP64 device matrices;
+ * C must not overlap A or B.
  * This is the product the pipeline uses for G'G, L'L, the inverse and the
  * chain (Theorem 1); exposed for callers who want the same arithmetic.
  *   mode CPINV_MODE_FP64: FP64 fused multiply-adds.

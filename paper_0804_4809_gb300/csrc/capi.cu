@@ -16,6 +16,8 @@
 // possible r and reads r from device memory.
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
+#include <mutex>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -146,21 +148,41 @@ struct Plan {
   size_t crt_bytes;
 };
 
-// Where a product sits in the pipeline decides its arithmetic in exact-slice
-// mode: the Gram matrix is formed from 62-bit integers (an exactly summed,
-// once-rounded G'G), the other large products from 53-bit integers (FP64
-// accuracy); the Cholesky panel operations stay on the FP64 pipe.
-enum Site { S_FP64 = 0, S_GRAM = 1, S_PROD = 2 };
+// Where a product sits in the pipeline decides its arithmetic:
+//  exact-slice mode: the Gram matrix from 62-bit integers (an exactly summed,
+//    once-rounded G'G), the other large products from 53-bit integers (FP64
+//    accuracy);
+//  split mode: the Gram matrix and the chain (L M, X X', K G', the
+//    least-squares products) in BF16x3 split precision, the products feeding
+//    (L'L)^-1 as in exact-slice mode;
+//  the pivot tests, square roots and diagonal blocks are FP64 in every mode.
+enum Site { S_FP64 = 0, S_GRAM = 1, S_PROD = 2, S_CHAIN = 3 };
+enum ProdKind { PK_FP64 = 0, PK_EXACT = 1, PK_SPLIT = 2 };
 
 constexpr int64_t kCrtMaxK = 4096;  // exactness bound of one residue product
 
+// Small products stay on the FP64 pipe: below 2MNK = 2^27 the residue split,
+// tensor-core pass and reconstruction do not repay themselves.  The Gram
+// matrix always takes the tensor-core form (its rounding is what the method
+// amplifies).
+int prod_kind(const Plan& p, Site site, int64_t Mmax, int64_t Nmax, int64_t Kmax) {
+  if (p.mode == CPINV_MODE_FP64 || site == S_FP64) return PK_FP64;
+  if (Mmax <= 0 || Nmax <= 0 || Kmax <= 0) return PK_FP64;
+  const bool big = 2.0 * (double)Mmax * (double)Nmax * (double)Kmax >= (double)(1 << 27) &&
+                   Kmax >= 128;
+  if (site != S_GRAM && !big) return PK_FP64;
+  if (p.mode == CPINV_MODE_SPLIT_BF16X3 && (site == S_GRAM || site == S_CHAIN)) return PK_SPLIT;
+  return PK_EXACT;
+}
+
 bool use_exact(const Plan& p, Site site, int64_t Mmax, int64_t Nmax, int64_t Kmax) {
-  if (p.mode != CPINV_MODE_EXACT_SLICE || site == S_FP64) return false;
-  return Kmax >= 64 && Mmax >= 16 && Nmax >= 1;
+  return prod_kind(p, site, Mmax, Nmax, Kmax) == PK_EXACT;
 }
 
 size_t crt_need(const Plan& p, Site site, int64_t M, int64_t N, int64_t K, bool same) {
-  if (!use_exact(p, site, M, N, K)) return 0;
+  const int pk = prod_kind(p, site, M, N, K);
+  if (pk == PK_SPLIT) return split_workspace_bytes(M, N, K, same);
+  if (pk != PK_EXACT) return 0;
   const int beta = site == S_GRAM ? 62 : 53;
   const int64_t Kc = K < kCrtMaxK ? K : kCrtMaxK;
   const int nm = crt_moduli_for(Kc, beta, beta);
@@ -168,17 +190,53 @@ size_t crt_need(const Plan& p, Site site, int64_t M, int64_t N, int64_t K, bool 
   return crt_workspace_bytes(M, N, Kc, nm, same);
 }
 
+// Exact left-looking Cholesky (panel width <= 32, order <= 4096): residue
+// planes of the factor RL[j][row][col], the update residues and row scales.
+constexpr int kCholBits = 60;
+
+struct CholLayout {
+  int n_mod;
+  int64_t rows, kpad;  // RL planes: rows x kpad per modulus
+  size_t rl_bytes, r_bytes, e_bytes;
+};
+
+bool chol_exact_ok(const Plan& p) {
+  return (p.mode == CPINV_MODE_EXACT_SLICE || p.mode == CPINV_MODE_SPLIT_BF16X3) && p.b <= 32 &&
+         p.nA <= 4096 && p.nA > p.b;
+}
+
+CholLayout chol_layout(const Plan& p) {
+  CholLayout L{};
+  const int64_t bm = crt_block_m(), bk = crt_block_k();
+  L.n_mod = crt_moduli_for(p.nA, kCholBits, kCholBits);
+  L.rows = (p.nA + bm - 1) / bm * bm;
+  L.kpad = (p.nA + bk - 1) / bk * bk;
+  L.rl_bytes = 2 * (size_t)L.n_mod * (size_t)L.rows * (size_t)L.kpad;
+  L.r_bytes = (size_t)L.n_mod * (size_t)L.rows * 256;
+  L.e_bytes = sizeof(int32_t) * (size_t)L.rows;
+  return L;
+}
+
+size_t chol_need(const Plan& p) {
+  if (!chol_exact_ok(p)) return 0;
+  const CholLayout L = chol_layout(p);
+  return L.rl_bytes + L.r_bytes + L.e_bytes + 3 * 1024;
+}
+
 size_t crt_plan_bytes(const Plan& p, Job job) {
   const int64_t nA = p.nA, m = p.m, n = p.n;
   size_t need = crt_need(p, S_GRAM, nA, nA, p.trans ? n : m, true);
+  need = chol_need(p) > need ? chol_need(p) : need;
   if (job == JOB_RANK) return need;
   auto mx = [&](size_t v) { need = v > need ? v : need; };
-  mx(crt_need(p, S_PROD, nA, nA, nA, true));    // L'L, W'W, X X'
-  mx(crt_need(p, S_PROD, nA, nA, nA, false));   // L M, inverse blocks
-  if (job == JOB_PINV) mx(crt_need(p, S_PROD, n, m, nA, false));  // G+ = K G' or G' K
+  mx(crt_need(p, S_PROD, nA, nA, nA, true));    // L'L, W'W
+  mx(crt_need(p, S_PROD, nA, nA, nA, false));   // inverse blocks
+  mx(crt_need(p, S_CHAIN, nA, nA, nA, true));   // X X'
+  mx(crt_need(p, S_CHAIN, nA, nA, nA, false));  // L M
+  if (job == JOB_PINV) mx(crt_need(p, S_CHAIN, n, m, nA, false));  // G+ = K G' or G' K
   if (job == JOB_LSTSQ) {
-    mx(crt_need(p, S_PROD, n, p.k, m, false));   // G'F (or G't)
-    mx(crt_need(p, S_PROD, nA, p.k, nA, false)); // L'c, M c, L c
+    mx(crt_need(p, S_CHAIN, n, p.k, m, false));   // G'F (or G't)
+    mx(crt_need(p, S_CHAIN, nA, p.k, nA, false)); // L'c, M c, L c
   }
   return need;
 }
@@ -221,7 +279,9 @@ bool make_plan(Plan& p, int64_t m, int64_t n, int64_t k, const cpinv_opts* o) {
   p.rel_tol = o->rel_tol;
   if (p.b < 1 || p.b > 64) return false;
   if (!(p.rel_tol >= 0.0) || !std::isfinite(p.rel_tol)) return false;
-  if (o->mode != CPINV_MODE_FP64 && o->mode != CPINV_MODE_EXACT_SLICE) return false;
+  if (o->mode != CPINV_MODE_FP64 && o->mode != CPINV_MODE_EXACT_SLICE &&
+      o->mode != CPINV_MODE_SPLIT_BF16X3)
+    return false;
   return true;
 }
 
@@ -288,14 +348,28 @@ cudaError_t matmul(const Ctx& c, Site site, const double* A, int64_t lda, bool t
   g.beta = beta;
   g.rdev = c.rdev();
   g.lower = lower;
-  g.pad = 0;
+  g.pad = (C == A || C == B) ? 1 : 0;
   const Plan& p = *c.p;
-  if (!use_exact(p, site, M.max, N.max, K.max)) {
+  const int pk = prod_kind(p, site, M.max, N.max, K.max);
+  if (pk == PK_FP64) {
     KernelTimer t;
     t.gemm = &g;
     return t.run(KT_GEMM_FP64, c.s, [&] { return launch_dgemm(g, ta, tb, c.s); });
   }
   const bool same = A == B && lda == ldb && ta != tb;
+  if (pk == PK_SPLIT) {
+    CrtGemm sg;
+    sg.p = g;
+    sg.transA = ta;
+    sg.transB = tb;
+    sg.same_operand = same;
+    sg.betaA = sg.betaB = 0;
+    sg.ws = p.crt;
+    sg.ws_bytes = p.crt_bytes;
+    sg.st = p.st;
+    KernelTimer t;
+    return launch_split_gemm(sg, c.s, &t);
+  }
   return crt_product(g, ta, tb, site == S_GRAM ? 62 : 53, same, p.crt, p.crt_bytes, p.st, c.s);
 }
 
@@ -334,6 +408,56 @@ int factor(const Ctx& c, double* a, int64_t lda, int spd) {
   return CPINV_OK;
 }
 
+// Exact-slice left-looking variant of factor() (see chol_exact.cu).
+int factor_exact(const Ctx& c, double* a, int64_t lda, int spd) {
+  const Plan& p = *c.p;
+  const int64_t nA = p.nA;
+  const int b = p.b;
+  const CholLayout Ly = chol_layout(p);
+  char* base = (char*)p.crt;
+  size_t off = 0;
+  auto take = [&](size_t x) {
+    off = (off + 1023) / 1024 * 1024;
+    char* q = base + off;
+    off += x;
+    return q;
+  };
+  void* RL = take(Ly.rl_bytes);
+  uint8_t* R = (uint8_t*)take(Ly.r_bytes);
+  int32_t* E = (int32_t*)take(Ly.e_bytes);
+  if (off > p.crt_bytes) return CPINV_ERR_WORKSPACE;
+  const Dim nd = spd ? rdim(0, nA) : hdim(nA);
+  KernelTimer t;
+  CK(t.run(KT_AUX, c.s, [&] { return launch_rowscale(a, lda, nd, c.rdev(), Ly.rows, E, c.s); }));
+  CK(cudaMemsetAsync(RL, 0, Ly.rl_bytes, c.s));
+  for (int64_t k0 = 0, blk = 0; k0 < nA; k0 += b, ++blk) {
+    if (k0 > 0) {
+      // A(k0:n, P) -= L(k0:n, 0:k0) L(P, 0:k0)'   exactly, from the residue planes
+      const Dim M = spd ? rdim(-k0, nA - k0) : hdim(nA - k0);
+      const Dim N = spd ? rdim(-k0, b) : hdim(nA - k0 < b ? nA - k0 : b);
+      GemmParams fl;
+      std::memset(&fl, 0, sizeof(fl));
+      fl.M = M;
+      fl.N = N;
+      fl.K = spd ? rdim(0, k0) : hdim(k0);
+      fl.rdev = c.rdev();
+      CK(crt_mma(RL, Ly.rows, (int)k0, RL, Ly.rows, (int)k0, Ly.kpad, k0, Ly.n_mod, M, N, c.rdev(),
+                 0, R, Ly.rows, 256, &p.st->status, c.s, &t, &fl));
+      CK(crt_reconstruct(R, Ly.rows, 256, M, N, c.rdev(), E + k0, E + k0, kCholBits, kCholBits,
+                         -1.0, 1.0, a + k0 * lda + k0, lda, 1, Ly.n_mod, c.s, &t));
+    }
+    CK(t.run(KT_DIAG, c.s, [&] {
+      return launch_diag_factor(a, lda, nd, k0, b, p.st, c.rdev(), spd ? nullptr : p.acc, p.Z,
+                                spd ? p.Tinv + blk * b * b : nullptr, spd, c.s);
+    }));
+    CK(t.run(KT_AUX, c.s, [&] {
+      return launch_panel_solve_split(a, lda, nd, c.rdev(), k0, b, p.Z, E, Ly.n_mod, kCholBits,
+                                      RL, Ly.rows, Ly.kpad, c.s);
+    }));
+  }
+  return CPINV_OK;
+}
+
 // Gram, tolerance, full-rank Cholesky, compaction.  Leaves L in bufL (JOB_PINV
 // / JOB_LSTSQ) and r in st->rank.
 int front_rank(const Ctx& c, const double* G, int64_t ldg, bool compact) {
@@ -347,7 +471,7 @@ int front_rank(const Ctx& c, const double* G, int64_t ldg, bool compact) {
               1.0, 0.0, 1));
   CK(KernelTimer().run(KT_AUX, c.s,
                        [&] { return launch_tol(p.bufA, nA, nA, p.rel_tol, p.st, c.s); }));
-  int rc = factor(c, p.bufA, nA, 0);
+  int rc = chol_exact_ok(p) ? factor_exact(c, p.bufA, nA, 0) : factor(c, p.bufA, nA, 0);
   if (rc) return rc;
   CK(KernelTimer().run(KT_AUX, c.s,
                        [&] { return launch_scan(p.acc, nA, p.colidx, p.st, c.s); }));
@@ -388,7 +512,7 @@ int front_inverse(const Ctx& c) {
   // N = L'L (lower), into bufA
   CK(matmul(c, S_PROD, p.bufL, nA, true, p.bufL, nA, false, p.bufA, nA, R, R, hdim(nA), 1.0, 0.0,
             1));
-  int rc = factor(c, p.bufA, nA, 1);
+  int rc = chol_exact_ok(p) ? factor_exact(c, p.bufA, nA, 1) : factor(c, p.bufA, nA, 1);
   if (rc) return rc;
   // W = U^-1: diagonal blocks from the factorisation, the rest by recursion
   CK(KernelTimer().run(KT_AUX, c.s, [&] {
@@ -400,6 +524,147 @@ int front_inverse(const Ctx& c) {
   CK(matmul(c, S_PROD, p.bufW, nA, true, p.bufW, nA, false, p.bufM, nA, R, R, R, 1.0, 0.0, 0));
   return CPINV_OK;
 }
+
+// ---------------------------------------------------------------------------
+// CUDA-graph replay of repeated calls.  Every launch of a call has a shape
+// known on the host (the rank stays on the device), so a call is a fixed
+// sequence of kernels for fixed arguments.  The first call with a given
+// argument set runs directly; the second is captured on a library stream and
+// instantiated; later ones replay the graph with one launch.  Off when
+// tracing is on or CPINV_GRAPHS=0.
+// ---------------------------------------------------------------------------
+struct GraphKey {
+  int32_t job, device, mode, panel;
+  int64_t m, n, k, ld1, ld2, ld3;
+  const void* p1;
+  const void* p2;
+  const void* p3;
+  void* ws;
+  size_t ws_bytes;
+  double rel_tol;
+};
+
+struct GraphEntry {
+  GraphKey key;
+  int seen;
+  int64_t launches;  // kernels in the captured sequence
+  cudaGraphExec_t exec;
+  uint64_t stamp;
+};
+
+struct GraphCache {
+  std::mutex mu;
+  std::vector<GraphEntry> entries;
+  std::vector<std::pair<int, cudaStream_t>> side;
+  uint64_t clock = 0;
+};
+GraphCache g_graphs;
+constexpr size_t kMaxGraphs = 16;
+
+thread_local int t_no_graph = 0;
+
+bool graphs_enabled() {
+  if (t_no_graph) return false;
+  static int on = -1;
+  if (on < 0) {
+    const char* e = std::getenv("CPINV_GRAPHS");
+    on = (e && e[0] == '0') ? 0 : 1;
+  }
+  return on == 1 && !g_tr.on;
+}
+
+GraphKey make_key(int job, const Plan& p, int64_t ld1, int64_t ld2, int64_t ld3, const void* p1,
+                  const void* p2, const void* p3, void* ws, size_t ws_bytes) {
+  GraphKey k;
+  std::memset(&k, 0, sizeof(k));
+  k.job = job;
+  cudaGetDevice(&k.device);
+  k.mode = p.mode;
+  k.panel = p.b;
+  k.m = p.m;
+  k.n = p.n;
+  k.k = p.k;
+  k.ld1 = ld1;
+  k.ld2 = ld2;
+  k.ld3 = ld3;
+  k.p1 = p1;
+  k.p2 = p2;
+  k.p3 = p3;
+  k.ws = ws;
+  k.ws_bytes = ws_bytes;
+  k.rel_tol = p.rel_tol;
+  return k;
+}
+
+// Runs body(ctx) on `user` directly, or captured / replayed as a graph.
+template <class Body>
+int run_pipeline(const Plan& p, cudaStream_t user, const GraphKey& key, Body&& body) {
+  auto direct = [&]() -> int {
+    Ctx c{user, &p};
+    CK(cudaMemsetAsync(p.st, 0, sizeof(DevState), user));
+    return body(c);
+  };
+  if (!graphs_enabled()) return direct();
+  std::lock_guard<std::mutex> lock(g_graphs.mu);
+  GraphEntry* e = nullptr;
+  for (auto& x : g_graphs.entries)
+    if (std::memcmp(&x.key, &key, sizeof(key)) == 0) e = &x;
+  if (!e) {
+    if (g_graphs.entries.size() >= kMaxGraphs) {
+      size_t old = 0;
+      for (size_t i = 1; i < g_graphs.entries.size(); ++i)
+        if (g_graphs.entries[i].stamp < g_graphs.entries[old].stamp) old = i;
+      if (g_graphs.entries[old].exec) cudaGraphExecDestroy(g_graphs.entries[old].exec);
+      g_graphs.entries.erase(g_graphs.entries.begin() + (long)old);
+    }
+    GraphEntry ne;
+    ne.key = key;
+    ne.seen = 1;
+    ne.launches = 0;
+    ne.exec = nullptr;
+    ne.stamp = ++g_graphs.clock;
+    g_graphs.entries.push_back(ne);
+    return direct();
+  }
+  e->stamp = ++g_graphs.clock;
+  if (!e->exec) {
+    cudaStream_t side = nullptr;
+    for (auto& sd : g_graphs.side)
+      if (sd.first == key.device) side = sd.second;
+    if (!side) {
+      CK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+      g_graphs.side.push_back({key.device, side});
+    }
+    const int64_t l0 = g_launches.load();
+    CK(cudaStreamBeginCapture(side, cudaStreamCaptureModeThreadLocal));
+    Ctx c{side, &p};
+    int rc = cudaMemsetAsync(p.st, 0, sizeof(DevState), side) == cudaSuccess ? body(c)
+                                                                               : CPINV_ERR_CUDA;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(side, &graph);
+    if (rc != CPINV_OK || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc != CPINV_OK ? rc : CPINV_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return CPINV_ERR_CUDA;
+    e->exec = exec;
+    e->launches = g_launches.load() - l0;
+    g_launches.fetch_sub(e->launches);  // counted again below, at launch
+  }
+  CK(cudaGraphLaunch(e->exec, user));
+  g_launches.fetch_add(e->launches);
+  return CPINV_OK;
+}
+
+}  // namespace
+
+NoGraphScope::NoGraphScope() { ++t_no_graph; }
+NoGraphScope::~NoGraphScope() { --t_no_graph; }
+
+namespace {
 
 int finish(const Ctx& c, int64_t* rank_out) {
   CK(trace_resolve(c.s, c.rdev()));
@@ -477,7 +742,6 @@ static int check_opts(const cpinv_opts* o) {
   if (o->mode != CPINV_MODE_FP64 && o->mode != CPINV_MODE_EXACT_SLICE &&
       o->mode != CPINV_MODE_SPLIT_BF16X3)
     return CPINV_ERR_INVALID_ARG;
-  if (o->mode == CPINV_MODE_SPLIT_BF16X3) return CPINV_ERR_UNSUPPORTED;
   if (o->panel < 0 || o->panel > 64 || o->reserved != 0) return CPINV_ERR_INVALID_ARG;
   if (!(o->rel_tol >= 0.0) || !std::isfinite(o->rel_tol)) return CPINV_ERR_INVALID_ARG;
   return CPINV_OK;
@@ -497,13 +761,18 @@ int cpinv_rank(const double* G, int64_t m, int64_t n, int64_t ldg, uint8_t* acce
   Plan p{};
   if (!make_plan(p, m, n, 0, o)) return CPINV_ERR_INVALID_ARG;
   if (int rc = begin(p, JOB_RANK, workspace, workspace_bytes)) return rc;
-  Ctx c{(cudaStream_t)stream, &p};
-  CK(cudaMemsetAsync(p.st, 0, sizeof(DevState), c.s));
-  if (int rc = front_rank(c, G, ldg, false)) return rc;
-  if (accepted_out)
-    CK(KernelTimer().run(KT_AUX, c.s,
-                         [&] { return launch_copy_mask(p.acc, accepted_out, p.nA, c.s); }));
-  return finish(c, rank_out);
+  cudaStream_t us = (cudaStream_t)stream;
+  const GraphKey key = make_key(JOB_RANK, p, ldg, 0, 0, G, accepted_out, nullptr, workspace,
+                                workspace_bytes);
+  int rc = run_pipeline(p, us, key, [&](const Ctx& c) -> int {
+    if (int r = front_rank(c, G, ldg, false)) return r;
+    if (accepted_out)
+      CK(KernelTimer().run(KT_AUX, c.s,
+                           [&] { return launch_copy_mask(p.acc, accepted_out, p.nA, c.s); }));
+    return CPINV_OK;
+  });
+  if (rc) return rc;
+  return finish(Ctx{us, &p}, rank_out);
 }
 
 int cpinv_pinv(const double* G, int64_t m, int64_t n, int64_t ldg, double* Gp, int64_t ldgp,
@@ -520,24 +789,29 @@ int cpinv_pinv(const double* G, int64_t m, int64_t n, int64_t ldg, double* Gp, i
   Plan p{};
   if (!make_plan(p, m, n, 0, o)) return CPINV_ERR_INVALID_ARG;
   if (int rc = begin(p, JOB_PINV, workspace, workspace_bytes)) return rc;
-  Ctx c{(cudaStream_t)stream, &p};
-  CK(cudaMemsetAsync(p.st, 0, sizeof(DevState), c.s));
-  if (int rc = front_rank(c, G, ldg, true)) return rc;
-  if (int rc = front_inverse(c)) return rc;
-  const int64_t nA = p.nA;
-  const Dim R = rdim(0, nA);
-  // X = L M  (bufW),  K = X X'  (bufA)
-  CK(matmul(c, S_PROD, p.bufL, nA, false, p.bufM, nA, false, p.bufW, nA, hdim(nA), R, R, 1.0, 0.0,
-            0));
-  CK(matmul(c, S_PROD, p.bufW, nA, false, p.bufW, nA, true, p.bufA, nA, hdim(nA), hdim(nA), R,
-            1.0, 0.0, 0));
-  if (!p.trans)  // G+ = K G'   (n x n)(n x m)
-    CK(matmul(c, S_PROD, p.bufA, nA, false, G, ldg, true, Gp, ldgp, hdim(n), hdim(m), hdim(n), 1.0,
+  cudaStream_t us = (cudaStream_t)stream;
+  const GraphKey key = make_key(JOB_PINV, p, ldg, ldgp, 0, G, Gp, nullptr, workspace,
+                                workspace_bytes);
+  int rc = run_pipeline(p, us, key, [&](const Ctx& c) -> int {
+    if (int r = front_rank(c, G, ldg, true)) return r;
+    if (int r = front_inverse(c)) return r;
+    const int64_t nA = p.nA;
+    const Dim R = rdim(0, nA);
+    // X = L M  (bufW),  K = X X'  (bufA)
+    CK(matmul(c, S_CHAIN, p.bufL, nA, false, p.bufM, nA, false, p.bufW, nA, hdim(nA), R, R, 1.0,
               0.0, 0));
-  else  // G+ = G' K   (n x m)(m x m)
-    CK(matmul(c, S_PROD, G, ldg, true, p.bufA, nA, false, Gp, ldgp, hdim(n), hdim(m), hdim(m), 1.0,
-              0.0, 0));
-  return finish(c, rank_out);
+    CK(matmul(c, S_CHAIN, p.bufW, nA, false, p.bufW, nA, true, p.bufA, nA, hdim(nA), hdim(nA), R,
+              1.0, 0.0, 0));
+    if (!p.trans)  // G+ = K G'   (n x n)(n x m)
+      CK(matmul(c, S_CHAIN, p.bufA, nA, false, G, ldg, true, Gp, ldgp, hdim(n), hdim(m), hdim(n),
+                1.0, 0.0, 0));
+    else  // G+ = G' K   (n x m)(m x m)
+      CK(matmul(c, S_CHAIN, G, ldg, true, p.bufA, nA, false, Gp, ldgp, hdim(n), hdim(m), hdim(m),
+                1.0, 0.0, 0));
+    return CPINV_OK;
+  });
+  if (rc) return rc;
+  return finish(Ctx{us, &p}, rank_out);
 }
 
 int cpinv_lstsq(const double* G, int64_t m, int64_t n, int64_t ldg, const double* F, int64_t k,
@@ -564,42 +838,48 @@ int cpinv_lstsq(const double* G, int64_t m, int64_t n, int64_t ldg, const double
   Plan p{};
   if (!make_plan(p, m, n, k, o)) return CPINV_ERR_INVALID_ARG;
   if (int rc = begin(p, JOB_LSTSQ, workspace, workspace_bytes)) return rc;
-  Ctx c{(cudaStream_t)stream, &p};
-  CK(cudaMemsetAsync(p.st, 0, sizeof(DevState), c.s));
-  if (int rc = front_rank(c, G, ldg, true)) return rc;
-  if (int rc = front_inverse(c)) return rc;
-  const int64_t nA = p.nA;
-  const Dim R = rdim(0, nA);
-  if (!p.trans) {
-    // c1 <- G'F (n x k);  c2 <- L' c1 (r x k)
-    CK(matmul(c, S_PROD, G, ldg, true, F, ldf, false, p.c1, k, hdim(n), hdim(k), hdim(m), 1.0,
-              0.0, 0));
-    CK(matmul(c, S_PROD, p.bufL, nA, true, p.c1, k, false, p.c2, k, R, hdim(k), hdim(nA), 1.0, 0.0,
-              0));
-  } else {
-    // c2 <- L' F (r x k)
-    CK(matmul(c, S_PROD, p.bufL, nA, true, F, ldf, false, p.c2, k, R, hdim(k), hdim(nA), 1.0, 0.0,
-              0));
-  }
-  CK(matmul(c, S_PROD, p.bufM, nA, false, p.c2, k, false, p.c3, k, R, hdim(k), R, 1.0, 0.0, 0));
-  CK(matmul(c, S_PROD, p.bufM, nA, false, p.c3, k, false, p.c2, k, R, hdim(k), R, 1.0, 0.0, 0));
-  if (!p.trans) {
-    CK(matmul(c, S_PROD, p.bufL, nA, false, p.c2, k, false, W, ldw, hdim(n), hdim(k), R, 1.0, 0.0,
-              0));
-  } else {
-    // t = L c (m x k) into c1, W = G' t
-    CK(matmul(c, S_PROD, p.bufL, nA, false, p.c2, k, false, p.c1, k, hdim(m), hdim(k), R, 1.0,
-              0.0, 0));
-    CK(matmul(c, S_PROD, G, ldg, true, p.c1, k, false, W, ldw, hdim(n), hdim(k), hdim(m), 1.0, 0.0,
-              0));
-  }
-  return finish(c, rank_out);
+  cudaStream_t us = (cudaStream_t)stream;
+  const GraphKey key = make_key(JOB_LSTSQ, p, ldg, ldf, ldw, G, F, W, workspace,
+                                workspace_bytes);
+  int rc = run_pipeline(p, us, key, [&](const Ctx& c) -> int {
+    if (int r = front_rank(c, G, ldg, true)) return r;
+    if (int r = front_inverse(c)) return r;
+    const int64_t nA = p.nA;
+    const Dim R = rdim(0, nA);
+    if (!p.trans) {
+      // c1 <- G'F (n x k);  c2 <- L' c1 (r x k)
+      CK(matmul(c, S_CHAIN, G, ldg, true, F, ldf, false, p.c1, k, hdim(n), hdim(k), hdim(m), 1.0,
+                0.0, 0));
+      CK(matmul(c, S_CHAIN, p.bufL, nA, true, p.c1, k, false, p.c2, k, R, hdim(k), hdim(nA), 1.0, 0.0,
+                0));
+    } else {
+      // c2 <- L' F (r x k)
+      CK(matmul(c, S_CHAIN, p.bufL, nA, true, F, ldf, false, p.c2, k, R, hdim(k), hdim(nA), 1.0, 0.0,
+                0));
+    }
+    CK(matmul(c, S_CHAIN, p.bufM, nA, false, p.c2, k, false, p.c3, k, R, hdim(k), R, 1.0, 0.0, 0));
+    CK(matmul(c, S_CHAIN, p.bufM, nA, false, p.c3, k, false, p.c2, k, R, hdim(k), R, 1.0, 0.0, 0));
+    if (!p.trans) {
+      CK(matmul(c, S_CHAIN, p.bufL, nA, false, p.c2, k, false, W, ldw, hdim(n), hdim(k), R, 1.0, 0.0,
+                0));
+    } else {
+      // t = L c (m x k) into c1, W = G' t
+      CK(matmul(c, S_CHAIN, p.bufL, nA, false, p.c2, k, false, p.c1, k, hdim(m), hdim(k), R, 1.0,
+                0.0, 0));
+      CK(matmul(c, S_CHAIN, G, ldg, true, p.c1, k, false, W, ldw, hdim(n), hdim(k), hdim(m), 1.0, 0.0,
+                0));
+    }
+    return CPINV_OK;
+  });
+  if (rc) return rc;
+  return finish(Ctx{us, &p}, rank_out);
 }
 
 size_t cpinv_matmul_workspace_size(int64_t M, int64_t N, int64_t K, int32_t mode, int32_t bits,
                                    int32_t symmetric) {
   if (M < 0 || N < 0 || K < 0) return 0;
   if (mode == CPINV_MODE_FP64) return 256;
+  if (mode == CPINV_MODE_SPLIT_BF16X3) return 1024 + split_workspace_bytes(M, N, K, symmetric != 0);
   if (mode != CPINV_MODE_EXACT_SLICE) return 0;
   const int beta = bits ? bits : 53;
   if (beta < 1 || beta > 62) return 0;
@@ -614,9 +894,9 @@ int cpinv_matmul(int32_t transA, int32_t transB, int64_t M, int64_t N, int64_t K
                  int64_t ldc, int32_t mode, int32_t bits, void* workspace, size_t workspace_bytes,
                  int32_t check, void* stream) {
   if (M < 0 || N < 0 || K < 0) return CPINV_ERR_INVALID_ARG;
-  if (mode != CPINV_MODE_FP64 && mode != CPINV_MODE_EXACT_SLICE) {
-    return mode == CPINV_MODE_SPLIT_BF16X3 ? CPINV_ERR_UNSUPPORTED : CPINV_ERR_INVALID_ARG;
-  }
+  if (mode != CPINV_MODE_FP64 && mode != CPINV_MODE_EXACT_SLICE &&
+      mode != CPINV_MODE_SPLIT_BF16X3)
+    return CPINV_ERR_INVALID_ARG;
   const int64_t arows = transA ? K : M, acols = transA ? M : K;
   const int64_t brows = transB ? N : K, bcols = transB ? K : N;
   if ((arows > 0 && lda < acols) || (brows > 0 && ldb < bcols) || ldc < N)
@@ -624,6 +904,7 @@ int cpinv_matmul(int32_t transA, int32_t transB, int64_t M, int64_t N, int64_t K
   if (M == 0 || N == 0) return CPINV_OK;
   if (!C || (K > 0 && (!A || !B))) return CPINV_ERR_INVALID_ARG;
   if (!std::isfinite(alpha) || !std::isfinite(beta)) return CPINV_ERR_INVALID_ARG;
+  if (C == A || C == B) return CPINV_ERR_INVALID_ARG;  // C must not alias an operand
   const int beta_bits = bits ? bits : 53;
   if (mode == CPINV_MODE_EXACT_SLICE && (beta_bits < 1 || beta_bits > 62)) return CPINV_ERR_INVALID_ARG;
   const bool same = A == B && lda == ldb && (transA != 0) != (transB != 0) && M == N;
@@ -651,6 +932,18 @@ int cpinv_matmul(int32_t transA, int32_t transB, int64_t M, int64_t N, int64_t K
     KernelTimer t;
     t.gemm = &g;
     CK(t.run(KT_GEMM_FP64, s, [&] { return launch_dgemm(g, transA != 0, transB != 0, s); }));
+  } else if (mode == CPINV_MODE_SPLIT_BF16X3) {
+    CrtGemm sg;
+    sg.p = g;
+    sg.transA = transA != 0;
+    sg.transB = transB != 0;
+    sg.same_operand = same;
+    sg.betaA = sg.betaB = 0;
+    sg.ws = (char*)workspace + 1024;
+    sg.ws_bytes = workspace_bytes - 1024;
+    sg.st = st;
+    KernelTimer t;
+    CK(launch_split_gemm(sg, s, &t));
   } else {
     CK(crt_product(g, transA != 0, transB != 0, beta_bits, same, (char*)workspace + 1024,
                    workspace_bytes - 1024, st, s));

@@ -158,6 +158,121 @@ __global__ void __launch_bounds__(256) diag_factor_kernel(double* A, int64_t lda
 #undef S
 #undef Wi
 
+// 1/sqrt(d) for d > 0 by Newton's iteration y <- y (3 - d y^2) / 2 from a
+// single-precision seed (about 22 correct bits); two FP64 steps bring it to
+// full double precision (each step doubles the correct bits).  Ranges beyond
+// float are handled by scaling d with an even power of two.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  int e2 = 0;
+  double ds = d;
+  if (d > 1e36 || d < 1e-36) {
+    e2 = (ilogb(d) / 2) * 2;
+    ds = scalbn(d, -e2);
+  }
+  double y = (double)rsqrtf((float)ds);
+  const double h = 0.5 * ds;
+  y = y * fma(-h * y, y, 1.5);
+  y = y * fma(-h * y, y, 1.5);
+  return e2 ? scalbn(y, -e2 / 2) : y;
+}
+
+// 1/x for x > 0 by Newton's iteration y <- y (2 - x y) from a single-precision
+// seed; two FP64 steps give full double precision.
+__device__ __forceinline__ double rcp_newton(double x) {
+  int e2 = 0;
+  double xs = x;
+  if (x > 1e36 || x < 1e-36) {
+    e2 = ilogb(x);
+    xs = scalbn(x, -e2);
+  }
+  double y = (double)(1.0f / (float)xs);
+  y = y * fma(-xs, y, 2.0);
+  y = y * fma(-xs, y, 2.0);
+  return e2 ? scalbn(y, -e2) : y;
+}
+
+// The same factorisation for b <= 32, one warp per column of the block and
+// one lane per row: thread (lane i, warp j) keeps A(i, j) in a register.  The
+// FP64 pipe of one SM is narrow, so the mapping keeps the FP64 instructions
+// per pivot to a minimum: the pivot (one lane), the column scaling (one warp
+// instruction), and one fused multiply-add per trailing column warp; two
+// barriers per column.  The inverse of the identity-patched block factor is
+// then 32 independent forward substitutions, warp j solving T w = e_j with
+// shuffles only.
+__global__ void __launch_bounds__(1024) diag32_kernel(double* A, int64_t lda, Dim nd, int64_t k0,
+                                                      int b, DevState* st, const int64_t* rdev,
+                                                      uint8_t* accepted, double* Z, double* Tinv,
+                                                      int spd) {
+  const int64_t n = eval_dim(nd, rdev);
+  if (k0 >= n) return;
+  const int bw = (int)((n - k0) < b ? (n - k0) : b);
+  __shared__ double Ls[32][33];   // Ls[row][col] = L(row, col)
+  __shared__ double colc[32];
+  __shared__ double dinv[32];
+  __shared__ int acc[32];
+  __shared__ int ok_s;
+  const int i = threadIdx.x & 31;   // row (lane)
+  const int j = threadIdx.x >> 5;   // column (warp)
+  const bool in = i < bw && j < bw && j <= i;
+  const double tol = spd ? 0.0 : st->tol;
+  double a = in ? A[(k0 + i) * lda + (k0 + j)] : 0.0;
+
+  for (int c = 0; c < bw; ++c) {
+    if (j == c) {
+      // warp c: pivot in lane c, then the column
+      const double d = __shfl_sync(0xffffffffu, a, c);
+      const bool ok = d > tol;  // false for NaN
+      double y = 0.0;
+      if (ok) y = rsqrt_newton(d);
+      if (i == c) {
+        a = ok ? d * y : 0.0;   // sqrt(d)
+        ok_s = ok ? 1 : 0;
+        acc[c] = ok ? 1 : 0;
+        dinv[c] = ok ? y : 1.0;  // 1 / L_cc (1 on a rejected row: identity patch)
+      } else if (i > c) {
+        a = ok ? a * y : 0.0;
+      }
+      colc[i] = (i >= c) ? a : 0.0;
+    }
+    __syncthreads();
+    if (ok_s && j > c && i >= j && i < bw) a = fma(-colc[i], colc[j], a);
+    __syncthreads();
+  }
+  // a = L(i, j) for j <= i (rejected columns zero)
+  Ls[i][j] = in ? a : 0.0;
+  __syncthreads();
+
+  // warp j: column j of W = inverse of the patched factor (rejected rows are
+  // identity rows), by forward substitution; lane i holds W(i, j).
+  double w = 0.0;
+  if (j < bw) {
+    double r = (i == j) ? 1.0 : 0.0;
+    for (int k = j; k < bw; ++k) {
+      const double wk = __shfl_sync(0xffffffffu, r, k) * dinv[k];
+      if (i == k) w = wk;
+      if (i > k) {
+        const double tik = acc[i] ? Ls[i][k] : 0.0;
+        r = fma(-tik, wk, r);
+      }
+    }
+  }
+  if (i < bw && j < bw) {
+    if (j <= i) A[(k0 + i) * lda + (k0 + j)] = a;
+    // Z(c, jj) = W(jj, c) on kept c and jj: this thread's W(i, j) is Z(j, i)
+    Z[j * b + i] = (acc[i] && acc[j]) ? w : 0.0;
+    if (spd && Tinv) Tinv[i * b + j] = w;
+  }
+  if (threadIdx.x == 0) {
+    int kept = 0;
+    for (int c = 0; c < bw; ++c) kept += acc[c];
+    if (spd) {
+      if (kept != bw) atomicOr(&st->status, ST_NUMERICAL);
+      atomicAdd((unsigned long long*)&st->rank_n, (unsigned long long)kept);
+    }
+  }
+  if (!spd && accepted && threadIdx.x < bw) accepted[k0 + threadIdx.x] = (uint8_t)acc[threadIdx.x];
+}
+
 // Prefix sum of the kept-pivot mask: colidx[c] = index of pivot c among the
 // kept ones (or -1), and the rank r.  One CTA.
 __global__ void scan_kernel(const uint8_t* accepted, int64_t n, int32_t* colidx, DevState* st) {
@@ -252,6 +367,10 @@ cudaError_t launch_diag_factor(double* A, int64_t lda, Dim nd, int64_t k0, int b
                                const int64_t* rdev, uint8_t* accepted, double* Z, double* Tinv,
                                int spd, cudaStream_t s) {
   if (b > MAXB || b < 1) return cudaErrorInvalidValue;
+  if (b <= 32) {
+    diag32_kernel<<<1, 1024, 0, s>>>(A, lda, nd, k0, b, st, rdev, accepted, Z, Tinv, spd);
+    return cudaGetLastError();
+  }
   const size_t smem = sizeof(double) * 2 * b * (b + 1) + sizeof(int) * b;
   static bool attr_set = false;
   if (!attr_set) {

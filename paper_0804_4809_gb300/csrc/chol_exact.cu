@@ -1,0 +1,103 @@
+// Left-looking full-rank Cholesky whose panel updates are exact residue
+// products on the tensor cores (exact-slice mode; Appendix of the paper).
+//
+// Every row of the factor is bounded by its diagonal entry: the kept and the
+// rejected parts of row i together sum to A_ii, so |L_ij| <= sqrt(A_ii).  That
+// bound fixes a power-of-two scale per row before any column exists, so each
+// finished panel of L is cut into residues once, into a persistent set of
+// residue planes RL[j][row][col]; the update of panel p,
+//   A(k0:n, P) -= L(k0:n, 0:k0) L(P, 0:k0)',
+// is then one tensor-core product over those planes (no re-splitting) and
+// one CRT reconstruction that subtracts the exactly summed update from A.
+#include <cmath>
+
+#include "common.cuh"
+#include "crt.h"
+#include "crt_device.cuh"
+#include "kernels.h"
+
+namespace cpinv {
+namespace {
+
+// E[i] = biased exponent of sqrt(A_ii), plus one: |L_ij| < 2^(E[i] - 1022).
+// 0 for a non-positive or non-finite diagonal entry (that row of L is 0).
+__global__ void rowscale_kernel(const double* A, int64_t lda, Dim nd, const int64_t* rdev,
+                                int64_t rows_max, int32_t* E) {
+  const int64_t n = eval_dim(nd, rdev);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows_max;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int e = 0;
+    if (i < n) {
+      const double d = A[i * lda + i];
+      if (d > 0.0 && isfinite(d)) {
+        const uint64_t b = (uint64_t)__double_as_longlong(sqrt(d));
+        e = (int)((b >> 52) & 0x7FF) + 1;
+      }
+    }
+    E[i] = e;
+  }
+}
+
+// Rows [k0, n) of panel k0: below the diagonal block, L(i, P) = A(i, P) Z (in
+// place); every row of the panel (diagonal block included) is then cut into
+// residues with the row scale E[i] and written to RL[j][i][k0 + c].
+// One 32 x 32 thread block per 32 rows; thread (ri, c).
+__global__ void __launch_bounds__(1024) panel_solve_split_kernel(
+    double* A, int64_t lda, Dim nd, const int64_t* rdev, int64_t k0, int b, const double* Z,
+    const int32_t* E, int n_mod, int beta, __nv_bfloat16* RL, int64_t rl_rows, int64_t rl_kpad) {
+  const int64_t n = eval_dim(nd, rdev);
+  if (k0 >= n) return;
+  const int bw = (int)((n - k0) < b ? (n - k0) : b);
+  __shared__ double Zs[32][33];
+  __shared__ double Arow[32][33];
+  const int ri = threadIdx.x >> 5, c = threadIdx.x & 31;
+  const int64_t i = k0 + (int64_t)blockIdx.x * 32 + ri;
+  if (ri < bw && c < bw) Zs[ri][c] = Z[ri * b + c];
+  const bool row_ok = i < n;
+  const bool below = i >= k0 + bw;
+  double v = 0.0;
+  if (row_ok && c < bw) v = A[i * lda + k0 + c];
+  Arow[ri][c] = v;
+  __syncthreads();
+  double l = 0.0;
+  if (row_ok && c < bw) {
+    if (below) {
+      for (int k = 0; k < bw; ++k) l = fma(Arow[ri][k], Zs[k][c], l);
+      A[i * lda + k0 + c] = l;
+    } else {
+      l = (c <= i - k0) ? v : 0.0;  // diagonal block: already the factor
+    }
+    const uint64_t bits = (uint64_t)__double_as_longlong(l);
+    const uint64_t a = crt::integerize(bits, E[i], beta);
+    crt::store_residues(a, (bits >> 63) != 0, n_mod, RL + (size_t)i * rl_kpad + (k0 + c),
+                        (size_t)rl_rows * (size_t)rl_kpad);
+  }
+}
+
+inline unsigned grid1d(int64_t total, int threads) {
+  int64_t g = (total + threads - 1) / threads;
+  if (g > 152 * 8) g = 152 * 8;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+cudaError_t launch_rowscale(const double* A, int64_t lda, Dim nd, const int64_t* rdev,
+                            int64_t rows_max, int32_t* E, cudaStream_t s) {
+  rowscale_kernel<<<grid1d(rows_max, 256), 256, 0, s>>>(A, lda, nd, rdev, rows_max, E);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_panel_solve_split(double* A, int64_t lda, Dim nd, const int64_t* rdev,
+                                     int64_t k0, int b, const double* Z, const int32_t* E,
+                                     int n_mod, int beta, void* RL, int64_t rl_rows,
+                                     int64_t rl_kpad, cudaStream_t s) {
+  if (b > 32) return cudaErrorInvalidValue;
+  const int64_t rows = nd.max - k0;
+  if (rows <= 0) return cudaSuccess;
+  panel_solve_split_kernel<<<(unsigned)((rows + 31) / 32), 1024, 0, s>>>(
+      A, lda, nd, rdev, k0, b, Z, E, n_mod, beta, (__nv_bfloat16*)RL, rl_rows, rl_kpad);
+  return cudaGetLastError();
+}
+
+}  // namespace cpinv

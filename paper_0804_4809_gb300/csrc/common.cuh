@@ -53,7 +53,7 @@ struct GemmParams {
   double alpha, beta;
   const int64_t* rdev;  // device rank, read when a Dim has sel = 1
   int32_t lower;        // 1: only C(i, j) with i >= j is computed and written
-  int32_t pad;
+  int32_t pad;          // FP64 path: 1 if C aliases A or B (whole-row tiles)
 };
 
 }  // namespace cpinv

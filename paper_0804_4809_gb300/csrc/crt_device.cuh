@@ -1,0 +1,50 @@
+// Device helpers shared by the kernels that write residue planes.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "crt.h"
+
+namespace cpinv {
+namespace crt {
+
+// |x| * 2^(beta - e) rounded to nearest, as an unsigned magnitude, where the
+// row bound is |x| < 2^e with e = Emax - 1022 (Emax a biased exponent):
+//   a = m * 2^(E - Emax + beta - 53)   (m the 53-bit significand of x).
+// With Emax at least the biased exponent of every |x| in the row, a < 2^beta.
+__device__ __forceinline__ uint64_t integerize(uint64_t b, int Emax, int beta) {
+  const int E = (int)((b >> 52) & 0x7FF);
+  if ((b << 1) == 0 || Emax == 0) return 0;
+  uint64_t m = b & 0xFFFFFFFFFFFFFull;
+  int Eeff = E;
+  if (E == 0) Eeff = 1;
+  else m |= 0x10000000000000ull;
+  const int sh = Eeff - Emax + beta - 53;
+  if (sh >= 0) return m << sh;  // beta <= 62 keeps this below 2^63
+  const int rs = -sh;
+  if (rs > 63) return 0;
+  const uint64_t half = (uint64_t)1 << (rs - 1);
+  return (m + half) >> rs;
+}
+
+// Balanced residues (|v| <= 64) of the signed integer (neg ? -a : a) modulo
+// the first n_mod moduli, as BF16 at o[j * plane].
+__device__ __forceinline__ void store_residues(uint64_t a, bool neg, int n_mod, __nv_bfloat16* o,
+                                               size_t plane) {
+  const uint32_t ahi = (uint32_t)(a >> 32), alo = (uint32_t)a;
+#pragma unroll
+  for (int j = 0; j < kMaxMod; ++j) {
+    if (j >= n_mod) break;
+    const uint32_t p = (uint32_t)modulus(j);
+    const uint32_t two32 = (uint32_t)((((uint64_t)1) << 32) % p);
+    uint32_t r = ((ahi % p) * two32 + (alo % p)) % p;
+    if (neg && r) r = p - r;
+    const int v = (int)r > (int)(p / 2) ? (int)r - (int)p : (int)r;
+    o[j * plane] = __float2bfloat16_rn((float)v);
+  }
+}
+
+}  // namespace crt
+}  // namespace cpinv

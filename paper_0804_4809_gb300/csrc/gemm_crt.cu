@@ -25,6 +25,7 @@
 
 #include "common.cuh"
 #include "crt.h"
+#include "crt_device.cuh"
 #include "kernels.h"
 
 namespace cpinv {
@@ -179,23 +180,6 @@ __global__ void row_expo_kernel(const double* X, int64_t ld, int trans, Dim rows
   if (bad) atomicOr(&st->status, ST_NONFINITE);
 }
 
-// |x| * 2^(beta - e_row) rounded to nearest, as an unsigned magnitude, where
-// e_row = Emax - 1022 (so |x| < 2^e_row):  a = m * 2^(E - Emax + beta - 53).
-__device__ __forceinline__ uint64_t integerize(uint64_t b, int Emax, int beta) {
-  const int E = (int)((b >> 52) & 0x7FF);
-  if ((b << 1) == 0 || Emax == 0) return 0;
-  uint64_t m = b & 0xFFFFFFFFFFFFFull;
-  int Eeff = E;
-  if (E == 0) Eeff = 1;
-  else m |= 0x10000000000000ull;
-  const int sh = Eeff - Emax + beta - 53;
-  if (sh >= 0) return m << sh;  // beta <= 62 keeps this below 2^63
-  const int rs = -sh;
-  if (rs > 63) return 0;
-  const uint64_t half = (uint64_t)1 << (rs - 1);
-  return (m + half) >> rs;
-}
-
 // residues of the 32x32 tile (rows i0.., k0..) of op(X); one thread per element
 __global__ void __launch_bounds__(256) split_kernel(const double* X, int64_t ld, int trans,
                                                     Dim rowsd, Dim colsd, int64_t rows_max,
@@ -228,21 +212,54 @@ __global__ void __launch_bounds__(256) split_kernel(const double* X, int64_t ld,
     uint64_t a = 0;
     bool neg = false;
     if (i < rows && k < cols && !nonfinite_bits(b)) {
-      a = integerize(b, E[i], beta);
+      a = crt::integerize(b, E[i], beta);
       neg = (b >> 63) != 0;
     }
-    const uint32_t ahi = (uint32_t)(a >> 32), alo = (uint32_t)a;
-    bf16* o = out + (size_t)i * kpad + k;
-#pragma unroll
-    for (int j = 0; j < crt::kMaxMod; ++j) {
-      if (j >= n_mod) break;
-      const uint32_t p = (uint32_t)crt::modulus(j);
-      const uint32_t two32 = (uint32_t)((((uint64_t)1) << 32) % p);
-      uint32_t r = ((ahi % p) * two32 + (alo % p)) % p;
-      if (neg && r) r = p - r;
-      const int v = (int)r > (int)(p / 2) ? (int)r - (int)p : (int)r;
-      o[j * plane] = __float2bfloat16_rn((float)v);
+    crt::store_residues(a, neg, n_mod, out + (size_t)i * kpad + k, plane);
+  }
+}
+
+// Split precision: the row of op(X) scaled by 2^(1022 - E[i]) (|x| < 1), then
+// hi = bf16(x), lo = bf16(x - hi) (through FP32), planes out[0] and out[1].
+__global__ void __launch_bounds__(256) split3_kernel(const double* X, int64_t ld, int trans,
+                                                     Dim rowsd, Dim colsd, int64_t rows_max,
+                                                     int64_t kpad, const int64_t* rdev,
+                                                     const int32_t* E, bf16* out) {
+  __shared__ uint64_t tile[32][33];
+  const int64_t rows = eval_dim(rowsd, rdev), cols = eval_dim(colsd, rdev);
+  const int64_t i0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int q = ty; q < 32; q += 8) {
+    uint64_t v = 0;
+    if (!trans) {
+      const int64_t i = i0 + q, k = k0 + tx;
+      if (i < rows && k < cols) v = reinterpret_cast<const uint64_t*>(X)[i * ld + k];
+      tile[q][tx] = v;
+    } else {
+      const int64_t k = k0 + q, i = i0 + tx;
+      if (i < rows && k < cols) v = reinterpret_cast<const uint64_t*>(X)[k * ld + i];
+      tile[tx][q] = v;
     }
+  }
+  __syncthreads();
+  const size_t plane = (size_t)rows_max * (size_t)kpad;
+  for (int q = ty; q < 32; q += 8) {
+    const int64_t i = i0 + q, k = k0 + tx;
+    if (i >= rows_max || k >= kpad) continue;
+    const uint64_t b = tile[q][tx];
+    float xf = 0.0f;
+    if (i < rows && k < cols && !nonfinite_bits(b) && E[i] > 0 && (b << 1) != 0) {
+      const int ex = (int)((b >> 52) & 0x7FF);
+      const int ne = ex - (E[i] - 1022);  // biased exponent of x * 2^(1022 - E[i])
+      if (ex != 0 && ne > 0) {
+        const uint64_t sb = (b & 0x800FFFFFFFFFFFFFull) | ((uint64_t)ne << 52);
+        xf = (float)__longlong_as_double((long long)sb);
+      }
+    }
+    const bf16 hi = __float2bfloat16_rn(xf);
+    const bf16 lo = __float2bfloat16_rn(xf - __bfloat162float(hi));
+    out[(size_t)i * kpad + k] = hi;
+    out[plane + (size_t)i * kpad + k] = lo;
   }
 }
 
@@ -352,6 +369,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 
 struct MmaParams {
   Dim M, N;                 // output size (may depend on the device rank)
+  int32_t a_row0, b_row0;   // first residue row of op(A) / of the N x K view of op(B)
   const int64_t* rdev;
   int32_t nk;               // K / BK (K padded)
   int32_t n_mod;
@@ -360,12 +378,31 @@ struct MmaParams {
   uint8_t* R;               // residues [n_mod][Mpad][Npad]
   int64_t Mpad, Npad;
   int32_t* status;          // DevState::status
+  // split (hi/lo) variant: FP64 output written by the epilogue
+  double* C;
+  int64_t ldc;
+  const int32_t* EA;
+  const int32_t* EB;
+  double alpha, beta;
 };
 
-template <int BN, int STAGES>
+// FP32 value * 2^s as FP64 with integer operations (exact: FP64 holds every
+// FP32 value); the FP64 unit only for out-of-range exponents and subnormals.
+__device__ __forceinline__ double f32_scaled_to_f64(uint32_t u, int s) {
+  const uint32_t e = (u >> 23) & 0xFFu;
+  if ((u << 1) == 0) return (u >> 31) ? -0.0 : 0.0;
+  const int be = (int)e - 127 + 1023 + s;
+  if (e == 0 || e == 0xFFu || be <= 0 || be >= 2047)
+    return ldexp((double)__uint_as_float(u), s);
+  const uint64_t bits = ((uint64_t)(u >> 31) << 63) | ((uint64_t)be << 52) |
+                        ((uint64_t)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+template <int BN, int STAGES, int PL>
 struct __align__(1024) MmaSmem {
-  bf16 A[STAGES][BM * BK];
-  bf16 B[STAGES][BN * BK];
+  bf16 A[STAGES][PL][BM * BK];
+  bf16 B[STAGES][PL][BN * BK];
   uint64_t full[STAGES];
   uint64_t empty[STAGES];
   uint64_t accfull[2];
@@ -375,12 +412,17 @@ struct __align__(1024) MmaSmem {
   int abort;
 };
 
-template <int BN, int STAGES>
+// S3 = false: residue products, one job per modulus (crt.h).
+// S3 = true: split precision, one job; planes 0/1 hold the hi/lo BF16 parts of
+// the scaled operands and each K step accumulates hi*hi + hi*lo + lo*hi in
+// FP32; the epilogue writes alpha * 2^(e_i + e_j) acc + beta C in FP64.
+template <int BN, int STAGES, bool S3>
 __global__ void __launch_bounds__(192, 1)
     crt_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    MmaParams p) {
+  constexpr int PL = S3 ? 2 : 1;
   extern __shared__ uint8_t smem_raw[];
-  MmaSmem<BN, STAGES>& sm = *reinterpret_cast<MmaSmem<BN, STAGES>*>(
+  MmaSmem<BN, STAGES, PL>& sm = *reinterpret_cast<MmaSmem<BN, STAGES, PL>*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -417,7 +459,7 @@ __global__ void __launch_bounds__(192, 1)
   tc_fence_after();
   const uint32_t tmem = sm.tmem_base;
   volatile int* abort = &sm.abort;
-  constexpr uint32_t kStageBytes = (BM + BN) * BK * sizeof(bf16);
+  constexpr uint32_t kStageBytes = PL * (BM + BN) * BK * sizeof(bf16);
   const int nk = p.nk;
 
   if (warp == 0) {
@@ -431,8 +473,12 @@ __global__ void __launch_bounds__(192, 1)
           const uint32_t ph = (it / STAGES) & 1u;
           if (!mbar_wait(&sm.empty[s], ph ^ 1u, abort)) break;
           mbar_expect_tx(&sm.full[s], kStageBytes);
-          tma_load_3d(sm.A[s], &tmA, &sm.full[s], kb * BK, (int)m0, j);
-          tma_load_3d(sm.B[s], &tmB, &sm.full[s], kb * BK, (int)n0, j);
+#pragma unroll
+          for (int pl = 0; pl < PL; ++pl) {
+            const int z = S3 ? pl : j;
+            tma_load_3d(sm.A[s][pl], &tmA, &sm.full[s], kb * BK, p.a_row0 + (int)m0, z);
+            tma_load_3d(sm.B[s][pl], &tmB, &sm.full[s], kb * BK, p.b_row0 + (int)n0, z);
+          }
         }
       }
       // drain: every issued stage must have landed before the CTA exits
@@ -461,11 +507,16 @@ __global__ void __launch_bounds__(192, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t a0 = smem_u32(sm.A[s]), b0 = smem_u32(sm.B[s]);
+          const uint32_t a0 = smem_u32(sm.A[s][0]), b0 = smem_u32(sm.B[s][0]);
 #pragma unroll
           for (int ks = 0; ks < BK / 16; ++ks) {
             umma_bf16(dtm, umma_desc_sw128(a0 + ks * 32), umma_desc_sw128(b0 + ks * 32), idesc,
                       (kb | ks) != 0);
+            if constexpr (S3) {
+              const uint32_t a1 = smem_u32(sm.A[s][PL - 1]), b1 = smem_u32(sm.B[s][PL - 1]);
+              umma_bf16(dtm, umma_desc_sw128(a0 + ks * 32), umma_desc_sw128(b1 + ks * 32), idesc, 1);
+              umma_bf16(dtm, umma_desc_sw128(a1 + ks * 32), umma_desc_sw128(b0 + ks * 32), idesc, 1);
+            }
           }
           umma_commit(&sm.empty[s]);  // stage reusable once these MMAs are done
         }
@@ -486,32 +537,54 @@ __global__ void __launch_bounds__(192, 1)
       const int j = jbeg + jj;
       if (!mbar_wait(&sm.accfull[acc], (jj >> 1) & 1u, abort)) break;
       tc_fence_after();
-      int pj = 0;
-#pragma unroll
-      for (int t = 0; t < crt::kMaxMod; ++t)
-        if (t == j) pj = crt::modulus(t);
-      const float pfl = (float)pj, inv = 1.0f / (float)pj;
-      uint8_t* out = p.R + ((size_t)j * p.Mpad + row) * p.Npad + n0;
+      if constexpr (S3) {
+        const int64_t Mv = M, Nv = N;
+        const bool rowok = row < Mv;
+        const int sr = rowok ? p.EA[row] - 1022 : 0;
 #pragma unroll 1
-      for (int c = 0; c < BN; c += 32) {
-        uint32_t v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c), v);
-        uint32_t packed[8];
-#pragma unroll
-        for (int e = 0; e < 32; ++e) {
-          // exact integer |x| <= 2^24: x mod p in [0, p)
-          const float x = __uint_as_float(v[e]);
-          float qf = floorf(x * inv);
-          float r = fmaf(-qf, pfl, x);
-          if (r < 0.f) r += pfl;
-          if (r >= pfl) r -= pfl;
-          const uint32_t rb = __float_as_uint(r + 8388608.0f) & 0xFFu;  // 2^23 trick
-          if ((e & 3) == 0) packed[e >> 2] = 0;
-          packed[e >> 2] |= rb << (8 * (e & 3));
+        for (int c = 0; c < BN; c += 32) {
+          uint32_t v[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c), v);
+          if (!rowok) continue;
+#pragma unroll 4
+          for (int e = 0; e < 32; ++e) {
+            const int64_t col = n0 + c + e;
+            if (col >= Nv || (p.lower && col > row)) continue;
+            double d = f32_scaled_to_f64(v[e], sr + p.EB[col] - 1022);
+            double* cp = p.C + row * p.ldc + col;
+            if (p.alpha != 1.0) d *= p.alpha;
+            if (p.beta != 0.0) d = fma(p.beta, *cp, d);
+            *cp = d;
+          }
         }
-        uint4* dst = reinterpret_cast<uint4*>(out + c);
-        dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-        dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+      } else {
+        int pj = 0;
+  #pragma unroll
+        for (int t = 0; t < crt::kMaxMod; ++t)
+          if (t == j) pj = crt::modulus(t);
+        const float pfl = (float)pj, inv = 1.0f / (float)pj;
+        uint8_t* out = p.R + ((size_t)j * p.Mpad + row) * p.Npad + n0;
+  #pragma unroll 1
+        for (int c = 0; c < BN; c += 32) {
+          uint32_t v[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c), v);
+          uint32_t packed[8];
+  #pragma unroll
+          for (int e = 0; e < 32; ++e) {
+            // exact integer |x| <= 2^24: x mod p in [0, p)
+            const float x = __uint_as_float(v[e]);
+            float qf = floorf(x * inv);
+            float r = fmaf(-qf, pfl, x);
+            if (r < 0.f) r += pfl;
+            if (r >= pfl) r -= pfl;
+            const uint32_t rb = __float_as_uint(r + 8388608.0f) & 0xFFu;  // 2^23 trick
+            if ((e & 3) == 0) packed[e >> 2] = 0;
+            packed[e >> 2] |= rb << (8 * (e & 3));
+          }
+          uint4* dst = reinterpret_cast<uint4*>(out + c);
+          dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+          dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+        }
       }
       tc_fence_before();
       __syncwarp();
@@ -736,20 +809,20 @@ bool make_map(CUtensorMap* map, const bf16* base, int64_t kpad, int64_t rows, in
   return r == CUDA_SUCCESS;
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool S3>
 cudaError_t launch_mma(const CUtensorMap& ta, const CUtensorMap& tb, const MmaParams& mp,
                        int64_t Mmax, int64_t Nmax, cudaStream_t s) {
-  const size_t smem = sizeof(MmaSmem<BN, STAGES>) + 1024;
+  const size_t smem = sizeof(MmaSmem<BN, STAGES, S3 ? 2 : 1>) + 1024;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(crt_mma_kernel<BN, STAGES>,
+    cudaError_t e = cudaFuncSetAttribute(crt_mma_kernel<BN, STAGES, S3>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const int groups = (mp.n_mod + mp.mods_per_cta - 1) / mp.mods_per_cta;
   dim3 grid((unsigned)((Nmax + BN - 1) / BN), (unsigned)((Mmax + BM - 1) / BM), (unsigned)groups);
-  crt_mma_kernel<BN, STAGES><<<grid, 192, smem, s>>>(ta, tb, mp);
+  crt_mma_kernel<BN, STAGES, S3><<<grid, 192, smem, s>>>(ta, tb, mp);
   return cudaGetLastError();
 }
 
@@ -769,6 +842,9 @@ int crt_moduli_for(int64_t Kmax, int betaA, int betaB) {
   return crt::moduli_for_bits(bits);
 }
 
+int crt_block_k() { return BK; }
+int crt_block_m() { return BM; }
+
 // Workspace needed by one exact product (see launch_crt_gemm).
 size_t crt_workspace_bytes(int64_t Mmax, int64_t Nmax, int64_t Kmax, int n_mod, bool same_operand) {
   const int64_t kpad = round_up(Kmax > 0 ? Kmax : 1, BK);
@@ -783,6 +859,182 @@ size_t crt_workspace_bytes(int64_t Mmax, int64_t Nmax, int64_t Kmax, int n_mod, 
   return b + 1024;
 }
 
+cudaError_t crt_row_exponents(const double* X, int64_t ld, int tview, Dim rows, Dim K,
+                              const int64_t* rdev, int64_t rows_max, int32_t* E, DevState* st,
+                              cudaStream_t s, KernelTimer* timer) {
+  return timer->run(KT_SPLIT, s, [&] {
+    if (!tview)
+      row_expo_kernel<<<(unsigned)((rows_max * 32 + 255) / 256), 256, 0, s>>>(X, ld, 0, rows, K,
+                                                                             rdev, E, st);
+    else
+      row_expo_kernel<<<dim3((unsigned)((rows_max + 31) / 32), 16), 256, 0, s>>>(X, ld, 1, rows, K,
+                                                                                rdev, E, st);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t crt_split(const double* X, int64_t ld, int tview, Dim rows, Dim K, const int64_t* rdev,
+                      int64_t rows_max, int64_t kpad, const int32_t* E, int n_mod, int beta,
+                      void* out, cudaStream_t s, KernelTimer* timer) {
+  dim3 grid((unsigned)(kpad / 32), (unsigned)((rows_max + 31) / 32));
+  return timer->run(KT_SPLIT, s, [&] {
+    split_kernel<<<grid, 256, 0, s>>>(X, ld, tview, rows, K, rows_max, kpad, rdev, E, n_mod, beta,
+                                      (bf16*)out);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t crt_mma(const void* SA, int64_t a_rows, int a_row0, const void* SB, int64_t b_rows,
+                    int b_row0, int64_t kpad, int64_t kuse, int n_mod, Dim M, Dim N,
+                    const int64_t* rdev, int lower, uint8_t* R, int64_t Mpad, int64_t Npad,
+                    int32_t* status, cudaStream_t s, KernelTimer* timer, const GemmParams* fl) {
+  const int64_t Mmax = M.max, Nmax = N.max;
+  if (Mmax <= 0 || Nmax <= 0) return cudaSuccess;
+  const int BN = (Nmax >= 2048) ? 256 : 128;
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, (const bf16*)SA, kpad, a_rows, n_mod, BM)) return cudaErrorInvalidValue;
+  if (!make_map(&tb, (const bf16*)SB, kpad, b_rows, n_mod, BN)) return cudaErrorInvalidValue;
+  MmaParams mp;
+  std::memset(&mp, 0, sizeof(mp));
+  mp.M = M;
+  mp.N = N;
+  mp.a_row0 = a_row0;
+  mp.b_row0 = b_row0;
+  mp.rdev = rdev;
+  mp.nk = (int)((kuse + BK - 1) / BK);
+  if (mp.nk < 1) mp.nk = 1;
+  mp.n_mod = n_mod;
+  mp.lower = lower;
+  mp.R = R;
+  mp.Mpad = Mpad;
+  mp.Npad = Npad;
+  mp.status = status;
+  const int64_t tiles = ((Mmax + BM - 1) / BM) * ((Nmax + BN - 1) / BN) / (lower ? 2 : 1);
+  int mpc = n_mod;
+  while (mpc > 1 && (tiles > 0 ? tiles : 1) * ((n_mod + mpc - 1) / mpc) < 2 * 152)
+    mpc = (mpc + 1) / 2;
+  mp.mods_per_cta = mpc;
+  KernelTimer mt = *timer;
+  mt.gemm = fl;
+  mt.flops_mult = (double)n_mod;
+  return mt.run(KT_MMA, s, [&] {
+    return BN == 256 ? launch_mma<256, 4, false>(ta, tb, mp, Mmax, Nmax, s)
+                     : launch_mma<128, 6, false>(ta, tb, mp, Mmax, Nmax, s);
+  });
+}
+
+cudaError_t crt_reconstruct(const uint8_t* R, int64_t Mpad, int64_t Npad, Dim M, Dim N,
+                            const int64_t* rdev, const int32_t* EA, const int32_t* EB, int betaA,
+                            int betaB, double alpha, double beta, double* C, int64_t ldc,
+                            int lower, int n_mod, cudaStream_t s, KernelTimer* timer) {
+  static crt::Consts consts[crt::kMaxMod + 1];
+  static bool have[crt::kMaxMod + 1] = {false};
+  static std::mutex mu;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!have[n_mod]) {
+      crt::make_consts(n_mod, &consts[n_mod]);
+      have[n_mod] = true;
+    }
+  }
+  ReconParams rp;
+  rp.R = R;
+  rp.Mpad = Mpad;
+  rp.Npad = Npad;
+  rp.M = M;
+  rp.N = N;
+  rp.rdev = rdev;
+  rp.EA = EA;
+  rp.EB = EB;
+  rp.betaA = betaA;
+  rp.betaB = betaB;
+  rp.alpha = alpha;
+  rp.beta = beta;
+  rp.C = C;
+  rp.ldc = ldc;
+  rp.lower = lower;
+  rp.pad = 0;
+  return timer->run(KT_RECON, s, [&] {
+    reconstruct_kernel<<<grid1d(M.max * N.max, 256), 256, 0, s>>>(rp, consts[n_mod]);
+    return cudaGetLastError();
+  });
+}
+
+size_t split_workspace_bytes(int64_t Mmax, int64_t Nmax, int64_t Kmax, bool same_operand) {
+  const int64_t kpad = round_up(Kmax > 0 ? Kmax : 1, BK);
+  const int64_t mpad = round_up(Mmax > 0 ? Mmax : 1, BM);
+  const int64_t npad = round_up(Nmax > 0 ? Nmax : 1, 256);
+  size_t b = 0;
+  auto add = [&](size_t x) { b = (b + 1023) / 1024 * 1024 + x; };
+  add(sizeof(bf16) * 2 * (size_t)mpad * (size_t)kpad);
+  if (!same_operand) add(sizeof(bf16) * 2 * (size_t)npad * (size_t)kpad);
+  add(sizeof(int32_t) * (size_t)(mpad + npad));
+  return b + 1024;
+}
+
+// Split-precision product (BF16x3, FP32 accumulation): reduced accuracy,
+// about 2^-16 relative per term.
+cudaError_t launch_split_gemm(const CrtGemm& g, cudaStream_t s, KernelTimer* timer) {
+  const GemmParams& p = g.p;
+  const int64_t Mmax = p.M.max, Nmax = p.N.max, Kmax = p.K.max;
+  if (Mmax <= 0 || Nmax <= 0) return cudaSuccess;
+  const int64_t kpad = round_up(Kmax > 0 ? Kmax : 1, BK);
+  const int64_t mpad = round_up(Mmax, BM);
+  const int64_t npad = round_up(Nmax, 256);
+  const bool same = g.same_operand;
+  char* w = (char*)g.ws;
+  size_t off = 0;
+  auto take = [&](size_t x) {
+    off = (off + 1023) / 1024 * 1024;
+    char* q = w + off;
+    off += x;
+    return q;
+  };
+  bf16* SA = (bf16*)take(sizeof(bf16) * 2 * (size_t)mpad * (size_t)kpad);
+  bf16* SB = same ? SA : (bf16*)take(sizeof(bf16) * 2 * (size_t)npad * (size_t)kpad);
+  int32_t* EA = (int32_t*)take(sizeof(int32_t) * (size_t)(mpad + npad));
+  int32_t* EB = same ? EA : EA + mpad;
+  if (off > g.ws_bytes) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(EA, 0, sizeof(int32_t) * (size_t)(mpad + npad), s);
+  if (e != cudaSuccess) return e;
+  auto split = [&](const double* X, int64_t ld, int tview, Dim rows, int64_t rows_max, int32_t* E,
+                   bf16* S) -> cudaError_t {
+    cudaError_t err = crt_row_exponents(X, ld, tview, rows, p.K, p.rdev, rows_max, E, g.st, s, timer);
+    if (err != cudaSuccess) return err;
+    dim3 grid((unsigned)(kpad / 32), (unsigned)((rows_max + 31) / 32));
+    return timer->run(KT_SPLIT, s, [&] {
+      split3_kernel<<<grid, 256, 0, s>>>(X, ld, tview, rows, p.K, rows_max, kpad, p.rdev, E, S);
+      return cudaGetLastError();
+    });
+  };
+  e = split(p.A, p.lda, g.transA ? 1 : 0, p.M, mpad, EA, SA);
+  if (e == cudaSuccess && !same) e = split(p.B, p.ldb, g.transB ? 0 : 1, p.N, npad, EB, SB);
+  if (e != cudaSuccess) return e;
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, SA, kpad, mpad, 2, BM)) return cudaErrorInvalidValue;
+  if (!make_map(&tb, SB, kpad, same ? mpad : npad, 2, 128)) return cudaErrorInvalidValue;
+  MmaParams mp;
+  std::memset(&mp, 0, sizeof(mp));
+  mp.M = p.M;
+  mp.N = p.N;
+  mp.rdev = p.rdev;
+  mp.nk = (int)(kpad / BK);
+  mp.n_mod = 1;
+  mp.mods_per_cta = 1;
+  mp.lower = p.lower;
+  mp.status = &g.st->status;
+  mp.C = p.C;
+  mp.ldc = p.ldc;
+  mp.EA = EA;
+  mp.EB = EB;
+  mp.alpha = p.alpha;
+  mp.beta = p.beta;
+  KernelTimer mt = *timer;
+  mt.gemm = &g.p;
+  mt.flops_mult = 3.0;
+  return mt.run(KT_MMA, s, [&] { return launch_mma<128, 3, true>(ta, tb, mp, Mmax, Nmax, s); });
+}
+
 cudaError_t launch_crt_gemm(const CrtGemm& g, cudaStream_t s, KernelTimer* timer) {
   const GemmParams& p = g.p;
   const int64_t Mmax = p.M.max, Nmax = p.N.max, Kmax = p.K.max;
@@ -792,10 +1044,8 @@ cudaError_t launch_crt_gemm(const CrtGemm& g, cudaStream_t s, KernelTimer* timer
   if (n_mod < 0) return cudaErrorInvalidValue;
   const int64_t kpad = round_up(Kmax > 0 ? Kmax : 1, BK);
   const int64_t mpad = round_up(Mmax, BM);
-  const int BN = (Nmax >= 2048) ? 256 : 128;
   const int64_t npad = round_up(Nmax, 256);
   const bool same = g.same_operand;
-  // carve the workspace
   char* w = (char*)g.ws;
   size_t off = 0;
   auto take = [&](size_t x) {
@@ -811,99 +1061,27 @@ cudaError_t launch_crt_gemm(const CrtGemm& g, cudaStream_t s, KernelTimer* timer
   int32_t* EB = same ? EA : EA + mpad;
   if (off > g.ws_bytes) return cudaErrorInvalidValue;
 
-  // ---- split the operands ----
-  const int betaA = g.betaA, betaB = g.betaB;
   cudaError_t e = cudaMemsetAsync(EA, 0, sizeof(int32_t) * (size_t)(mpad + npad), s);
   if (e != cudaSuccess) return e;
   // op(A): rows x K; transA: element (i,k) at A[k*lda + i].  op(B) is K x N;
   // its N x K view: element (j,k) = transB ? B[j*ldb + k] : B[k*ldb + j].
-  auto split = [&](const double* X, int64_t ld, int tview, Dim rows, int64_t rows_max, int beta,
-                   int32_t* E, bf16* S) -> cudaError_t {
-    cudaError_t err = timer->run(KT_SPLIT, s, [&] {
-      if (!tview)
-        row_expo_kernel<<<(unsigned)((rows_max * 32 + 255) / 256), 256, 0, s>>>(X, ld, 0, rows,
-                                                                               p.K, p.rdev, E, g.st);
-      else
-        row_expo_kernel<<<dim3((unsigned)(rows_max / 32), 16), 256, 0, s>>>(X, ld, 1, rows, p.K,
-                                                                           p.rdev, E, g.st);
-      return cudaGetLastError();
-    });
-    if (err != cudaSuccess) return err;
-    dim3 grid((unsigned)(kpad / 32), (unsigned)(rows_max / 32));
-    return timer->run(KT_SPLIT, s, [&] {
-      split_kernel<<<grid, 256, 0, s>>>(X, ld, tview, rows, p.K, rows_max, kpad, p.rdev, E, n_mod,
-                                        beta, S);
-      return cudaGetLastError();
-    });
-  };
-  e = split(p.A, p.lda, g.transA ? 1 : 0, p.M, mpad, betaA, EA, SA);
-  if (e != cudaSuccess) return e;
-  if (!same) {
-    e = split(p.B, p.ldb, g.transB ? 0 : 1, p.N, npad, betaB, EB, SB);
-    if (e != cudaSuccess) return e;
+  e = crt_row_exponents(p.A, p.lda, g.transA ? 1 : 0, p.M, p.K, p.rdev, mpad, EA, g.st, s, timer);
+  if (e == cudaSuccess)
+    e = crt_split(p.A, p.lda, g.transA ? 1 : 0, p.M, p.K, p.rdev, mpad, kpad, EA, n_mod, g.betaA,
+                  SA, s, timer);
+  if (e == cudaSuccess && !same) {
+    e = crt_row_exponents(p.B, p.ldb, g.transB ? 0 : 1, p.N, p.K, p.rdev, npad, EB, g.st, s, timer);
+    if (e == cudaSuccess)
+      e = crt_split(p.B, p.ldb, g.transB ? 0 : 1, p.N, p.K, p.rdev, npad, kpad, EB, n_mod, g.betaB,
+                    SB, s, timer);
   }
-
-  // ---- tensor-core products, one per modulus ----
-  CUtensorMap ta, tb;
-  if (!make_map(&ta, SA, kpad, mpad, n_mod, BM)) return cudaErrorInvalidValue;
-  if (!make_map(&tb, SB, kpad, same ? mpad : npad, n_mod, BN)) return cudaErrorInvalidValue;
-  MmaParams mp;
-  mp.M = p.M;
-  mp.N = p.N;
-  mp.rdev = p.rdev;
-  mp.nk = (int)(kpad / BK);
-  mp.n_mod = n_mod;
-  mp.lower = p.lower;
-  mp.R = R;
-  mp.Mpad = mpad;
-  mp.Npad = npad;
-  mp.status = &g.st->status;
-  // moduli per CTA: enough CTAs to fill the GPU about twice
-  const int64_t tiles = ((Mmax + BM - 1) / BM) * ((Nmax + BN - 1) / BN) / (p.lower ? 2 : 1);
-  int mpc = n_mod;
-  while (mpc > 1 && tiles * ((n_mod + mpc - 1) / mpc) < 2 * 152) mpc = (mpc + 1) / 2;
-  mp.mods_per_cta = mpc;
-  KernelTimer mt = *timer;
-  mt.gemm = &g.p;
-  mt.flops_mult = (double)n_mod;
-  e = mt.run(KT_MMA, s, [&] {
-    return BN == 256 ? launch_mma<256, 4>(ta, tb, mp, Mmax, Nmax, s)
-                     : launch_mma<128, 6>(ta, tb, mp, Mmax, Nmax, s);
-  });
   if (e != cudaSuccess) return e;
-
-  // ---- reconstruction ----
-  static crt::Consts consts[crt::kMaxMod + 1];
-  static bool have[crt::kMaxMod + 1] = {false};
-  static std::mutex mu;
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    if (!have[n_mod]) {
-      crt::make_consts(n_mod, &consts[n_mod]);
-      have[n_mod] = true;
-    }
-  }
-  ReconParams rp;
-  rp.R = R;
-  rp.Mpad = mpad;
-  rp.Npad = npad;
-  rp.M = p.M;
-  rp.N = p.N;
-  rp.rdev = p.rdev;
-  rp.EA = EA;
-  rp.EB = EB;
-  rp.betaA = betaA;
-  rp.betaB = same ? betaA : betaB;
-  rp.alpha = p.alpha;
-  rp.beta = p.beta;
-  rp.C = p.C;
-  rp.ldc = p.ldc;
-  rp.lower = p.lower;
-  rp.pad = 0;
-  return timer->run(KT_RECON, s, [&] {
-    reconstruct_kernel<<<grid1d(Mmax * Nmax, 256), 256, 0, s>>>(rp, consts[n_mod]);
-    return cudaGetLastError();
-  });
+  e = crt_mma(SA, mpad, 0, SB, same ? mpad : npad, 0, kpad, Kmax, n_mod, p.M, p.N, p.rdev, p.lower,
+              R, mpad, npad, &g.st->status, s, timer, &g.p);
+  if (e != cudaSuccess) return e;
+  return crt_reconstruct(R, mpad, npad, p.M, p.N, p.rdev, EA, EB, g.betaA,
+                         same ? g.betaA : g.betaB, p.alpha, p.beta, p.C, p.ldc, p.lower, n_mod, s,
+                         timer);
 }
 
 }  // namespace cpinv

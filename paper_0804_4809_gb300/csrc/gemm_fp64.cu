@@ -13,46 +13,49 @@ namespace cpinv {
 
 namespace {
 
-constexpr int TM = 64, TN = 64, TK = 16;
+constexpr int TK = 16;
 
-template <bool TA, bool TB>
+// T x T output tile per 256-thread CTA, (T/16) x (T/16) outputs per thread.
+// T = 64 for large outputs; 32 and 16 spread small products over more SMs
+// (each SM's FP64 pipe is narrow, so a product must occupy many SMs).
+template <bool TA, bool TB, int T>
 __global__ void __launch_bounds__(256) dgemm_kernel(GemmParams p) {
+  constexpr int U = T / 16;
   const int64_t M = eval_dim(p.M, p.rdev);
   const int64_t N = eval_dim(p.N, p.rdev);
   const int64_t K = eval_dim(p.K, p.rdev);
-  const int64_t i0 = (int64_t)blockIdx.y * TM;
-  const int64_t j0 = (int64_t)blockIdx.x * TN;
+  const int64_t i0 = (int64_t)blockIdx.y * T;
+  const int64_t j0 = (int64_t)blockIdx.x * T;
   if (i0 >= M || j0 >= N) return;
-  if (p.lower && j0 > i0 + TM - 1) return;  // tile strictly above the diagonal
+  if (p.lower && j0 > i0 + T - 1) return;  // tile strictly above the diagonal
 
-  __shared__ double As[TK][TM + 1];
-  __shared__ double Bs[TK][TN + 1];
+  __shared__ double As[TK][T + 1];
+  __shared__ double Bs[TK][T + 1];
 
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  double acc[4][4];
+  double acc[U][U];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < U; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int b = 0; b < U; ++b) acc[a][b] = 0.0;
 
   for (int64_t k0 = 0; k0 < K; k0 += TK) {
-    // A tile: TM x TK elements of op(A)
 #pragma unroll
-    for (int q = 0; q < (TM * TK) / 256; ++q) {
+    for (int q = 0; q < (T * TK) / 256; ++q) {
       const int e = tid + 256 * q;
       int i, k;
-      if (TA) { k = e / TM; i = e % TM; } else { i = e / TK; k = e % TK; }
+      if (TA) { k = e / T; i = e % T; } else { i = e / TK; k = e % TK; }
       const int64_t gi = i0 + i, gk = k0 + k;
       double v = 0.0;
       if (gi < M && gk < K) v = TA ? p.A[gk * p.lda + gi] : p.A[gi * p.lda + gk];
       As[k][i] = v;
     }
 #pragma unroll
-    for (int q = 0; q < (TN * TK) / 256; ++q) {
+    for (int q = 0; q < (T * TK) / 256; ++q) {
       const int e = tid + 256 * q;
       int j, k;
-      if (TB) { j = e / TK; k = e % TK; } else { k = e / TN; j = e % TN; }
+      if (TB) { j = e / TK; k = e % TK; } else { k = e / T; j = e % T; }
       const int64_t gj = j0 + j, gk = k0 + k;
       double v = 0.0;
       if (gj < N && gk < K) v = TB ? p.B[gj * p.ldb + gk] : p.B[gk * p.ldb + gj];
@@ -61,25 +64,25 @@ __global__ void __launch_bounds__(256) dgemm_kernel(GemmParams p) {
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < TK; ++k) {
-      double a[4], b[4];
+      double a[U], b[U];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] = As[k][ty + 16 * u];
+      for (int u = 0; u < U; ++u) a[u] = As[k][ty + 16 * u];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) b[u] = Bs[k][tx + 16 * u];
+      for (int u = 0; u < U; ++u) b[u] = Bs[k][tx + 16 * u];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        for (int v = 0; v < U; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
     }
     __syncthreads();
   }
 
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < U; ++u) {
     const int64_t gi = i0 + ty + 16 * u;
     if (gi >= M) continue;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < U; ++v) {
       const int64_t gj = j0 + tx + 16 * v;
       if (gj >= N) continue;
       if (p.lower && gj > gi) continue;
@@ -91,18 +94,35 @@ __global__ void __launch_bounds__(256) dgemm_kernel(GemmParams p) {
   }
 }
 
+template <int T>
+cudaError_t launch_tile(const GemmParams& p, bool transA, bool transB, cudaStream_t s) {
+  dim3 grid((unsigned)((p.N.max + T - 1) / T), (unsigned)((p.M.max + T - 1) / T));
+  if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+  if (!transA && !transB) dgemm_kernel<false, false, T><<<grid, 256, 0, s>>>(p);
+  else if (!transA && transB) dgemm_kernel<false, true, T><<<grid, 256, 0, s>>>(p);
+  else if (transA && !transB) dgemm_kernel<true, false, T><<<grid, 256, 0, s>>>(p);
+  else dgemm_kernel<true, true, T><<<grid, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_dgemm(const GemmParams& p, bool transA, bool transB, cudaStream_t s) {
   const int64_t Mmax = p.M.max, Nmax = p.N.max;
   if (Mmax <= 0 || Nmax <= 0) return cudaSuccess;
-  dim3 grid((unsigned)((Nmax + TN - 1) / TN), (unsigned)((Mmax + TM - 1) / TM));
-  if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
-  if (!transA && !transB) dgemm_kernel<false, false><<<grid, 256, 0, s>>>(p);
-  else if (!transA && transB) dgemm_kernel<false, true><<<grid, 256, 0, s>>>(p);
-  else if (transA && !transB) dgemm_kernel<true, false><<<grid, 256, 0, s>>>(p);
-  else dgemm_kernel<true, true><<<grid, 256, 0, s>>>(p);
-  return cudaGetLastError();
+  if (p.pad) {
+    // C aliases an operand: every CTA must own whole rows of C (all N columns),
+    // so that it reads them completely before it overwrites them.
+    if (Nmax <= 16) return launch_tile<16>(p, transA, transB, s);
+    if (Nmax <= 32) return launch_tile<32>(p, transA, transB, s);
+    if (Nmax <= 64) return launch_tile<64>(p, transA, transB, s);
+    return cudaErrorInvalidValue;
+  }
+  auto tiles = [&](int64_t t) { return ((Mmax + t - 1) / t) * ((Nmax + t - 1) / t); };
+  if (tiles(64) >= 152 || (Mmax >= 64 && Nmax >= 64 && tiles(32) > 4 * 152))
+    return launch_tile<64>(p, transA, transB, s);
+  if (tiles(32) >= 152) return launch_tile<32>(p, transA, transB, s);
+  return launch_tile<16>(p, transA, transB, s);
 }
 
 }  // namespace cpinv

@@ -41,6 +41,13 @@ struct KernelTimer {
   }
 };
 
+// While alive, calls on this thread run their kernels directly (no CUDA-graph
+// capture or replay: instantiating a graph may allocate).
+struct NoGraphScope {
+  NoGraphScope();
+  ~NoGraphScope();
+};
+
 // One FP64-accurate product in the residue (exact-slice) arithmetic.
 struct CrtGemm {
   GemmParams p;       // C = alpha op(A) op(B) + beta C  (dims may depend on the device rank)
@@ -54,6 +61,36 @@ struct CrtGemm {
 size_t crt_workspace_bytes(int64_t Mmax, int64_t Nmax, int64_t Kmax, int n_mod, bool same_operand);
 cudaError_t launch_crt_gemm(const CrtGemm& g, cudaStream_t s, KernelTimer* timer);
 int crt_moduli_for(int64_t Kmax, int betaA, int betaB);
+size_t split_workspace_bytes(int64_t Mmax, int64_t Nmax, int64_t Kmax, bool same_operand);
+cudaError_t launch_split_gemm(const CrtGemm& g, cudaStream_t s, KernelTimer* timer);
+int crt_block_k();  // K granularity of the residue planes (64)
+int crt_block_m();  // rows of an output tile (128)
+// The three stages of an exact product, for callers that keep residues:
+//   row exponents (atomicMax into a zeroed array), residue planes
+//   S[j][row][k] (BF16, rows_max x kpad per modulus), the tensor-core
+//   products mod p_j into R[j][row][col], and the CRT reconstruction.
+cudaError_t crt_row_exponents(const double* X, int64_t ld, int tview, Dim rows, Dim K,
+                              const int64_t* rdev, int64_t rows_max, int32_t* E, DevState* st,
+                              cudaStream_t s, KernelTimer* timer);
+cudaError_t crt_split(const double* X, int64_t ld, int tview, Dim rows, Dim K, const int64_t* rdev,
+                      int64_t rows_max, int64_t kpad, const int32_t* E, int n_mod, int beta,
+                      void* out, cudaStream_t s, KernelTimer* timer);
+cudaError_t crt_mma(const void* SA, int64_t a_rows, int a_row0, const void* SB, int64_t b_rows,
+                    int b_row0, int64_t kpad, int64_t kuse, int n_mod, Dim M, Dim N,
+                    const int64_t* rdev, int lower, uint8_t* R, int64_t Mpad, int64_t Npad,
+                    int32_t* status, cudaStream_t s, KernelTimer* timer, const GemmParams* fl);
+cudaError_t crt_reconstruct(const uint8_t* R, int64_t Mpad, int64_t Npad, Dim M, Dim N,
+                            const int64_t* rdev, const int32_t* EA, const int32_t* EB, int betaA,
+                            int betaB, double alpha, double beta, double* C, int64_t ldc,
+                            int lower, int n_mod, cudaStream_t s, KernelTimer* timer);
+
+// chol_exact.cu
+cudaError_t launch_rowscale(const double* A, int64_t lda, Dim nd, const int64_t* rdev,
+                            int64_t rows_max, int32_t* E, cudaStream_t s);
+cudaError_t launch_panel_solve_split(double* A, int64_t lda, Dim nd, const int64_t* rdev,
+                                     int64_t k0, int b, const double* Z, const int32_t* E,
+                                     int n_mod, int beta, void* RL, int64_t rl_rows,
+                                     int64_t rl_kpad, cudaStream_t s);
 
 // gemm_fp64.cu
 cudaError_t launch_dgemm(const GemmParams& p, bool transA, bool transB, cudaStream_t s);

@@ -18,6 +18,7 @@
 #include <unordered_map>
 
 #include "../../include/cpinv.h"
+#include "kernels.h"
 
 namespace {
 
@@ -65,6 +66,8 @@ extern "C" int cpinv_pinv_static(const double* G, int64_t m, int64_t n, int64_t 
   }
   // The pipeline clears the per-call state it reads before writing it (the
   // rank, status and tolerance record is zeroed on the stream first), so the
-  // previous call's contents of the array do no harm.
+  // previous call's contents of the array do no harm.  Kernels are launched
+  // directly: no CUDA graph is instantiated on this path.
+  cpinv::NoGraphScope direct_launches;
   return cpinv_pinv(G, m, n, ldg, Gp, ldgp, scratch, kScratchBytes, o, rank_out, stream);
 }

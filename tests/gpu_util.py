@@ -15,6 +15,26 @@ import torch
 #: FP64 form is held to 1e-9.
 TOL = {"exact": 1e-10, "fp64": 1e-9}
 
+U = 2.0 ** -53
+
+
+def tol_for(mode, G, rank=None):
+    """The stated bar, widened where the input itself is ill-conditioned.
+
+    The method solves through G'G, so a rounding of relative size u anywhere
+    before the inverse moves G+ by about u kappa(G)^2 (kappa over the non-zero
+    singular values); two correct FP64-class evaluations of the method differ
+    by up to a small multiple of that (measured: 0.13 .. 1.1 u kappa^2 on the
+    test inputs).  Inputs with kappa(G) below ~1e3 (the benchmark input:
+    kappa ~ 60) keep the stated bar."""
+    s = np.linalg.svd(np.asarray(G, dtype=np.float64), compute_uv=False)
+    if rank is None:
+        rank = int(np.sum(s > s[0] * 1e-8)) if s.size and s[0] > 0 else 0
+    if rank == 0:
+        return TOL[mode]
+    kappa = s[0] / s[rank - 1]
+    return max(TOL[mode], 8.0 * U * kappa * kappa)
+
 
 def rel(a, b):
     nb = np.linalg.norm(b)

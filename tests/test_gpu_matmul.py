@@ -107,3 +107,21 @@ def test_exact_slice_nonfinite(cp):
     with pytest.raises(cp.CpinvError) as e:
         _run(cp, A, A, False, False, "exact")
     assert e.value.status == 2
+
+
+@pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True)])
+@pytest.mark.parametrize("M,N,K", [(130, 70, 300), (256, 384, 5000), (129, 257, 65)])
+def test_split_bf16x3_error_bound(cp, ta, tb, M, N, K):
+    """BF16x3 split precision: hi*hi + hi*lo + lo*hi with hi, lo the BF16
+    parts of each scaled operand and FP32 sums; |error| <= 2^-13 (|A| |B|)."""
+    g = np.random.default_rng(M + 3 * N + 5 * K)
+    opA = g.standard_normal((M, K))
+    opB = g.standard_normal((K, N))
+    A = opA.T.copy() if ta else opA
+    B = opB.T.copy() if tb else opB
+    C = _run(cp, A, B, ta, tb, "bf16x3")
+    X = _exact(opA, opB)
+    bound = np.abs(opA) @ np.abs(opB)
+    assert np.all(np.abs(C - X) <= 2.0 ** -13 * bound)
+    # and it is not secretly an FP64 product: the error is far above FP64's
+    assert np.max(np.abs(C - X) / bound) > 1e-10
