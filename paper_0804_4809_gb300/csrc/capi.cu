@@ -335,6 +335,7 @@ cudaError_t matmul(const Ctx& c, Site site, const double* A, int64_t lda, bool t
                    int64_t ldb, bool tb, double* C, int64_t ldc, Dim M, Dim N, Dim K,
                    double alpha, double beta, int lower) {
   GemmParams g;
+  std::memset(&g, 0, sizeof(g));
   g.A = A;
   g.B = B;
   g.C = C;
@@ -482,24 +483,62 @@ int front_rank(const Ctx& c, const double* G, int64_t ldg, bool compact) {
   return CPINV_OK;
 }
 
-// W[lo:hi, lo:hi] = U[lo:hi, lo:hi]^-1 for the lower-triangular U in bufA,
-// given the inverted diagonal blocks already in W:  split at mid,
-//   W21 = -W22 (U21 W11)     (bufM holds U21 W11)
-int tri_inverse(const Ctx& c, int64_t lo, int64_t hi) {
+// W = U^-1 for the lower-triangular U (order r <= nA) in bufA, given the
+// inverted b x b diagonal blocks already in W.  Recursive halving, done level
+// by level from the smallest blocks up: a node [lo, lo + 2s) with children
+// [lo, mid) and [mid, mid + s) gets
+//   W21 = -W22 (U21 W11)        (bufM holds U21 W11)
+// All nodes of a level have the same size (the block count is padded to a
+// power of two; nodes past the rank are empty), so a level is one batched
+// FP64 launch per product when its products are small, and per-node
+// tensor-core products when they are large.
+int tri_inverse(const Ctx& c) {
   const Plan& p = *c.p;
   const int64_t nA = p.nA, b = p.b;
-  if (hi - lo <= b) return CPINV_OK;
-  const int64_t blocks = (hi - lo + b - 1) / b;  // >= 2
-  const int64_t mid = lo + (blocks / 2) * b;      // lo < mid < hi
-  int rc = tri_inverse(c, lo, mid);
-  if (rc) return rc;
-  rc = tri_inverse(c, mid, hi);
-  if (rc) return rc;
-  const Dim rows = rdim(-mid, hi - mid), cols = rdim(-lo, mid - lo);
-  CK(matmul(c, S_PROD, p.bufA + mid * nA + lo, nA, false, p.bufW + lo * nA + lo, nA, false,
-            p.bufM + mid * nA + lo, nA, rows, cols, cols, 1.0, 0.0, 0));
-  CK(matmul(c, S_PROD, p.bufW + mid * nA + mid, nA, false, p.bufM + mid * nA + lo, nA, false,
-            p.bufW + mid * nA + lo, nA, rows, cols, rows, -1.0, 0.0, 0));
+  int64_t nb = 1;
+  while (nb * b < nA) nb <<= 1;
+  for (int64_t s = b; s < nb * b; s <<= 1) {
+    const int64_t nodes = (nb * b) / (2 * s);
+    const Dim rows = rdim(-s, s), cols = rdim(0, s);  // node 0: mid = s, lo = 0
+    if (prod_kind(p, S_PROD, s, s, s) == PK_FP64) {
+      auto batched = [&](const double* A, const double* B, double* C, Dim M, Dim N, Dim K,
+                         double alpha) -> cudaError_t {
+        GemmParams g;
+        std::memset(&g, 0, sizeof(g));
+        g.A = A;
+        g.B = B;
+        g.C = C;
+        g.lda = g.ldb = g.ldc = nA;
+        g.M = M;
+        g.N = N;
+        g.K = K;
+        g.alpha = alpha;
+        g.beta = 0.0;
+        g.rdev = c.rdev();
+        // node z: lo = 2 s z, mid = lo + s (row and column offsets move by 2s)
+        g.zA = g.zB = g.zC = 2 * s * nA + 2 * s;
+        g.zM = g.zN = g.zK = (int32_t)(-2 * s);
+        g.nz = (int32_t)nodes;
+        KernelTimer t;
+        t.gemm = &g;
+        return t.run(KT_GEMM_FP64, c.s, [&] { return launch_dgemm(g, false, false, c.s); });
+      };
+      // Tmp = U21 W11:  (rows mid.., cols lo..)
+      CK(batched(p.bufA + s * nA, p.bufW, p.bufM + s * nA, rows, cols, cols, 1.0));
+      // W21 = -W22 Tmp
+      CK(batched(p.bufW + s * nA + s, p.bufM + s * nA, p.bufW + s * nA, rows, cols, rows, -1.0));
+    } else {
+      for (int64_t z = 0; z < nodes; ++z) {
+        const int64_t lo = 2 * s * z, mid = lo + s;
+        if (mid >= nA) break;
+        const Dim rz = rdim(-mid, s), cz = rdim(-lo, s);
+        CK(matmul(c, S_PROD, p.bufA + mid * nA + lo, nA, false, p.bufW + lo * nA + lo, nA, false,
+                  p.bufM + mid * nA + lo, nA, rz, cz, cz, 1.0, 0.0, 0));
+        CK(matmul(c, S_PROD, p.bufW + mid * nA + mid, nA, false, p.bufM + mid * nA + lo, nA, false,
+                  p.bufW + mid * nA + lo, nA, rz, cz, rz, -1.0, 0.0, 0));
+      }
+    }
+  }
   return CPINV_OK;
 }
 
@@ -518,7 +557,7 @@ int front_inverse(const Ctx& c) {
   CK(KernelTimer().run(KT_AUX, c.s, [&] {
     return launch_tri_inv_init(p.bufW, nA, nA, c.rdev(), p.Tinv, b, c.s);
   }));
-  rc = tri_inverse(c, 0, nA);
+  rc = tri_inverse(c);
   if (rc) return rc;
   // M = W'W (full, symmetric)
   CK(matmul(c, S_PROD, p.bufW, nA, true, p.bufW, nA, false, p.bufM, nA, R, R, R, 1.0, 0.0, 0));

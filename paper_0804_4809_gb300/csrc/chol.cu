@@ -238,23 +238,23 @@ __global__ void __launch_bounds__(1024) diag32_kernel(double* A, int64_t lda, Di
     if (ok_s && j > c && i >= j && i < bw) a = fma(-colc[i], colc[j], a);
     __syncthreads();
   }
-  // a = L(i, j) for j <= i (rejected columns zero)
-  Ls[i][j] = in ? a : 0.0;
+  // a = L(i, j) for j <= i (rejected columns zero).  The inverse below works
+  // on T~(i, k) = T(i, k) / T(k, k) of the patched factor T (rejected rows
+  // are identity rows): with r the running right-hand side, r_i -= T~(i, k) r_k
+  // once r_k is final, and W(i, j) = r_i / T(i, i) at the end.
+  Ls[i][j] = (in && acc[i]) ? a * dinv[j] : 0.0;
   __syncthreads();
 
-  // warp j: column j of W = inverse of the patched factor (rejected rows are
-  // identity rows), by forward substitution; lane i holds W(i, j).
+  // warp j: column j of W = inverse of the patched factor, by forward
+  // substitution with shuffles only; lane i ends with W(i, j).
   double w = 0.0;
   if (j < bw) {
     double r = (i == j) ? 1.0 : 0.0;
     for (int k = j; k < bw; ++k) {
-      const double wk = __shfl_sync(0xffffffffu, r, k) * dinv[k];
-      if (i == k) w = wk;
-      if (i > k) {
-        const double tik = acc[i] ? Ls[i][k] : 0.0;
-        r = fma(-tik, wk, r);
-      }
+      const double rk = __shfl_sync(0xffffffffu, r, k);
+      if (i > k) r = fma(-Ls[i][k], rk, r);
     }
+    if (i >= j && i < bw) w = r * dinv[i];
   }
   if (i < bw && j < bw) {
     if (j <= i) A[(k0 + i) * lda + (k0 + j)] = a;

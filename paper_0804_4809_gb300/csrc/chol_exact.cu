@@ -41,18 +41,24 @@ __global__ void rowscale_kernel(const double* A, int64_t lda, Dim nd, const int6
 // Rows [k0, n) of panel k0: below the diagonal block, L(i, P) = A(i, P) Z (in
 // place); every row of the panel (diagonal block included) is then cut into
 // residues with the row scale E[i] and written to RL[j][i][k0 + c].
-// One 32 x 32 thread block per 32 rows; thread (ri, c).
-__global__ void __launch_bounds__(1024) panel_solve_split_kernel(
+// One 8-row x 32-column block of threads per 8 rows (many CTAs: the FP64
+// pipe of each SM is narrow).
+constexpr int kPanelRows = 8;
+
+__global__ void __launch_bounds__(256) panel_solve_split_kernel(
     double* A, int64_t lda, Dim nd, const int64_t* rdev, int64_t k0, int b, const double* Z,
     const int32_t* E, int n_mod, int beta, __nv_bfloat16* RL, int64_t rl_rows, int64_t rl_kpad) {
   const int64_t n = eval_dim(nd, rdev);
   if (k0 >= n) return;
   const int bw = (int)((n - k0) < b ? (n - k0) : b);
   __shared__ double Zs[32][33];
-  __shared__ double Arow[32][33];
+  __shared__ double Arow[kPanelRows][33];
   const int ri = threadIdx.x >> 5, c = threadIdx.x & 31;
-  const int64_t i = k0 + (int64_t)blockIdx.x * 32 + ri;
-  if (ri < bw && c < bw) Zs[ri][c] = Z[ri * b + c];
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int zr = e >> 5, zc = e & 31;
+    Zs[zr][zc] = (zr < bw && zc < bw) ? Z[zr * b + zc] : 0.0;
+  }
+  const int64_t i = k0 + (int64_t)blockIdx.x * kPanelRows + ri;
   const bool row_ok = i < n;
   const bool below = i >= k0 + bw;
   double v = 0.0;
@@ -95,7 +101,7 @@ cudaError_t launch_panel_solve_split(double* A, int64_t lda, Dim nd, const int64
   if (b > 32) return cudaErrorInvalidValue;
   const int64_t rows = nd.max - k0;
   if (rows <= 0) return cudaSuccess;
-  panel_solve_split_kernel<<<(unsigned)((rows + 31) / 32), 1024, 0, s>>>(
+  panel_solve_split_kernel<<<(unsigned)((rows + kPanelRows - 1) / kPanelRows), 256, 0, s>>>(
       A, lda, nd, rdev, k0, b, Z, E, n_mod, beta, (__nv_bfloat16*)RL, rl_rows, rl_kpad);
   return cudaGetLastError();
 }

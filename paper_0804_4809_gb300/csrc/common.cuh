@@ -54,6 +54,10 @@ struct GemmParams {
   const int64_t* rdev;  // device rank, read when a Dim has sel = 1
   int32_t lower;        // 1: only C(i, j) with i >= j is computed and written
   int32_t pad;          // FP64 path: 1 if C aliases A or B (whole-row tiles)
+  // batch of nz products (FP64 path): product z uses A + z*zA, B + z*zB,
+  // C + z*zC and dimension offsets M.off + z*zM, N.off + z*zN, K.off + z*zK
+  int64_t zA, zB, zC;
+  int32_t zM, zN, zK, nz;
 };
 
 }  // namespace cpinv

@@ -46,5 +46,25 @@ __device__ __forceinline__ void store_residues(uint64_t a, bool neg, int n_mod, 
   }
 }
 
+// BF16 bits of a small integer |v| <= 64 (exact): the float with those bits is
+// formed by adding v to 1.5 * 2^23 in the integer domain and subtracting it
+// back in FP32 (exact), and its top 16 bits are the BF16 encoding.
+__device__ __forceinline__ uint32_t small_int_bf16_bits(int v) {
+  const float f = __int_as_float(0x4B400000 + v) - 12582912.0f;
+  return __float_as_uint(f) >> 16;
+}
+
+// Balanced residue of (neg ? -a : a) modulo the j-th modulus, from the three
+// 21-bit chunks of a < 2^63 (one reduction of a value below 2^29).
+template <int J>
+__device__ __forceinline__ int residue21(uint32_t a0, uint32_t a1, uint32_t a2, bool neg) {
+  constexpr uint32_t p = (uint32_t)modulus(J);
+  constexpr uint32_t c1 = (uint32_t)((1ull << 21) % p);
+  constexpr uint32_t c2 = (uint32_t)((1ull << 42) % p);
+  uint32_t r = (a2 * c2 + a1 * c1 + a0) % p;
+  if (neg && r) r = p - r;
+  return (int)r > (int)(p / 2) ? (int)r - (int)p : (int)r;
+}
+
 }  // namespace crt
 }  // namespace cpinv

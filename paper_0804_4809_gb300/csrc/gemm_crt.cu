@@ -22,6 +22,8 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "common.cuh"
 #include "crt.h"
@@ -180,42 +182,72 @@ __global__ void row_expo_kernel(const double* X, int64_t ld, int trans, Dim rows
   if (bad) atomicOr(&st->status, ST_NONFINITE);
 }
 
-// residues of the 32x32 tile (rows i0.., k0..) of op(X); one thread per element
+// Residue planes of the 32-row x 64-column tile (rows i0.., k0..) of op(X):
+// 256 threads, each four rows x two adjacent columns, so that every modulus is
+// written as one 32-bit word (two BF16) per thread and row.
+template <int J>
+__device__ __forceinline__ void split_store(const uint32_t (&c0)[3], bool n0, const uint32_t (&c1)[3],
+                                            bool n1, int n_mod, uint32_t* dst, size_t plane_words) {
+  if (J >= n_mod) return;
+  const uint32_t lo = crt::small_int_bf16_bits(crt::residue21<J>(c0[0], c0[1], c0[2], n0));
+  const uint32_t hi = crt::small_int_bf16_bits(crt::residue21<J>(c1[0], c1[1], c1[2], n1));
+  dst[J * plane_words] = lo | (hi << 16);
+}
+
+template <int... Js>
+__device__ __forceinline__ void split_store_all(std::integer_sequence<int, Js...>,
+                                                const uint32_t (&c0)[3], bool n0,
+                                                const uint32_t (&c1)[3], bool n1, int n_mod,
+                                                uint32_t* dst, size_t plane_words) {
+  (split_store<Js>(c0, n0, c1, n1, n_mod, dst, plane_words), ...);
+}
+
 __global__ void __launch_bounds__(256) split_kernel(const double* X, int64_t ld, int trans,
                                                     Dim rowsd, Dim colsd, int64_t rows_max,
                                                     int64_t kpad, const int64_t* rdev,
                                                     const int32_t* E, int n_mod, int beta,
                                                     bf16* out) {
-  __shared__ uint64_t tile[32][33];
+  __shared__ uint64_t tile[32][65];
   const int64_t rows = eval_dim(rowsd, rdev), cols = eval_dim(colsd, rdev);
-  const int64_t i0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
+  const int64_t i0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 64;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-  // load: element (i, k) of op(X)
-  for (int q = ty; q < 32; q += 8) {
-    uint64_t v = 0;
-    if (!trans) {
-      const int64_t i = i0 + q, k = k0 + tx;
-      if (i < rows && k < cols) v = reinterpret_cast<const uint64_t*>(X)[i * ld + k];
-      tile[q][tx] = v;
-    } else {
+  const uint64_t* Xb = reinterpret_cast<const uint64_t*>(X);
+  if (!trans) {
+    for (int q = ty; q < 32; q += 8)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t i = i0 + q, k = k0 + tx + 32 * h;
+        tile[q][tx + 32 * h] = (i < rows && k < cols) ? Xb[i * ld + k] : 0ull;
+      }
+  } else {
+    for (int q = ty; q < 64; q += 8) {
       const int64_t k = k0 + q, i = i0 + tx;
-      if (i < rows && k < cols) v = reinterpret_cast<const uint64_t*>(X)[k * ld + i];
-      tile[tx][q] = v;
+      tile[tx][q] = (i < rows && k < cols) ? Xb[k * ld + i] : 0ull;
     }
   }
   __syncthreads();
-  const size_t plane = (size_t)rows_max * (size_t)kpad;
-  for (int q = ty; q < 32; q += 8) {
-    const int64_t i = i0 + q, k = k0 + tx;
-    if (i >= rows_max || k >= kpad) continue;
-    const uint64_t b = tile[q][tx];
-    uint64_t a = 0;
-    bool neg = false;
-    if (i < rows && k < cols && !nonfinite_bits(b)) {
-      a = crt::integerize(b, E[i], beta);
-      neg = (b >> 63) != 0;
+  const size_t plane_words = (size_t)rows_max * (size_t)kpad / 2;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int q = ty + 8 * u;
+    const int64_t i = i0 + q;
+    if (i >= rows_max) continue;
+    const int Ei = i < rows ? E[i] : 0;
+    uint32_t c[2][3];
+    bool neg[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint64_t b = tile[q][2 * tx + h];
+      uint64_t a = 0;
+      if (!nonfinite_bits(b)) a = crt::integerize(b, Ei, beta);
+      neg[h] = (b >> 63) != 0;
+      c[h][0] = (uint32_t)(a & 0x1FFFFF);
+      c[h][1] = (uint32_t)((a >> 21) & 0x1FFFFF);
+      c[h][2] = (uint32_t)(a >> 42);
     }
-    crt::store_residues(a, neg, n_mod, out + (size_t)i * kpad + k, plane);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(out + (size_t)i * kpad + k0) + tx;
+    split_store_all(std::make_integer_sequence<int, crt::kMaxMod>{}, c[0], neg[0], c[1], neg[1],
+                    n_mod, dst, plane_words);
   }
 }
 
@@ -546,7 +578,7 @@ __global__ void __launch_bounds__(192, 1)
           uint32_t v[32];
           tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c), v);
           if (!rowok) continue;
-#pragma unroll 4
+#pragma unroll
           for (int e = 0; e < 32; ++e) {
             const int64_t col = n0 + c + e;
             if (col >= Nv || (p.lower && col > row)) continue;
@@ -665,114 +697,180 @@ __device__ __forceinline__ double compose_double(bool neg, const uint32_t (&mag)
   return __longlong_as_double((long long)bits);
 }
 
-__global__ void __launch_bounds__(256) reconstruct_kernel(ReconParams p,
-                                                          const __grid_constant__ crt::Consts c) {
-  __shared__ uint8_t tab[crt::kMaxMod][128];
-  for (int e = threadIdx.x; e < c.n * 128; e += blockDim.x) tab[e / 128][e % 128] = c.tab[e / 128][e % 128];
-  __syncthreads();
-  const int64_t M = eval_dim(p.M, p.rdev), N = eval_dim(p.N, p.rdev);
-  const int64_t total = M * N;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = idx / N, j = idx % N;
-    if (p.lower && j > i) continue;
-    uint64_t acc[crt::kLimbs] = {0, 0, 0, 0, 0};
-    const uint8_t* r = p.R + i * p.Npad + j;
-    const size_t plane = (size_t)p.Mpad * (size_t)p.Npad;
-    for (int m = 0; m < c.n; ++m) {
-      const uint32_t t = tab[m][r[m * plane]];
+// CRT constants of every moduli count, in device memory (uploaded once per
+// device): blocks read them with coalesced loads.
+__device__ crt::Consts g_crt_consts[crt::kMaxMod + 1];
+
+// select S[k] for a uniform runtime k without local memory
+__device__ __forceinline__ uint32_t limb_at(const uint32_t (&S)[crt::kLimbs], int k) {
+  uint32_t w = 0;
 #pragma unroll
-      for (int l = 0; l < crt::kLimbs; ++l) acc[l] += (uint64_t)t * c.Mj[m][l];
-    }
-    uint32_t S[crt::kLimbs];
-    uint64_t carry = 0;
+  for (int l = 0; l < crt::kLimbs; ++l) w = (l == k) ? S[l] : w;
+  return w;
+}
+
+struct CrtShared {
+  uint8_t tab[crt::kMaxMod][128];
+  uint32_t Mj[crt::kMaxMod][crt::kLimbs];
+  uint32_t P[crt::kLimbs];
+  uint32_t halfP[crt::kLimbs];
+};
+
+// S (the CRT sum, < n P) -> centred X = S mod P in (-P/2, P/2] -> FP64,
+// correctly rounded, times 2^scale.
+__device__ __forceinline__ double crt_finish(const uint32_t (&S)[crt::kLimbs],
+                                             const uint32_t* P, const uint32_t* halfP, int shift,
+                                             float inv_ptop, int scale) {
+  // q = floor(S / P) in [0, n): estimate from the top bits, then correct
+  uint64_t stop = 0;
 #pragma unroll
-    for (int l = 0; l < crt::kLimbs; ++l) {
-      const uint64_t v = acc[l] + carry;
-      S[l] = (uint32_t)v;
-      carry = v >> 32;
-    }
-    // q = floor(S / P) in [0, n): estimate from the top bits, then correct
-    uint64_t stop = 0;
+  for (int b = 0; b < 2; ++b) {
+    const int pos = shift + 32 * b;  // 32-bit chunk of S >> shift
+    const int li = pos >> 5, off = pos & 31;
+    uint32_t w = limb_at(S, li) >> off;
+    if (off) w |= limb_at(S, li + 1) << (32 - off);
+    stop |= (uint64_t)w << (32 * b);
+  }
+  int qe = (int)floorf((float)stop * inv_ptop);
+  qe = qe < 0 ? 0 : qe;
+  // X = S - qe * P  (signed, two's complement over the limbs)
+  int64_t borrow = 0;
+  uint32_t X[crt::kLimbs];
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      const int pos = c.shift + 32 * b;  // 32-bit chunk of S >> shift
-      const int li = pos >> 5, off = pos & 31;
-      uint32_t w = 0;
-      if (li < crt::kLimbs) w = S[li] >> off;
-      if (off && li + 1 < crt::kLimbs) w |= S[li + 1] << (32 - off);
-      stop |= (uint64_t)w << (32 * b);
-    }
-    int qe = (int)floorf((float)stop * c.inv_ptop);
-    qe = qe < 0 ? 0 : qe;
-    // X = S - qe * P  (signed, two's complement over the limbs)
-    int64_t borrow = 0;
-    uint32_t X[crt::kLimbs];
+  for (int l = 0; l < crt::kLimbs; ++l) {
+    const int64_t v = (int64_t)S[l] - (int64_t)((uint64_t)qe * P[l]) + borrow;
+    X[l] = (uint32_t)v;
+    borrow = v >> 32;  // arithmetic
+  }
+  // fix-up: bring X into [0, P) (the estimate is off by at most one)
 #pragma unroll
-    for (int l = 0; l < crt::kLimbs; ++l) {
-      const int64_t v = (int64_t)S[l] - (int64_t)((uint64_t)qe * c.P[l]) + borrow;
-      X[l] = (uint32_t)v;
-      borrow = v >> 32;  // arithmetic
-    }
-    // fix-up: bring X into [0, P)
-    for (int pass = 0; pass < 2; ++pass) {
-      if ((int32_t)X[crt::kLimbs - 1] < 0) {  // X < 0: X += P
-        uint64_t cc = 0;
-#pragma unroll
-        for (int l = 0; l < crt::kLimbs; ++l) {
-          const uint64_t v = (uint64_t)X[l] + c.P[l] + cc;
-          X[l] = (uint32_t)v;
-          cc = v >> 32;
-        }
-      } else {
-        // X >= P ?
-        bool ge = true;
-#pragma unroll
-        for (int l = crt::kLimbs - 1; l >= 0; --l) {
-          if (X[l] != c.P[l]) {
-            ge = X[l] > c.P[l];
-            break;
-          }
-        }
-        if (ge) {
-          int64_t bb = 0;
-#pragma unroll
-          for (int l = 0; l < crt::kLimbs; ++l) {
-            const int64_t v = (int64_t)X[l] - (int64_t)c.P[l] + bb;
-            X[l] = (uint32_t)v;
-            bb = v >> 32;
-          }
-        }
-      }
-    }
-    // centre: X > P/2 -> X - P (negative); magnitude and sign
-    bool gt = false;
-#pragma unroll
-    for (int l = crt::kLimbs - 1; l >= 0; --l) {
-      if (X[l] != c.halfP[l]) {
-        gt = X[l] > c.halfP[l];
-        break;
-      }
-    }
-    uint32_t mag[crt::kLimbs];
-    if (gt) {  // |X - P| = P - X
-      int64_t bb = 0;
+  for (int pass = 0; pass < 1; ++pass) {
+    if ((int32_t)X[crt::kLimbs - 1] < 0) {  // X < 0: X += P
+      uint64_t cc = 0;
 #pragma unroll
       for (int l = 0; l < crt::kLimbs; ++l) {
-        const int64_t v = (int64_t)c.P[l] - (int64_t)X[l] + bb;
-        mag[l] = (uint32_t)v;
-        bb = v >> 32;
+        const uint64_t v = (uint64_t)X[l] + P[l] + cc;
+        X[l] = (uint32_t)v;
+        cc = v >> 32;
       }
     } else {
+      bool ge = true, decided = false;  // X >= P ?
 #pragma unroll
-      for (int l = 0; l < crt::kLimbs; ++l) mag[l] = X[l];
+      for (int l = crt::kLimbs - 1; l >= 0; --l) {
+        if (!decided && X[l] != P[l]) {
+          ge = X[l] > P[l];
+          decided = true;
+        }
+      }
+      if (ge) {
+        int64_t bb = 0;
+#pragma unroll
+        for (int l = 0; l < crt::kLimbs; ++l) {
+          const int64_t v = (int64_t)X[l] - (int64_t)P[l] + bb;
+          X[l] = (uint32_t)v;
+          bb = v >> 32;
+        }
+      }
     }
-    const int scale = (p.EA[i] - 1022 - p.betaA) + (p.EB[j] - 1022 - p.betaB);
-    double v = compose_double(gt, mag, scale);
-    double* cp = p.C + i * p.ldc + j;
-    if (p.alpha != 1.0) v *= p.alpha;
-    if (p.beta != 0.0) v = fma(p.beta, *cp, v);
-    *cp = v;
+  }
+  // centre: X > P/2 -> X - P (negative); magnitude and sign
+  bool gt = false, decided = false;
+#pragma unroll
+  for (int l = crt::kLimbs - 1; l >= 0; --l) {
+    if (!decided && X[l] != halfP[l]) {
+      gt = X[l] > halfP[l];
+      decided = true;
+    }
+  }
+  uint32_t mag[crt::kLimbs];
+  int64_t bb = 0;
+#pragma unroll
+  for (int l = 0; l < crt::kLimbs; ++l) {
+    const int64_t v = (int64_t)P[l] - (int64_t)X[l] + bb;
+    mag[l] = gt ? (uint32_t)v : X[l];
+    bb = v >> 32;
+  }
+  return compose_double(gt, mag, scale);
+}
+
+// Two adjacent columns per thread: the residue bytes of a modulus come in one
+// 16-bit load and each multiplier P/p_j is read once for both sums.
+constexpr int kRecW = 2;
+
+__global__ void __launch_bounds__(256, 2) reconstruct_kernel(ReconParams p, int n_mod) {
+  const crt::Consts& c = g_crt_consts[n_mod];
+  __shared__ CrtShared sh;
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&c.tab[0][0]);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&sh.tab[0][0]);
+    for (int e = threadIdx.x; e < n_mod * 32; e += blockDim.x) dst[e] = src[e];
+    for (int e = threadIdx.x; e < n_mod * crt::kLimbs; e += blockDim.x)
+      sh.Mj[e / crt::kLimbs][e % crt::kLimbs] = c.Mj[e / crt::kLimbs][e % crt::kLimbs];
+  }
+  __syncthreads();
+  if (threadIdx.x < crt::kLimbs) {
+    sh.P[threadIdx.x] = c.P[threadIdx.x];
+    sh.halfP[threadIdx.x] = c.halfP[threadIdx.x];
+  }
+  __syncthreads();
+  const int n = n_mod;
+  const int shift = c.shift;
+  const float inv_ptop = c.inv_ptop;
+  const int64_t M = eval_dim(p.M, p.rdev), N = eval_dim(p.N, p.rdev);
+  const int64_t NG = (N + kRecW - 1) / kRecW;  // column groups
+  const int64_t total = M * NG;
+  const size_t plane = (size_t)p.Mpad * (size_t)p.Npad;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / NG, j0 = (idx - i * NG) * kRecW;
+    if (p.lower && j0 > i) continue;
+    const uint16_t* r = reinterpret_cast<const uint16_t*>(p.R + i * p.Npad + j0);
+    uint64_t acc[kRecW][crt::kLimbs];
+#pragma unroll
+    for (int e = 0; e < kRecW; ++e)
+#pragma unroll
+      for (int l = 0; l < crt::kLimbs; ++l) acc[e][l] = 0;
+    // residues in groups of eight loads in flight, then their sums
+#pragma unroll
+    for (int m0 = 0; m0 < crt::kMaxMod; m0 += 8) {
+      uint32_t rv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) rv[q] = (m0 + q) < n ? r[(m0 + q) * (plane / kRecW)] : 0u;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int m = m0 + q;
+        if (m < n) {
+          uint32_t mj[crt::kLimbs];
+#pragma unroll
+          for (int l = 0; l < crt::kLimbs; ++l) mj[l] = sh.Mj[m][l];
+#pragma unroll
+          for (int e = 0; e < kRecW; ++e) {
+            const uint32_t t = sh.tab[m][(rv[q] >> (8 * e)) & 0xFFu];
+#pragma unroll
+            for (int l = 0; l < crt::kLimbs; ++l) acc[e][l] += (uint64_t)t * mj[l];
+          }
+        }
+      }
+    }
+    const int sa = p.EA[i] - 1022 - p.betaA;
+#pragma unroll
+    for (int e = 0; e < kRecW; ++e) {
+      const int64_t j = j0 + e;
+      if (j >= N || (p.lower && j > i)) continue;
+      uint32_t S[crt::kLimbs];
+      uint64_t carry = 0;
+#pragma unroll
+      for (int l = 0; l < crt::kLimbs; ++l) {
+        const uint64_t v = acc[e][l] + carry;
+        S[l] = (uint32_t)v;
+        carry = v >> 32;
+      }
+      double v = crt_finish(S, sh.P, sh.halfP, shift, inv_ptop, sa + p.EB[j] - 1022 - p.betaB);
+      double* cp = p.C + i * p.ldc + j;
+      if (p.alpha != 1.0) v *= p.alpha;
+      if (p.beta != 0.0) v = fma(p.beta, *cp, v);
+      *cp = v;
+    }
   }
 }
 
@@ -876,7 +974,7 @@ cudaError_t crt_row_exponents(const double* X, int64_t ld, int tview, Dim rows, 
 cudaError_t crt_split(const double* X, int64_t ld, int tview, Dim rows, Dim K, const int64_t* rdev,
                       int64_t rows_max, int64_t kpad, const int32_t* E, int n_mod, int beta,
                       void* out, cudaStream_t s, KernelTimer* timer) {
-  dim3 grid((unsigned)(kpad / 32), (unsigned)((rows_max + 31) / 32));
+  dim3 grid((unsigned)(kpad / 64), (unsigned)((rows_max + 31) / 32));
   return timer->run(KT_SPLIT, s, [&] {
     split_kernel<<<grid, 256, 0, s>>>(X, ld, tview, rows, K, rows_max, kpad, rdev, E, n_mod, beta,
                                       (bf16*)out);
@@ -890,7 +988,7 @@ cudaError_t crt_mma(const void* SA, int64_t a_rows, int a_row0, const void* SB, 
                     int32_t* status, cudaStream_t s, KernelTimer* timer, const GemmParams* fl) {
   const int64_t Mmax = M.max, Nmax = N.max;
   if (Mmax <= 0 || Nmax <= 0) return cudaSuccess;
-  const int BN = (Nmax >= 2048) ? 256 : 128;
+  const int BN = (Nmax >= 2048) ? 256 : (Nmax <= 32 ? 32 : 128);
   CUtensorMap ta, tb;
   if (!make_map(&ta, (const bf16*)SA, kpad, a_rows, n_mod, BM)) return cudaErrorInvalidValue;
   if (!make_map(&tb, (const bf16*)SB, kpad, b_rows, n_mod, BN)) return cudaErrorInvalidValue;
@@ -909,17 +1007,21 @@ cudaError_t crt_mma(const void* SA, int64_t a_rows, int a_row0, const void* SB, 
   mp.Mpad = Mpad;
   mp.Npad = Npad;
   mp.status = status;
-  const int64_t tiles = ((Mmax + BM - 1) / BM) * ((Nmax + BN - 1) / BN) / (lower ? 2 : 1);
-  int mpc = n_mod;
-  while (mpc > 1 && (tiles > 0 ? tiles : 1) * ((n_mod + mpc - 1) / mpc) < 2 * 152)
-    mpc = (mpc + 1) / 2;
-  mp.mods_per_cta = mpc;
+  // CTAs: about one wave of (tile, group of moduli); a CTA runs its moduli
+  // back to back (double-buffered accumulators), amortising its set-up
+  int64_t tiles = ((Mmax + BM - 1) / BM) * ((Nmax + BN - 1) / BN) / (lower ? 2 : 1);
+  if (tiles < 1) tiles = 1;
+  int64_t groups = (152 + tiles - 1) / tiles;
+  if (groups > n_mod) groups = n_mod;
+  if (groups < 1) groups = 1;
+  mp.mods_per_cta = (int)((n_mod + groups - 1) / groups);
   KernelTimer mt = *timer;
   mt.gemm = fl;
   mt.flops_mult = (double)n_mod;
   return mt.run(KT_MMA, s, [&] {
-    return BN == 256 ? launch_mma<256, 4, false>(ta, tb, mp, Mmax, Nmax, s)
-                     : launch_mma<128, 6, false>(ta, tb, mp, Mmax, Nmax, s);
+    if (BN == 256) return launch_mma<256, 4, false>(ta, tb, mp, Mmax, Nmax, s);
+    if (BN == 32) return launch_mma<32, 8, false>(ta, tb, mp, Mmax, Nmax, s);
+    return launch_mma<128, 6, false>(ta, tb, mp, Mmax, Nmax, s);
   });
 }
 
@@ -927,14 +1029,22 @@ cudaError_t crt_reconstruct(const uint8_t* R, int64_t Mpad, int64_t Npad, Dim M,
                             const int64_t* rdev, const int32_t* EA, const int32_t* EB, int betaA,
                             int betaB, double alpha, double beta, double* C, int64_t ldc,
                             int lower, int n_mod, cudaStream_t s, KernelTimer* timer) {
-  static crt::Consts consts[crt::kMaxMod + 1];
-  static bool have[crt::kMaxMod + 1] = {false};
-  static std::mutex mu;
   {
+    // upload the tables of every moduli count once per device (outside any
+    // stream capture: the first call of an argument set always runs directly)
+    static std::mutex mu;
+    static std::vector<int> done;
     std::lock_guard<std::mutex> lock(mu);
-    if (!have[n_mod]) {
-      crt::make_consts(n_mod, &consts[n_mod]);
-      have[n_mod] = true;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    bool have = false;
+    for (int d : done) have |= (d == dev);
+    if (!have) {
+      static crt::Consts host[crt::kMaxMod + 1];
+      for (int k = 1; k <= crt::kMaxMod; ++k) crt::make_consts(k, &host[k]);
+      cudaError_t e = cudaMemcpyToSymbol(g_crt_consts, host, sizeof(host));
+      if (e != cudaSuccess) return e;
+      done.push_back(dev);
     }
   }
   ReconParams rp;
@@ -955,7 +1065,8 @@ cudaError_t crt_reconstruct(const uint8_t* R, int64_t Mpad, int64_t Npad, Dim M,
   rp.lower = lower;
   rp.pad = 0;
   return timer->run(KT_RECON, s, [&] {
-    reconstruct_kernel<<<grid1d(M.max * N.max, 256), 256, 0, s>>>(rp, consts[n_mod]);
+    reconstruct_kernel<<<grid1d(M.max * ((N.max + kRecW - 1) / kRecW), 256), 256, 0, s>>>(rp,
+                                                                                        n_mod);
     return cudaGetLastError();
   });
 }

@@ -21,6 +21,15 @@ constexpr int TK = 16;
 template <bool TA, bool TB, int T>
 __global__ void __launch_bounds__(256) dgemm_kernel(GemmParams p) {
   constexpr int U = T / 16;
+  if (blockIdx.z) {
+    const int64_t z = blockIdx.z;
+    p.A += z * p.zA;
+    p.B += z * p.zB;
+    p.C += z * p.zC;
+    p.M.off += z * p.zM;
+    p.N.off += z * p.zN;
+    p.K.off += z * p.zK;
+  }
   const int64_t M = eval_dim(p.M, p.rdev);
   const int64_t N = eval_dim(p.N, p.rdev);
   const int64_t K = eval_dim(p.K, p.rdev);
@@ -96,8 +105,9 @@ __global__ void __launch_bounds__(256) dgemm_kernel(GemmParams p) {
 
 template <int T>
 cudaError_t launch_tile(const GemmParams& p, bool transA, bool transB, cudaStream_t s) {
-  dim3 grid((unsigned)((p.N.max + T - 1) / T), (unsigned)((p.M.max + T - 1) / T));
-  if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+  dim3 grid((unsigned)((p.N.max + T - 1) / T), (unsigned)((p.M.max + T - 1) / T),
+            (unsigned)(p.nz > 1 ? p.nz : 1));
+  if (grid.y > 65535u || grid.z > 65535u) return cudaErrorInvalidConfiguration;
   if (!transA && !transB) dgemm_kernel<false, false, T><<<grid, 256, 0, s>>>(p);
   else if (!transA && transB) dgemm_kernel<false, true, T><<<grid, 256, 0, s>>>(p);
   else if (transA && !transB) dgemm_kernel<true, false, T><<<grid, 256, 0, s>>>(p);
@@ -118,7 +128,8 @@ cudaError_t launch_dgemm(const GemmParams& p, bool transA, bool transB, cudaStre
     if (Nmax <= 64) return launch_tile<64>(p, transA, transB, s);
     return cudaErrorInvalidValue;
   }
-  auto tiles = [&](int64_t t) { return ((Mmax + t - 1) / t) * ((Nmax + t - 1) / t); };
+  const int64_t nz = p.nz > 1 ? p.nz : 1;
+  auto tiles = [&](int64_t t) { return nz * ((Mmax + t - 1) / t) * ((Nmax + t - 1) / t); };
   if (tiles(64) >= 152 || (Mmax >= 64 && Nmax >= 64 && tiles(32) > 4 * 152))
     return launch_tile<64>(p, transA, transB, s);
   if (tiles(32) >= 152) return launch_tile<32>(p, transA, transB, s);
