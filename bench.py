@@ -289,6 +289,7 @@ def ours(args):
         outs[md] = o
     clocks = sampler.stop()
     e2e = run_e2e(modes[0], G_host, args.steps, device)
+    batched = batched_bench(args, device, flush) if (not args.no_batched and ws == 1) else None
 
     # max over ranks of the timed total
     head = modes[0]
@@ -357,22 +358,30 @@ def ours(args):
 
     # roofline of the dominant kernel (from the profiled pass, events on the launch stream)
     prof = results[head]["profile"]
-    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])[0] if prof else None
     peaks = measured_peaks()
-    if dom is not None:
-        p = prof[dom]
+    bf16_peak = peaks.get("bf16_tflops_sustained") or 1700.0
+    bf16_src = ("of measured (bf16 sustained, MEASURED_PEAKS)" if peaks.get("bf16_tflops_sustained")
+                else "of fallback (1.7 PFLOP/s bf16 sustained)")
+    fp64_src = "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (measured DFMA loop: 1.20)"
+    kinds = {"gemm_fp64": ("alu", FP64_PEAK_TFLOPS, fp64_src),
+             "diag_factor": ("alu", FP64_PEAK_TFLOPS, fp64_src),
+             "tc_mma": ("tensor", bf16_peak, bf16_src)}
+    total_ms = sum(v["ms"] for v in prof.values()) or 1.0
+
+    def roof(name):
+        p = prof[name]
+        bound, peak, src = kinds.get(name, ("alu", FP64_PEAK_TFLOPS, fp64_src))
         achieved = p["flops"] / (p["ms"] / 1e3) / 1e12 if p["ms"] > 0 else 0.0
-        if dom == "gemm_fp64":
-            bound, peak, src = "alu", FP64_PEAK_TFLOPS, "FP64 pipe: 152 SM x 2 DFMA/clk x 2.07 GHz"
-        else:
-            bound = "tensor"
-            peak = peaks.get("bf16_tflops_sustained") or 1700.0
-            src = "measured bf16 sustained" if peaks else "fallback"
-        line["roofline"] = {"kernel": dom, "bound": bound, "achieved": round(achieved, 4),
-                            "peak": round(peak, 4), "unit": "TFLOP/s",
-                            "frac": round(achieved / peak, 4), "traffic": None,
-                            "peak_source": src,
-                            "share_of_step": round(p["ms"] / sum(v["ms"] for v in prof.values()), 4)}
+        return {"kernel": name, "bound": bound, "achieved": round(achieved, 4),
+                "peak": round(peak, 4), "unit": "TFLOP/s", "frac": round(achieved / peak, 5),
+                "traffic": None, "peak_source": src, "launches": p["launches"],
+                "share_of_step": round(p["ms"] / total_ms, 4)}
+
+    if prof:
+        dom = max(prof.items(), key=lambda kv: kv[1]["ms"])[0]
+        line["roofline"] = roof(dom)
+        if "tc_mma" in prof and dom != "tc_mma":
+            line["roofline_tensor"] = roof("tc_mma")
     line["e2e"] = {"value": round(flops * K * ws / t_e2e / 1e12, 4), "unit": "TFLOP/s",
                    "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
                    "mode": modes[0]}
@@ -383,6 +392,8 @@ def ours(args):
                                 "kind": "oracle",
                                 "sample": f"{len(cpu['times'])} full pseudoinverse(s) of the same "
                                           f"4096x2048 input, median {t_cpu:.2f} s"}
+    if batched is not None:
+        line["batched"] = batched
     print(json.dumps(line), flush=True)
 
 
@@ -409,6 +420,109 @@ def gemm_bench(args):
     fl = 2.0 * N * M * N
     print(json.dumps({"workload": "C = K G' (2048x2048 @ 2048x4096)", "mode": mode,
                       "ms": round(t * 1e3, 4), "fp64_equiv_tflops": round(fl / t / 1e12, 3)}))
+
+
+# ---------------------------------------------------------------------------
+# batched uneven least squares (512 problems) against a per-matrix loop
+# ---------------------------------------------------------------------------
+
+BATCH = {"P": 512, "seed": 4, "k": 4}
+BATCH_WORKLOAD = ("512 rank-deficient problems, m~U{64..1024}, n~U{32..min(m,512)}, "
+                  "r~U{n/2..n}, G = A B N(0,1), k = 4, seed 4, gap-checked draws")
+
+
+def lstsq_flops(m: int, n: int, r: int, k: int) -> float:
+    """Algorithmic flops of one least-squares solve W = G+ F: Gram m n^2, G'F
+    2 m n k, full-rank Cholesky, L'L n r^2, inverse r^3, chain 4 n r k +
+    4 r^2 k."""
+    chol = n * r * r - 2.0 / 3.0 * r ** 3 + r * (n - r) ** 2
+    return float(m * n * n + 2 * m * n * k + chol + n * r * r + r ** 3 + 4 * n * r * k
+                 + 4 * r * r * k)
+
+
+def batch_problems():
+    from paper_0804_4809_gb300 import inputs
+    with open(os.path.join(ROOT, "tests", "golden", "batched_gap.json")) as fh:
+        att = {int(i): int(a) for i, a in json.load(fh)["attempts"].items()}
+    return inputs.batched_problems(BATCH["P"], BATCH["seed"], k=BATCH["k"], attempts=att)
+
+
+def batched_bench(args, device, flush, loop_steps: int = 2) -> dict:
+    """Device time of the whole batch (one CUDA-graph replay per step) and of
+    a loop of single-problem FP64 calls over the same problems."""
+    import ctypes
+
+    import torch
+
+    from paper_0804_4809_gb300 import cpinv
+    probs = batch_problems()
+    Gs = [torch.from_numpy(p.G).to(device) for p in probs]
+    Fs = [torch.from_numpy(p.F).to(device) for p in probs]
+    stream = torch.cuda.Stream(device)
+    sid = stream.cuda_stream
+    with torch.cuda.stream(stream):
+        plan = cpinv.BatchedLstsq(Gs, Fs)
+        _, ranks, st = plan(stream=sid)          # direct + panel tuning
+        for _ in range(max(2, args.warmup)):
+            plan(sync=False, stream=sid)          # capture, then replays
+        torch.cuda.synchronize()
+        l0 = cpinv.launch_count()
+        ms = time_steps(lambda: plan(sync=False, stream=sid), args.steps, flush, stream)
+        launches = (cpinv.launch_count() - l0) / args.steps
+        _, ranks2, st2 = plan(stream=sid)
+        # per-matrix loop: one cpinv_lstsq call per problem, same stream
+        o = cpinv.make_opts("fp64")
+        wsz = max(cpinv.lib().cpinv_lstsq_workspace_size(p.m, p.n, p.F.shape[1], ctypes.byref(o))
+                  for p in probs)
+        wsb = torch.empty(wsz, dtype=torch.uint8, device=device)
+        Wl = [torch.empty((p.n, p.F.shape[1]), dtype=torch.float64, device=device) for p in probs]
+
+        def loop():
+            for G, F, W, p in zip(Gs, Fs, Wl, probs):
+                rc = cpinv.lib().cpinv_lstsq(G.data_ptr(), p.m, p.n, p.n, F.data_ptr(),
+                                             p.F.shape[1], p.F.shape[1], W.data_ptr(),
+                                             p.F.shape[1], wsb.data_ptr(), wsz, ctypes.byref(o),
+                                             None, sid)
+                if rc:
+                    raise cpinv.CpinvError(rc, "per-matrix loop")
+
+        loop()
+        torch.cuda.synchronize()
+        l1 = cpinv.launch_count()
+        loop_ms = time_steps(loop, loop_steps, flush, stream)
+        loop_launches = (cpinv.launch_count() - l1) / loop_steps
+    torch.cuda.synchronize()
+    diff = max(float((a - b).norm() / max(float(b.norm()), 1e-300)) for a, b in zip(plan.Ws, Wl))
+    flops = sum(lstsq_flops(p.m, p.n, r, p.F.shape[1]) for p, r in zip(probs, ranks))
+    t = sum(ms) / 1e3 / args.steps
+    tl = sum(loop_ms) / 1e3 / loop_steps
+    return {
+        "workload": BATCH_WORKLOAD,
+        "problems_per_s": round(BATCH["P"] / t, 2),
+        "tflops": round(flops / t / 1e12, 4),
+        "ms_per_batch": round(t * 1e3, 4),
+        "gpu_launches_per_batch": launches,
+        "loop_problems_per_s": round(BATCH["P"] / tl, 2),
+        "loop_ms": round(tl * 1e3, 3),
+        "loop_launches": loop_launches,
+        "speedup_vs_loop": round(tl / t, 3),
+        "max_rel_diff_batch_vs_loop": diff,
+        "ranks_match_construction": ranks == [p.r for p in probs] and ranks2 == ranks,
+        "all_ok": all(x == 0 for x in st) and all(x == 0 for x in st2),
+        "algorithmic_gflop_per_batch": round(flops / 1e9, 3),
+        "dtype": "f64",
+    }
+
+
+def batched_main(args):
+    import torch
+
+    from paper_0804_4809_gb300 import build
+    build.build()
+    dev = torch.device("cuda", 0)
+    flushbuf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    res = batched_bench(args, dev, flushbuf.zero_)
+    print(json.dumps(res), flush=True)
 
 
 def best_modes():
@@ -464,8 +578,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-baseline", action="store_true",
                     help="run only the selected mode (profiling runs)")
-    ap.add_argument("--workload", default="pinv", choices=["pinv", "gemm"],
-                    help="gemm: the exact-slice product alone, at the G+ = K G' shape")
+    ap.add_argument("--workload", default="pinv", choices=["pinv", "gemm", "batched"],
+                    help="gemm: the exact-slice product alone, at the G+ = K G' shape; "
+                         "batched: 512 uneven least-squares problems vs a per-matrix loop")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched-workload summary in the main line")
     ap.add_argument("--cpu-reps", type=int, default=3)
     ap.add_argument("--cpu-budget-s", type=float, default=25.0)
     args = ap.parse_args()
@@ -475,6 +592,8 @@ def main():
         return reference(args)
     if args.workload == "gemm":
         return gemm_bench(args)
+    if args.workload == "batched":
+        return batched_main(args)
     return ours(args)
 
 

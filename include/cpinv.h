@@ -106,6 +106,51 @@ int cpinv_lstsq(const double* G, int64_t m, int64_t n, int64_t ldg,
                 const cpinv_opts* o, int64_t* rank_out, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Batched least squares: W_p = G_p+ F_p for P independent problems of
+ * uneven size (Theorem 1 and the Appendix applied to each problem on its
+ * own, with its own tolerance and rank), all enqueued on `stream` as one
+ * batch.  Every problem is computed in FP64 arithmetic.
+ *   probs : HOST array of P descriptors; G, F, W in each are DEVICE pointers
+ *           (row-major, as for cpinv_lstsq).  Requires 1 <= n <= m,
+ *           n <= CPINV_BATCHED_MAX_N, 1 <= k <= CPINV_BATCHED_MAX_K,
+ *           m <= CPINV_BATCHED_MAX_M (else CPINV_ERR_UNSUPPORTED).
+ *   o     : mode must be CPINV_MODE_FP64 (else CPINV_ERR_UNSUPPORTED); panel
+ *           0 (chosen by timing both candidates on the first call of each
+ *           bucket shape; set CPINV_TUNE_FILE to a path to keep the choices
+ *           as JSON lines), 16 or 32; rel_tol as for cpinv_lstsq.
+ *   ranks_out, status_out : HOST arrays of P entries, or NULL.  If either
+ *           is non-NULL the call synchronizes `stream` and writes each
+ *           problem's rank r_p (-1 on failure) and CPINV_* status; the
+ *           return value is then the first non-OK problem status (or OK).
+ *           With both NULL the call returns after enqueueing.
+ *   workspace : cpinv_lstsq_batched_workspace_size(P, probs, o) bytes (0 on
+ *           invalid arguments), 256-byte aligned, on the current device.
+ * A second call with identical arguments (same pointers, sizes, workspace
+ * and options) replays the whole batch as one CUDA graph.  The workspace and
+ * the descriptors' buffers must stay valid until the stream reaches the end
+ * of the batch.
+ * ------------------------------------------------------------------------- */
+#define CPINV_BATCHED_MAX_N 512
+#define CPINV_BATCHED_MAX_K 256
+#define CPINV_BATCHED_MAX_M 1048576
+
+typedef struct cpinv_problem {
+  int64_t m, n, k;   /* G is m x n, F is m x k, W is n x k */
+  const double* G;
+  int64_t ldg;
+  const double* F;
+  int64_t ldf;
+  double* W;
+  int64_t ldw;
+} cpinv_problem;
+
+size_t cpinv_lstsq_batched_workspace_size(int32_t P, const cpinv_problem* probs,
+                                          const cpinv_opts* o);
+int cpinv_lstsq_batched(int32_t P, const cpinv_problem* probs, int64_t* ranks_out,
+                        int32_t* status_out, void* workspace, size_t workspace_bytes,
+                        const cpinv_opts* o, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Numerical rank and kept-pivot mask (Appendix: tol rule and full-rank
  * Cholesky).  accepted_out (device, may be NULL) receives one byte per
  * column of the factored Gram matrix -- min(m, n) bytes: columns of G when

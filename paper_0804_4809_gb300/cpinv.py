@@ -38,6 +38,14 @@ class ProfileEntry(ctypes.Structure):
                 ("ms", ctypes.c_double), ("flops", ctypes.c_double)]
 
 
+class Problem(ctypes.Structure):
+    """One problem of a batched least-squares call (``cpinv_problem``)."""
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("G", ctypes.c_void_p), ("ldg", ctypes.c_int64),
+                ("F", ctypes.c_void_p), ("ldf", ctypes.c_int64),
+                ("W", ctypes.c_void_p), ("ldw", ctypes.c_int64)]
+
+
 class CpinvError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"cpinv status {status}: {msg}")
@@ -61,6 +69,11 @@ SIGNATURES = {
     "cpinv_rank_workspace_size": (_c_sz, [_c_i64, _c_i64, ctypes.POINTER(Opts)]),
     "cpinv_rank": (ctypes.c_int, [_c_vp, _c_i64, _c_i64, _c_i64, _c_vp, _c_vp, _c_sz,
                                   ctypes.POINTER(Opts), ctypes.POINTER(_c_i64), _c_vp]),
+    "cpinv_lstsq_batched_workspace_size": (_c_sz, [ctypes.c_int32, ctypes.POINTER(Problem),
+                                                   ctypes.POINTER(Opts)]),
+    "cpinv_lstsq_batched": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(Problem),
+                                           ctypes.POINTER(_c_i64), ctypes.POINTER(ctypes.c_int32),
+                                           _c_vp, _c_sz, ctypes.POINTER(Opts), _c_vp]),
     "cpinv_pinv_static": (ctypes.c_int, [_c_vp, _c_i64, _c_i64, _c_i64, _c_vp, _c_i64,
                                          ctypes.POINTER(Opts), ctypes.POINTER(_c_i64), _c_vp]),
     "cpinv_matmul_workspace_size": (_c_sz, [_c_i64, _c_i64, _c_i64, ctypes.c_int32,
@@ -191,6 +204,60 @@ def rank(G: torch.Tensor, mode="fp64", rel_tol: float = 1e-9, panel: int = 0, sl
                           _stream(G.device))
     _check(st)
     return int(r.value), mask
+
+
+class BatchedLstsq:
+    """W_p = G_p+ F_p for a list of problems of uneven size, as one batch.
+
+    The descriptor array, the outputs and the workspace are built once, so
+    repeated calls with the same tensors replay one CUDA graph of the whole
+    batch.  ``Gs``/``Fs`` are lists of CUDA float64 matrices (m_p x n_p with
+    n_p <= m_p, and m_p x k_p)."""
+
+    def __init__(self, Gs, Fs, rel_tol: float = 1e-9, panel: int = 0):
+        if len(Gs) != len(Fs):
+            raise ValueError("Gs and Fs differ in length")
+        self.Gs = [_mat(G, "G") for G in Gs]
+        self.Fs = [_mat(F, "F") for F in Fs]
+        self.P = len(self.Gs)
+        self.device = self.Gs[0].device if self.P else torch.device("cuda")
+        self.opts = make_opts("fp64", rel_tol, panel)
+        self.Ws = []
+        self.probs = (Problem * max(self.P, 1))()
+        for i, (G, F) in enumerate(zip(self.Gs, self.Fs)):
+            m, n = G.shape
+            if F.shape[0] != m:
+                raise ValueError(f"problem {i}: F must have as many rows as G")
+            W = torch.empty((n, F.shape[1]), dtype=torch.float64, device=G.device)
+            self.Ws.append(W)
+            self.probs[i] = Problem(m, n, F.shape[1], G.data_ptr(), _ld(G), F.data_ptr(), _ld(F),
+                                    W.data_ptr(), _ld(W))
+        nbytes = lib().cpinv_lstsq_batched_workspace_size(self.P, self.probs,
+                                                          ctypes.byref(self.opts))
+        if nbytes == 0 and self.P:
+            raise CpinvError(1, "invalid or unsupported problem sizes")
+        self.ws = _workspace(nbytes, self.device)
+        self.ranks = (_c_i64 * max(self.P, 1))()
+        self.status = (ctypes.c_int32 * max(self.P, 1))()
+
+    def __call__(self, sync: bool = True, stream: int | None = None):
+        """Runs the batch; with ``sync`` returns (Ws, ranks, statuses)."""
+        st = lib().cpinv_lstsq_batched(self.P, self.probs, self.ranks if sync else None,
+                                       self.status if sync else None, self.ws.data_ptr(),
+                                       self.ws.numel(), ctypes.byref(self.opts),
+                                       _stream(self.device) if stream is None else stream)
+        if not sync:
+            _check(st)
+            return self.Ws, None, None
+        statuses = [int(self.status[i]) for i in range(self.P)]
+        if st != 0 and all(x == 0 for x in statuses):
+            _check(st)
+        return self.Ws, [int(self.ranks[i]) for i in range(self.P)], statuses
+
+
+def lstsq_batched(Gs, Fs, rel_tol: float = 1e-9, panel: int = 0):
+    """One batched call: returns (Ws, ranks, statuses) (see ``BatchedLstsq``)."""
+    return BatchedLstsq(Gs, Fs, rel_tol, panel)()
 
 
 def profile_enable(on: bool = True) -> bool:

@@ -1,0 +1,868 @@
+// Batched minimum-norm least squares, W_p = G_p+ F_p for many independent
+// problems of uneven size (cpinv_lstsq_batched in include/cpinv.h); each
+// problem follows the Appendix pipeline exactly as the single-problem path
+// does, in FP64 arithmetic.
+//
+// The problems are grouped into buckets by n rounded up to a multiple of 128.
+// Inside a bucket every problem keeps its own m, n and rank in its DevState,
+// and every launch reads them through Dim selectors (SEL_M, SEL_N, the rank),
+// so a product of problem z covers exactly its own m x n block: padding costs
+// memory, not arithmetic.  Each stage of the pipeline is then one launch for
+// all problems of the bucket: the products as z-batched FP64 products
+// (gemm_fp64.cu; the triangular inverse batches the nodes of a level x the
+// problems), the diagonal blocks as one CTA per problem
+// (diag32_batched_kernel), the small kernels below with one grid layer per
+// problem.  Buckets run on several streams; from the second call with the
+// same arguments on, the whole batch replays as one CUDA graph.  The panel
+// width of each bucket shape is picked by timing both candidates on its first
+// call (optionally remembered in a JSON-lines file).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/cpinv.h"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace cpinv {
+namespace {
+
+struct ProblemDesc {
+  int64_t m, n, k;
+  const double* G;
+  int64_t ldg;
+  const double* F;
+  int64_t ldf;
+  double* W;
+  int64_t ldw;
+  int64_t id;  // index in the caller's array
+};
+
+constexpr int64_t kNStep = 128;  // bucket granularity of n
+constexpr int64_t kMaxN = 512;   // largest n of a batched problem
+constexpr int kBatchStreams = 4;
+// problems per bucket at most: the triangular inverse launches (problems x
+// nodes of a level) z-layers, at most 16 nodes, within the 65535 limit
+constexpr size_t kMaxBucket = 2048;
+static_assert(kMaxN == CPINV_BATCHED_MAX_N, "compaction block size");
+
+// Per problem: zeroed state with its own m and n.
+__global__ void init_state_kernel(const ProblemDesc* d, DevState* st, int nz) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= nz) return;
+  DevState s = {};
+  s.dim_m = d[z].m;
+  s.dim_n = d[z].n;
+  st[z] = s;
+}
+
+// G_z (m x n) and F_z (m x k, zero columns up to kp) into the bucket buffers
+// (row strides np and kp).  Grid: x over columns, y over rows, z problems.
+__global__ void pack_kernel(const ProblemDesc* d, double* Gp, int64_t mp, int64_t np, double* Fp,
+                            int64_t kp) {
+  const ProblemDesc q = d[blockIdx.z];
+  double* g = Gp + (int64_t)blockIdx.z * mp * np;
+  double* f = Fp + (int64_t)blockIdx.z * mp * kp;
+  for (int64_t i = blockIdx.y; i < q.m; i += gridDim.y) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < q.n + kp;
+         j += (int64_t)gridDim.x * blockDim.x) {
+      if (j < q.n) {
+        g[i * np + j] = q.G[i * q.ldg + j];
+      } else {
+        const int64_t c = j - q.n;
+        f[i * kp + c] = c < q.k ? q.F[i * q.ldf + c] : 0.0;
+      }
+    }
+  }
+}
+
+__global__ void unpack_kernel(const ProblemDesc* d, const double* Wp, int64_t np, int64_t kp) {
+  const ProblemDesc q = d[blockIdx.y];
+  const double* w = Wp + (int64_t)blockIdx.y * np * kp;
+  const int64_t total = q.n * q.k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / q.k, c = e % q.k;
+    q.W[i * q.ldw + c] = w[i * kp + c];
+  }
+}
+
+// Per problem (one block each): the Appendix tolerance rel_tol * min{A_jj :
+// A_jj > 0} over its own n diagonal entries, and the non-finite flag.
+__global__ void __launch_bounds__(256) tol_batched_kernel(const double* A, int64_t np,
+                                                          double rel_tol, DevState* st) {
+  DevState* s = st + blockIdx.x;
+  const int64_t n = s->dim_n;
+  const double* a = A + (int64_t)blockIdx.x * np * np;
+  __shared__ double smin[256];
+  __shared__ int sbad[256];
+  double mn = INFINITY;
+  int bad = 0;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+    const double v = a[j * np + j];
+    if (!isfinite(v)) bad = 1;
+    else if (v > 0.0 && v < mn) mn = v;
+  }
+  smin[threadIdx.x] = mn;
+  sbad[threadIdx.x] = bad;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + w]);
+      sbad[threadIdx.x] |= sbad[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double m = smin[0];
+    const int has = m < INFINITY;
+    s->has_pos = has;
+    s->min_pos = has ? m : 0.0;
+    s->tol = has ? rel_tol * m : INFINITY;
+    if (sbad[0]) s->status |= ST_NONFINITE;
+  }
+}
+
+// Per problem (one block of kMaxN threads each): rank r = number of kept
+// pivots, and the compact factor L (n x r): column idx(c) = column c of the
+// full factor for each kept c, upper part zero.  Columns >= r are not
+// written (never read).
+__global__ void __launch_bounds__(kMaxN) compact_batched_kernel(const uint8_t* acc,
+                                                                const double* Lfull, double* L,
+                                                                int64_t np, DevState* st) {
+  const int64_t z = blockIdx.x;
+  const int64_t n = st[z].dim_n;
+  const uint8_t* a = acc + z * np;
+  const double* lf = Lfull + z * np * np;
+  double* l = L + z * np * np;
+  __shared__ int32_t idx[kMaxN];
+  __shared__ int32_t warp_cnt[kMaxN / 32];
+  // exclusive scan of the mask, one column per thread
+  const int c = threadIdx.x, lane = c & 31, w = c >> 5;
+  const int keep = (c < n && a[c]) ? 1 : 0;
+  int incl = keep;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) warp_cnt[w] = incl;
+  __syncthreads();
+  if (c == 0) {
+    int run = 0;
+    for (int q = 0; q < kMaxN / 32; ++q) {
+      const int v = warp_cnt[q];
+      warp_cnt[q] = run;
+      run += v;
+    }
+    st[z].rank = run;
+  }
+  __syncthreads();
+  idx[c] = keep ? warp_cnt[w] + incl - 1 : -1;
+  __syncthreads();
+  for (int64_t e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int64_t i = e / n, cc = e % n;
+    const int32_t j = idx[cc];
+    if (j >= 0) l[i * np + j] = (cc <= i) ? lf[i * np + cc] : 0.0;
+  }
+}
+
+// W_z = block diagonal of U^-1 (the inverted b x b blocks of the Cholesky
+// factor U of L'L, order r_z), zero elsewhere.
+__global__ void tri_inv_init_batched_kernel(double* W, int64_t np, const double* Tinv, int b,
+                                            int64_t zT, const DevState* st) {
+  const int64_t z = blockIdx.y;
+  const int64_t r = st[z].rank;
+  double* w = W + z * np * np;
+  const double* t = Tinv + z * zT;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < np * np;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / np, j = e % np;
+    double v = 0.0;
+    if (i < r && j < r && i / b == j / b && j <= i) {
+      const int64_t q = i / b;
+      v = t[q * (int64_t)b * b + (i - q * b) * b + (j - q * b)];
+    }
+    w[i * np + j] = v;
+  }
+}
+
+// Ranks and status bits into the caller-ordered arrays.  A factorisation of
+// L'L that kept fewer than r pivots marks the problem as failed.
+__global__ void ranks_kernel(const ProblemDesc* d, const DevState* st, int nz, int64_t* ranks,
+                             int32_t* status) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= nz) return;
+  const int64_t id = d[z].id;
+  int32_t s = st[z].status;
+  if (st[z].rank_n != st[z].rank) s |= ST_NUMERICAL;
+  ranks[id] = st[z].rank;
+  status[id] = s;
+}
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+inline unsigned g1(int64_t total, int threads, int64_t cap) {
+  int64_t g = (total + threads - 1) / threads;
+  if (g > cap) g = cap;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+// ---------------------------------------------------------------------------
+// host side: layout
+// ---------------------------------------------------------------------------
+
+struct Bucket {
+  int64_t mp, np, kp;
+  std::vector<int> ids;
+  int b;
+  double work;  // flop estimate, for spreading buckets over streams
+  size_t off_desc, off_G, off_F, off_A, off_L, off_W, off_M, off_T, off_Z, off_acc, off_st,
+      off_c1, off_c2, off_c3, off_Wp;
+};
+
+struct Layout {
+  std::vector<Bucket> buckets;
+  size_t off_ranks, off_status, total;
+};
+
+Layout make_layout(int P, const cpinv_problem* probs) {
+  Layout L;
+  std::map<int64_t, size_t> where;  // n bucket -> the bucket being filled
+  for (int i = 0; i < P; ++i) {
+    const int64_t np = round_up(std::max<int64_t>(probs[i].n, 1), kNStep);
+    auto it = where.find(np);
+    if (it != where.end() && L.buckets[it->second].ids.size() >= kMaxBucket) {
+      where.erase(it);
+      it = where.end();
+    }
+    if (it == where.end()) {
+      Bucket b{};
+      b.np = np;
+      b.mp = 1;
+      b.kp = 1;
+      b.b = 32;
+      it = where.emplace(np, L.buckets.size()).first;
+      L.buckets.push_back(b);
+    }
+    Bucket& b = L.buckets[it->second];
+    b.ids.push_back(i);
+    b.mp = std::max<int64_t>(b.mp, probs[i].m);
+    b.kp = std::max<int64_t>(b.kp, probs[i].k);
+    const double m = (double)probs[i].m, n = (double)probs[i].n;
+    b.work += m * n * n + 2.0 * n * n * n;
+  }
+  size_t off = 0;
+  auto take = [&](size_t x) {
+    off = (off + 255) / 256 * 256;
+    const size_t o = off;
+    off += x;
+    return o;
+  };
+  for (auto& b : L.buckets) {
+    b.mp = round_up(b.mp, 8);
+    b.kp = round_up(b.kp, 2);
+    const size_t nz = b.ids.size(), np = (size_t)b.np, mp = (size_t)b.mp, kp = (size_t)b.kp;
+    b.off_desc = take(sizeof(ProblemDesc) * nz);
+    b.off_st = take(sizeof(DevState) * nz);
+    b.off_G = take(8 * nz * mp * np);
+    b.off_F = take(8 * nz * mp * kp);
+    b.off_A = take(8 * nz * np * np);
+    b.off_L = take(8 * nz * np * np);
+    b.off_W = take(8 * nz * np * np);
+    b.off_M = take(8 * nz * np * np);
+    b.off_T = take(8 * nz * np * 32);  // (np / b) blocks of b x b, b <= 32
+    b.off_Z = take(8 * nz * 32 * 32);
+    b.off_acc = take(nz * np);
+    b.off_c1 = take(8 * nz * np * kp);
+    b.off_c2 = take(8 * nz * np * kp);
+    b.off_c3 = take(8 * nz * np * kp);
+    b.off_Wp = take(8 * nz * np * kp);
+  }
+  L.off_ranks = take(sizeof(int64_t) * (size_t)std::max(P, 1));
+  L.off_status = take(sizeof(int32_t) * (size_t)std::max(P, 1));
+  L.total = (off + 255) / 256 * 256;
+  return L;
+}
+
+#define BK_CHECK(x)                               \
+  do {                                            \
+    cudaError_t _e = (x);                         \
+    if (_e != cudaSuccess) return CPINV_ERR_CUDA; \
+  } while (0)
+
+// One batched FP64 product over the nz problems of a bucket:
+//   C_z = alpha op(A_z) op(B_z) + beta C_z
+// (operand strides zA, zB, zC; dims read problem z's DevState).
+struct BGemm {
+  GemmParams g;
+  bool ta = false, tb = false;
+  BGemm(int nz, const DevState* st) {
+    std::memset(&g, 0, sizeof(g));
+    g.nz = nz;
+    g.rdev = &st->rank;
+    g.zR = (int64_t)(sizeof(DevState) / sizeof(int64_t));
+  }
+  BGemm& a(const double* p, int64_t ld, int64_t z, bool t) {
+    g.A = p;
+    g.lda = ld;
+    g.zA = z;
+    ta = t;
+    return *this;
+  }
+  BGemm& b(const double* p, int64_t ld, int64_t z, bool t) {
+    g.B = p;
+    g.ldb = ld;
+    g.zB = z;
+    tb = t;
+    return *this;
+  }
+  BGemm& c(double* p, int64_t ld, int64_t z) {
+    g.C = p;
+    g.ldc = ld;
+    g.zC = z;
+    return *this;
+  }
+  BGemm& dims(Dim M, Dim N, Dim K) {
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    return *this;
+  }
+  cudaError_t run(cudaStream_t s, double alpha, double beta, int lower) {
+    g.alpha = alpha;
+    g.beta = beta;
+    g.lower = lower;
+    g.pad = (g.C == g.A || g.C == g.B) ? 1 : 0;
+    KernelTimer t;
+    t.gemm = &g;
+    t.flops_mult = (double)g.nz;
+    return t.run(KT_GEMM_FP64, s, [&] { return launch_dgemm(g, ta, tb, s); });
+  }
+};
+
+// Full-rank Cholesky of every problem of the bucket, right-looking by panels
+// of width b <= 32, in place on the lower triangles of A.  spd = 0: order n_z,
+// pivot test against the problem's tolerance, kept-pivot mask into acc.
+// spd = 1: order r_z, tolerance 0, block inverses into T.
+int bucket_factor(cudaStream_t s, const Bucket& bk, char* ws, int spd, int b) {
+  const int nz = (int)bk.ids.size();
+  const int64_t np = bk.np, nb = (np + b - 1) / b;
+  double* A = (double*)(ws + bk.off_A);
+  DevState* st = (DevState*)(ws + bk.off_st);
+  double* Z = (double*)(ws + bk.off_Z);
+  double* T = (double*)(ws + bk.off_T);
+  uint8_t* acc = (uint8_t*)(ws + bk.off_acc);
+  const int64_t zz = np * np;
+  const int32_t sel = spd ? SEL_RANK : SEL_N;
+  for (int64_t k0 = 0, blk = 0; k0 < np; k0 += b, ++blk) {
+    DiagBatch d;
+    std::memset(&d, 0, sizeof(d));
+    d.A = A;
+    d.lda = np;
+    d.zA = zz;
+    d.nd = Dim{0, np, sel, 0};
+    d.k0 = k0;
+    d.b = b;
+    d.spd = spd;
+    d.st = st;
+    d.accepted = spd ? nullptr : acc;
+    d.zAcc = np;
+    d.Z = Z;
+    d.zZ = (int64_t)b * b;
+    d.Tinv = spd ? T + blk * b * b : nullptr;
+    d.zT = nb * b * b;
+    BK_CHECK(KernelTimer().run(KT_DIAG, s, [&] { return launch_diag_batched(d, nz, s); }));
+    if (k0 + b >= np) continue;
+    double* panel = A + (k0 + b) * np + k0;
+    double* trail = A + (k0 + b) * np + (k0 + b);
+    const Dim below{-(k0 + b), np - k0 - b, sel, 0}, bw{-k0, b, sel, 0};
+    // L = A Z below the diagonal block (in place), then the trailing update
+    BK_CHECK(BGemm(nz, st)
+                 .a(panel, np, zz, false)
+                 .b(Z, b, (int64_t)b * b, false)
+                 .c(panel, np, zz)
+                 .dims(below, bw, bw)
+                 .run(s, 1.0, 0.0, 0));
+    BK_CHECK(BGemm(nz, st)
+                 .a(panel, np, zz, false)
+                 .b(panel, np, zz, true)
+                 .c(trail, np, zz)
+                 .dims(below, below, bw)
+                 .run(s, -1.0, 1.0, 1));
+  }
+  return CPINV_OK;
+}
+
+// W = U^-1 from its inverted diagonal blocks (already in W), level by level
+// of the recursive halving: node [lo, lo + 2s) gets W21 = -W22 (U21 W11).
+// One launch per product and level covers all nodes of all problems.
+int bucket_tri_inverse(cudaStream_t s, const Bucket& bk, char* ws, int b) {
+  const int nz = (int)bk.ids.size();
+  const int64_t np = bk.np, zz = np * np;
+  const double* U = (const double*)(ws + bk.off_A);
+  double* W = (double*)(ws + bk.off_W);
+  double* Tmp = (double*)(ws + bk.off_M);
+  const DevState* st = (const DevState*)(ws + bk.off_st);
+  int64_t nbp = 1;
+  while (nbp * b < np) nbp <<= 1;
+  for (int64_t sz = b; sz < nbp * b; sz <<= 1) {
+    const int64_t nodes = (nbp * b) / (2 * sz);
+    auto level = [&](const double* A, const double* B, double* C, Dim M, Dim N, Dim K,
+                     double alpha) {
+      BGemm g(nz, st);
+      g.a(A, np, 0, false).b(B, np, 0, false).c(C, np, 0).dims(M, N, K);
+      if (nodes > 1) {
+        // inner index: the node (offsets move by 2 sz along both axes)
+        g.g.zA = g.g.zB = g.g.zC = 2 * sz * np + 2 * sz;
+        g.g.zM = g.g.zN = g.g.zK = (int32_t)(-2 * sz);
+        g.g.zR = 0;
+        g.g.nzi = (int32_t)nodes;
+        g.g.nz = (int32_t)(nodes * nz);
+        g.g.oA = g.g.oB = g.g.oC = zz;
+        g.g.oR = (int64_t)(sizeof(DevState) / sizeof(int64_t));
+      } else {
+        g.g.zA = g.g.zB = g.g.zC = zz;
+      }
+      return g.run(s, alpha, 0.0, 0);
+    };
+    const Dim rows = rdim(-sz, sz), cols = rdim(0, sz);  // node 0: lo = 0, mid = sz
+    BK_CHECK(level(U + sz * np, W, Tmp + sz * np, rows, cols, cols, 1.0));
+    BK_CHECK(level(W + sz * np + sz, Tmp + sz * np, W + sz * np, rows, cols, rows, -1.0));
+  }
+  return CPINV_OK;
+}
+
+// The whole least-squares pipeline for one bucket, on stream s.
+int run_bucket(cudaStream_t s, const Bucket& bk, char* ws, double rel_tol, int b,
+               int64_t* ranks_dev, int32_t* status_dev) {
+  const int nz = (int)bk.ids.size();
+  const int64_t mp = bk.mp, np = bk.np, kp = bk.kp;
+  const int64_t nb = (np + b - 1) / b;
+  const ProblemDesc* desc = (const ProblemDesc*)(ws + bk.off_desc);
+  double* Gp = (double*)(ws + bk.off_G);
+  double* Fp = (double*)(ws + bk.off_F);
+  double* A = (double*)(ws + bk.off_A);
+  double* L = (double*)(ws + bk.off_L);
+  double* W = (double*)(ws + bk.off_W);
+  double* Mm = (double*)(ws + bk.off_M);
+  double* T = (double*)(ws + bk.off_T);
+  uint8_t* acc = (uint8_t*)(ws + bk.off_acc);
+  DevState* st = (DevState*)(ws + bk.off_st);
+  double* c1 = (double*)(ws + bk.off_c1);
+  double* c2 = (double*)(ws + bk.off_c2);
+  double* c3 = (double*)(ws + bk.off_c3);
+  double* Wp = (double*)(ws + bk.off_Wp);
+  const int64_t zz = np * np, zk = np * kp, zg = mp * np, zf = mp * kp;
+  const Dim R = rdim(0, np), Nn = ndim(0, np), Mr = mdim(mp), Kk = hdim(kp);
+  KernelTimer t;
+  BK_CHECK(t.run(KT_AUX, s, [&] {
+    init_state_kernel<<<(nz + 127) / 128, 128, 0, s>>>(desc, st, nz);
+    return cudaGetLastError();
+  }));
+  BK_CHECK(cudaMemsetAsync(acc, 0, (size_t)nz * np, s));
+  BK_CHECK(t.run(KT_AUX, s, [&] {
+    pack_kernel<<<dim3(g1(np + kp, 128, 8), (unsigned)std::min<int64_t>(mp, 256), (unsigned)nz),
+                  128, 0, s>>>(desc, Gp, mp, np, Fp, kp);
+    return cudaGetLastError();
+  }));
+  // A = G'G (lower), the tolerance, the full-rank Cholesky, compaction to L
+  BK_CHECK(BGemm(nz, st).a(Gp, np, zg, true).b(Gp, np, zg, false).c(A, np, zz).dims(Nn, Nn, Mr)
+               .run(s, 1.0, 0.0, 1));
+  BK_CHECK(t.run(KT_AUX, s, [&] {
+    tol_batched_kernel<<<nz, 256, 0, s>>>(A, np, rel_tol, st);
+    return cudaGetLastError();
+  }));
+  if (int rc = bucket_factor(s, bk, ws, 0, b)) return rc;
+  BK_CHECK(t.run(KT_AUX, s, [&] {
+    compact_batched_kernel<<<nz, kMaxN, 0, s>>>(acc, A, L, np, st);
+    return cudaGetLastError();
+  }));
+  // N = L'L, N = U U', W = U^-1, M = W'W = N^-1
+  BK_CHECK(BGemm(nz, st).a(L, np, zz, true).b(L, np, zz, false).c(A, np, zz).dims(R, R, Nn)
+               .run(s, 1.0, 0.0, 1));
+  if (int rc = bucket_factor(s, bk, ws, 1, b)) return rc;
+  BK_CHECK(t.run(KT_AUX, s, [&] {
+    tri_inv_init_batched_kernel<<<dim3(g1(np * np, 256, 64), (unsigned)nz), 256, 0, s>>>(
+        W, np, T, b, nb * b * b, st);
+    return cudaGetLastError();
+  }));
+  if (int rc = bucket_tri_inverse(s, bk, ws, b)) return rc;
+  BK_CHECK(BGemm(nz, st).a(W, np, zz, true).b(W, np, zz, false).c(Mm, np, zz).dims(R, R, R)
+               .run(s, 1.0, 0.0, 0));
+  // W = L (M (M (L' (G'F))))   (Theorem 1 applied to F, right to left)
+  BK_CHECK(BGemm(nz, st).a(Gp, np, zg, true).b(Fp, kp, zf, false).c(c1, kp, zk).dims(Nn, Kk, Mr)
+               .run(s, 1.0, 0.0, 0));
+  BK_CHECK(BGemm(nz, st).a(L, np, zz, true).b(c1, kp, zk, false).c(c2, kp, zk).dims(R, Kk, Nn)
+               .run(s, 1.0, 0.0, 0));
+  BK_CHECK(BGemm(nz, st).a(Mm, np, zz, false).b(c2, kp, zk, false).c(c3, kp, zk).dims(R, Kk, R)
+               .run(s, 1.0, 0.0, 0));
+  BK_CHECK(BGemm(nz, st).a(Mm, np, zz, false).b(c3, kp, zk, false).c(c2, kp, zk).dims(R, Kk, R)
+               .run(s, 1.0, 0.0, 0));
+  BK_CHECK(BGemm(nz, st).a(L, np, zz, false).b(c2, kp, zk, false).c(Wp, kp, zk).dims(Nn, Kk, R)
+               .run(s, 1.0, 0.0, 0));
+  BK_CHECK(t.run(KT_AUX, s, [&] {
+    unpack_kernel<<<dim3(g1(np * kp, 256, 16), (unsigned)nz), 256, 0, s>>>(desc, Wp, np, kp);
+    return cudaGetLastError();
+  }));
+  BK_CHECK(t.run(KT_AUX, s, [&] {
+    ranks_kernel<<<(nz + 127) / 128, 128, 0, s>>>(desc, st, nz, ranks_dev, status_dev);
+    return cudaGetLastError();
+  }));
+  return CPINV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Panel-width autotuner.  Per bucket shape (device, padded n, m, k, problem
+// count) the faster of b = 16 and b = 32, timed on the first call; with
+// CPINV_TUNE_FILE set, choices are read from and appended to that file as
+// JSON lines {"key": "...", "panel": b}.
+// ---------------------------------------------------------------------------
+struct Tuner {
+  std::mutex mu;
+  std::map<std::string, int> best;
+  bool loaded = false;
+  std::string file;
+
+  static std::string key(const Bucket& b, int device) {
+    cudaDeviceProp prop;
+    std::memset(&prop, 0, sizeof(prop));
+    cudaGetDeviceProperties(&prop, device);
+    char buf[320];
+    std::snprintf(buf, sizeof(buf), "%s|sm%d%d|fp64|n%lld|m%lld|k%lld|p%zu", prop.name, prop.major,
+                  prop.minor, (long long)b.np, (long long)b.mp, (long long)b.kp, b.ids.size());
+    return buf;
+  }
+  void load() {
+    if (loaded) return;
+    loaded = true;
+    const char* f = std::getenv("CPINV_TUNE_FILE");
+    if (!f || !*f) return;
+    file = f;
+    FILE* fp = std::fopen(f, "r");
+    if (!fp) return;
+    char line[512];
+    while (std::fgets(line, sizeof(line), fp)) {
+      const char* k = std::strstr(line, "\"key\": \"");
+      const char* pn = std::strstr(line, "\"panel\": ");
+      if (!k || !pn) continue;
+      k += 8;
+      const char* e = std::strchr(k, '"');
+      if (!e) continue;
+      const int b = std::atoi(pn + 9);
+      if (b == 16 || b == 32) best[std::string(k, e)] = b;
+    }
+    std::fclose(fp);
+  }
+  void store(const std::string& k, int b) {
+    best[k] = b;
+    if (file.empty()) return;
+    FILE* fp = std::fopen(file.c_str(), "a");
+    if (!fp) return;
+    std::fprintf(fp, "{\"key\": \"%s\", \"panel\": %d}\n", k.c_str(), b);
+    std::fclose(fp);
+  }
+};
+Tuner g_tuner;
+
+// Library streams of each device: the bucket streams and a capture stream,
+// with the events that fork and join them.
+struct DeviceStreams {
+  int device;
+  cudaStream_t side[kBatchStreams];
+  cudaEvent_t join[kBatchStreams];
+  cudaEvent_t fork;
+  cudaStream_t capture;
+};
+std::mutex g_dev_mu;
+std::vector<DeviceStreams*> g_dev;
+
+int device_streams(DeviceStreams** out) {
+  int device = 0;
+  BK_CHECK(cudaGetDevice(&device));
+  std::lock_guard<std::mutex> lock(g_dev_mu);
+  for (auto* d : g_dev)
+    if (d->device == device) {
+      *out = d;
+      return CPINV_OK;
+    }
+  auto* d = new DeviceStreams();
+  d->device = device;
+  for (int i = 0; i < kBatchStreams; ++i) {
+    BK_CHECK(cudaStreamCreateWithFlags(&d->side[i], cudaStreamNonBlocking));
+    BK_CHECK(cudaEventCreateWithFlags(&d->join[i], cudaEventDisableTiming));
+  }
+  BK_CHECK(cudaEventCreateWithFlags(&d->fork, cudaEventDisableTiming));
+  BK_CHECK(cudaStreamCreateWithFlags(&d->capture, cudaStreamNonBlocking));
+  g_dev.push_back(d);
+  *out = d;
+  return CPINV_OK;
+}
+
+// Picks the panel width of every bucket (the option, a tuned choice, or a
+// measurement of both candidates on `s` when `measure`).
+int choose_panels(Layout& L, char* ws, double rel_tol, int panel, bool measure, cudaStream_t s) {
+  int device = 0;
+  BK_CHECK(cudaGetDevice(&device));
+  std::lock_guard<std::mutex> lock(g_tuner.mu);
+  g_tuner.load();
+  int64_t* ranks_dev = (int64_t*)(ws + L.off_ranks);
+  int32_t* status_dev = (int32_t*)(ws + L.off_status);
+  for (auto& bk : L.buckets) {
+    bk.b = panel ? panel : 32;
+    if (panel) continue;
+    const std::string k = Tuner::key(bk, device);
+    auto it = g_tuner.best.find(k);
+    if (it != g_tuner.best.end()) {
+      bk.b = it->second;
+      continue;
+    }
+    if (!measure) continue;
+    cudaEvent_t e0, e1;
+    BK_CHECK(cudaEventCreate(&e0));
+    BK_CHECK(cudaEventCreate(&e1));
+    float best_ms = 0.f;
+    int best_b = 32;
+    for (int cand : {16, 32}) {
+      // one untimed run (first launches load modules), one timed
+      if (int rc = run_bucket(s, bk, ws, rel_tol, cand, ranks_dev, status_dev)) return rc;
+      BK_CHECK(cudaEventRecord(e0, s));
+      if (int rc = run_bucket(s, bk, ws, rel_tol, cand, ranks_dev, status_dev)) return rc;
+      BK_CHECK(cudaEventRecord(e1, s));
+      BK_CHECK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      BK_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+      if (cand == 16 || ms < best_ms) {
+        best_ms = ms;
+        best_b = cand;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    bk.b = best_b;
+    g_tuner.store(k, best_b);
+  }
+  return CPINV_OK;
+}
+
+// All buckets: fork from `s` onto the bucket streams (largest work first,
+// each to the least loaded stream), join back on `s`.
+int run_all(const Layout& L, DeviceStreams* d, char* ws, double rel_tol, cudaStream_t s) {
+  int64_t* ranks_dev = (int64_t*)(ws + L.off_ranks);
+  int32_t* status_dev = (int32_t*)(ws + L.off_status);
+  const int ns = (int)std::min<size_t>(kBatchStreams, L.buckets.size());
+  BK_CHECK(cudaEventRecord(d->fork, s));
+  for (int i = 0; i < ns; ++i) BK_CHECK(cudaStreamWaitEvent(d->side[i], d->fork, 0));
+  std::vector<size_t> order(L.buckets.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+  std::sort(order.begin(), order.end(),
+            [&](size_t a, size_t b) { return L.buckets[a].work > L.buckets[b].work; });
+  std::vector<double> load((size_t)ns, 0.0);
+  for (size_t i : order) {
+    const Bucket& bk = L.buckets[i];
+    const int q = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[(size_t)q] += bk.work;
+    if (int rc = run_bucket(d->side[q], bk, ws, rel_tol, bk.b, ranks_dev, status_dev)) return rc;
+  }
+  for (int i = 0; i < ns; ++i) {
+    BK_CHECK(cudaEventRecord(d->join[i], d->side[i]));
+    BK_CHECK(cudaStreamWaitEvent(s, d->join[i], 0));
+  }
+  return CPINV_OK;
+}
+
+// Graphs of whole batches, keyed by every argument that shapes the launches.
+struct BatchGraph {
+  std::vector<int64_t> key;
+  int64_t launches = 0;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t stamp = 0;
+};
+std::mutex g_bgraph_mu;
+std::vector<BatchGraph> g_bgraphs;
+uint64_t g_bclock = 0;
+constexpr size_t kMaxBatchGraphs = 8;
+
+std::vector<int64_t> batch_key(int P, const cpinv_problem* probs, void* ws, size_t ws_bytes,
+                               double rel_tol, int panel) {
+  std::vector<int64_t> k;
+  k.reserve(8 + 9 * (size_t)P);
+  int device = 0;
+  cudaGetDevice(&device);
+  int64_t tol_bits;
+  std::memcpy(&tol_bits, &rel_tol, sizeof(tol_bits));
+  k.insert(k.end(), {(int64_t)device, (int64_t)(uintptr_t)ws, (int64_t)ws_bytes, tol_bits,
+                     (int64_t)panel, (int64_t)P});
+  for (int i = 0; i < P; ++i) {
+    const cpinv_problem& q = probs[i];
+    k.insert(k.end(), {q.m, q.n, q.k, (int64_t)(uintptr_t)q.G, q.ldg, (int64_t)(uintptr_t)q.F,
+                       q.ldf, (int64_t)(uintptr_t)q.W, q.ldw});
+  }
+  return k;
+}
+
+// The problem descriptors of every bucket, copied on `s` before the batch
+// (also before each graph replay: the workspace may have served another batch).
+int upload_descriptors(const Layout& L, const cpinv_problem* probs, char* ws, cudaStream_t s) {
+  for (const auto& bk : L.buckets) {
+    std::vector<ProblemDesc> d(bk.ids.size());
+    for (size_t z = 0; z < bk.ids.size(); ++z) {
+      const cpinv_problem& q = probs[bk.ids[z]];
+      d[z] = ProblemDesc{q.m, q.n, q.k, q.G, q.ldg, q.F, q.ldf, q.W, q.ldw, (int64_t)bk.ids[z]};
+    }
+    BK_CHECK(cudaMemcpyAsync(ws + bk.off_desc, d.data(), sizeof(ProblemDesc) * d.size(),
+                             cudaMemcpyHostToDevice, s));
+  }
+  return CPINV_OK;
+}
+
+int batched_enqueue(int P, const cpinv_problem* probs, char* ws, size_t ws_bytes, double rel_tol,
+                    int panel, cudaStream_t s) {
+  Layout L = make_layout(P, probs);
+  DeviceStreams* d = nullptr;
+  if (int rc = device_streams(&d)) return rc;
+  if (int rc = upload_descriptors(L, probs, ws, s)) return rc;
+  if (!graph_replay_allowed()) {
+    if (int rc = choose_panels(L, ws, rel_tol, panel, true, s)) return rc;
+    return run_all(L, d, ws, rel_tol, s);
+  }
+  std::lock_guard<std::mutex> lock(g_bgraph_mu);
+  std::vector<int64_t> key = batch_key(P, probs, ws, ws_bytes, rel_tol, panel);
+  BatchGraph* e = nullptr;
+  for (auto& x : g_bgraphs)
+    if (x.key == key) e = &x;
+  if (!e) {
+    // first call with these arguments: tune and run directly
+    if (g_bgraphs.size() >= kMaxBatchGraphs) {
+      size_t old = 0;
+      for (size_t i = 1; i < g_bgraphs.size(); ++i)
+        if (g_bgraphs[i].stamp < g_bgraphs[old].stamp) old = i;
+      if (g_bgraphs[old].exec) cudaGraphExecDestroy(g_bgraphs[old].exec);
+      g_bgraphs.erase(g_bgraphs.begin() + (long)old);
+    }
+    BatchGraph ne;
+    ne.key = std::move(key);
+    ne.stamp = ++g_bclock;
+    g_bgraphs.push_back(std::move(ne));
+    if (int rc = choose_panels(L, ws, rel_tol, panel, true, s)) return rc;
+    return run_all(L, d, ws, rel_tol, s);
+  }
+  e->stamp = ++g_bclock;
+  if (!e->exec) {
+    if (int rc = choose_panels(L, ws, rel_tol, panel, false, s)) return rc;
+    // the capture stream starts after everything enqueued on s so far
+    BK_CHECK(cudaEventRecord(d->fork, s));
+    BK_CHECK(cudaStreamWaitEvent(d->capture, d->fork, 0));
+    const int64_t l0 = cpinv_launch_count();
+    BK_CHECK(cudaStreamBeginCapture(d->capture, cudaStreamCaptureModeThreadLocal));
+    const int rc = run_all(L, d, ws, rel_tol, d->capture);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(d->capture, &graph);
+    if (rc != CPINV_OK || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc != CPINV_OK ? rc : CPINV_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return CPINV_ERR_CUDA;
+    e->exec = exec;
+    e->launches = cpinv_launch_count() - l0;
+    launches_add(-e->launches);  // counted at each replay
+  }
+  BK_CHECK(cudaGraphLaunch(e->exec, s));
+  launches_add(e->launches);
+  return CPINV_OK;
+}
+
+int check_problems(int P, const cpinv_problem* probs) {
+  if (P < 0 || (P > 0 && !probs)) return CPINV_ERR_INVALID_ARG;
+  for (int i = 0; i < P; ++i) {
+    const cpinv_problem& q = probs[i];
+    if (q.m < 1 || q.n < 1 || q.k < 1) return CPINV_ERR_INVALID_ARG;
+    if (!q.G || !q.F || !q.W) return CPINV_ERR_INVALID_ARG;
+    if (q.ldg < q.n || q.ldf < q.k || q.ldw < q.k) return CPINV_ERR_INVALID_ARG;
+    if (q.n > q.m || q.n > CPINV_BATCHED_MAX_N || q.k > CPINV_BATCHED_MAX_K ||
+        q.m > CPINV_BATCHED_MAX_M)
+      return CPINV_ERR_UNSUPPORTED;
+  }
+  return CPINV_OK;
+}
+
+int check_opts(const cpinv_opts* o, double* rel_tol, int* panel) {
+  cpinv_opts d;
+  cpinv_default_opts(&d);
+  if (!o) o = &d;
+  if (o->reserved != 0) return CPINV_ERR_INVALID_ARG;
+  if (!(o->rel_tol >= 0.0) || !std::isfinite(o->rel_tol)) return CPINV_ERR_INVALID_ARG;
+  if (o->panel != 0 && o->panel != 16 && o->panel != 32) return CPINV_ERR_INVALID_ARG;
+  if (o->mode != CPINV_MODE_FP64) return CPINV_ERR_UNSUPPORTED;
+  *rel_tol = o->rel_tol;
+  *panel = o->panel;
+  return CPINV_OK;
+}
+
+}  // namespace
+}  // namespace cpinv
+
+using namespace cpinv;
+
+extern "C" {
+
+size_t cpinv_lstsq_batched_workspace_size(int32_t P, const cpinv_problem* probs,
+                                          const cpinv_opts* o) {
+  double rel_tol;
+  int panel;
+  if (check_problems(P, probs) != CPINV_OK || check_opts(o, &rel_tol, &panel) != CPINV_OK)
+    return 0;
+  return make_layout(P, probs).total;
+}
+
+int cpinv_lstsq_batched(int32_t P, const cpinv_problem* probs, int64_t* ranks_out,
+                        int32_t* status_out, void* workspace, size_t ws_bytes,
+                        const cpinv_opts* o, void* stream) {
+  for (int i = 0; i < P && ranks_out; ++i) ranks_out[i] = -1;
+  for (int i = 0; i < P && status_out; ++i) status_out[i] = CPINV_ERR_INVALID_ARG;
+  double rel_tol;
+  int panel;
+  if (int rc = check_problems(P, probs)) return rc;
+  if (int rc = check_opts(o, &rel_tol, &panel)) return rc;
+  if (P == 0) return CPINV_OK;
+  const Layout L = make_layout(P, probs);
+  if (!workspace || ((uintptr_t)workspace & 255u) || ws_bytes < L.total)
+    return CPINV_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  if (int rc = batched_enqueue(P, probs, ws, ws_bytes, rel_tol, panel, s)) return rc;
+  if (!ranks_out && !status_out) return CPINV_OK;
+  std::vector<int64_t> r((size_t)P);
+  std::vector<int32_t> st((size_t)P);
+  if (cudaMemcpyAsync(r.data(), ws + L.off_ranks, sizeof(int64_t) * P, cudaMemcpyDeviceToHost,
+                      s) != cudaSuccess ||
+      cudaMemcpyAsync(st.data(), ws + L.off_status, sizeof(int32_t) * P, cudaMemcpyDeviceToHost,
+                      s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return CPINV_ERR_CUDA;
+  if (trace_on()) {
+    const DevState* st0 = (const DevState*)(ws + L.buckets[0].off_st);
+    if (trace_finish(s, &st0->rank) != cudaSuccess) return CPINV_ERR_CUDA;
+  }
+  int worst = CPINV_OK;
+  for (int i = 0; i < P; ++i) {
+    int code = CPINV_OK;
+    if (st[(size_t)i] & ST_NONFINITE) code = CPINV_ERR_NONFINITE_INPUT;
+    else if (st[(size_t)i] & ST_NUMERICAL) code = CPINV_ERR_NUMERICAL;
+    else if (st[(size_t)i] & ST_TIMEOUT) code = CPINV_ERR_TIMEOUT;
+    if (ranks_out) ranks_out[i] = code ? -1 : r[(size_t)i];
+    if (status_out) status_out[i] = code;
+    if (code && !worst) worst = code;
+  }
+  return worst;
+}
+
+}  // extern "C"

@@ -40,8 +40,9 @@ struct Arena {
   }
 };
 
+// (a batched problem's own m or n is not known here: its bound `max` stands in)
 int64_t eval_host(const Dim& d, int64_t r) {
-  int64_t v = d.off + (d.sel ? r : 0);
+  int64_t v = d.off + (d.sel == SEL_RANK ? r : d.sel ? d.max : 0);
   v = v < 0 ? 0 : v;
   return v > d.max ? d.max : v;
 }
@@ -374,6 +375,29 @@ cudaError_t matmul(const Ctx& c, Site site, const double* A, int64_t lda, bool t
   return crt_product(g, ta, tb, site == S_GRAM ? 62 : 53, same, p.crt, p.crt_bytes, p.st, c.s);
 }
 
+// Tracing of a diagonal-block launch: its algorithmic work is the block
+// factorisation and the block inverse, (2/3) bw^3 flops with bw = the block
+// order (clamped to the device rank when factoring N).
+struct DiagTimer {
+  GemmParams g;
+  KernelTimer t;
+  template <class F>
+  cudaError_t run(int kind, cudaStream_t s, F&& f) {
+    t.gemm = &g;
+    return t.run(kind, s, f);
+  }
+};
+DiagTimer diag_timer(const Ctx& c, int64_t k0, int b, int spd) {
+  DiagTimer d;
+  std::memset(&d.g, 0, sizeof(d.g));
+  const Dim bw = spd ? rdim(-k0, b) : hdim(c.p->nA - k0 < b ? c.p->nA - k0 : b);
+  d.g.M = d.g.N = d.g.K = bw;
+  d.g.lower = 1;
+  d.g.rdev = c.rdev();
+  d.t.flops_mult = 2.0 / 3.0;
+  return d;
+}
+
 // Blocked full-rank Cholesky, in place on the lower triangle of a (ld = lda).
 // spd = 0: order nA (host), pivot test against the Appendix tolerance, mask
 //          written to acc.  spd = 1: order r (device), tolerance 0, block
@@ -384,7 +408,7 @@ int factor(const Ctx& c, double* a, int64_t lda, int spd) {
   const int b = p.b;
   for (int64_t k0 = 0, blk = 0; k0 < nA; k0 += b, ++blk) {
     const Dim nd = spd ? rdim(0, nA) : hdim(nA);
-    CK(KernelTimer().run(KT_DIAG, c.s, [&] {
+    CK(diag_timer(c, k0, b, spd).run(KT_DIAG, c.s, [&] {
       return launch_diag_factor(a, lda, nd, k0, b, p.st, c.rdev(), spd ? nullptr : p.acc, p.Z,
                                 spd ? p.Tinv + blk * b * b : nullptr, spd, c.s);
     }));
@@ -447,7 +471,7 @@ int factor_exact(const Ctx& c, double* a, int64_t lda, int spd) {
       CK(crt_reconstruct(R, Ly.rows, 256, M, N, c.rdev(), E + k0, E + k0, kCholBits, kCholBits,
                          -1.0, 1.0, a + k0 * lda + k0, lda, 1, Ly.n_mod, c.s, &t));
     }
-    CK(t.run(KT_DIAG, c.s, [&] {
+    CK(diag_timer(c, k0, b, spd).run(KT_DIAG, c.s, [&] {
       return launch_diag_factor(a, lda, nd, k0, b, p.st, c.rdev(), spd ? nullptr : p.acc, p.Z,
                                 spd ? p.Tinv + blk * b * b : nullptr, spd, c.s);
     }));
@@ -702,6 +726,9 @@ int run_pipeline(const Plan& p, cudaStream_t user, const GraphKey& key, Body&& b
 
 NoGraphScope::NoGraphScope() { ++t_no_graph; }
 NoGraphScope::~NoGraphScope() { --t_no_graph; }
+bool graph_replay_allowed() { return graphs_enabled(); }
+void launches_add(int64_t n) { g_launches.fetch_add(n); }
+cudaError_t trace_finish(cudaStream_t s, const int64_t* rdev) { return trace_resolve(s, rdev); }
 
 namespace {
 

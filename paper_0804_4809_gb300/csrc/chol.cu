@@ -176,21 +176,6 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
   return e2 ? scalbn(y, -e2 / 2) : y;
 }
 
-// 1/x for x > 0 by Newton's iteration y <- y (2 - x y) from a single-precision
-// seed; two FP64 steps give full double precision.
-__device__ __forceinline__ double rcp_newton(double x) {
-  int e2 = 0;
-  double xs = x;
-  if (x > 1e36 || x < 1e-36) {
-    e2 = ilogb(x);
-    xs = scalbn(x, -e2);
-  }
-  double y = (double)(1.0f / (float)xs);
-  y = y * fma(-xs, y, 2.0);
-  y = y * fma(-xs, y, 2.0);
-  return e2 ? scalbn(y, -e2) : y;
-}
-
 // The same factorisation for b <= 32, one warp per column of the block and
 // one lane per row: thread (lane i, warp j) keeps A(i, j) in a register.  The
 // FP64 pipe of one SM is narrow, so the mapping keeps the FP64 instructions
@@ -199,10 +184,9 @@ __device__ __forceinline__ double rcp_newton(double x) {
 // barriers per column.  The inverse of the identity-patched block factor is
 // then 32 independent forward substitutions, warp j solving T w = e_j with
 // shuffles only.
-__global__ void __launch_bounds__(1024) diag32_kernel(double* A, int64_t lda, Dim nd, int64_t k0,
-                                                      int b, DevState* st, const int64_t* rdev,
-                                                      uint8_t* accepted, double* Z, double* Tinv,
-                                                      int spd) {
+__device__ __forceinline__ void diag32_block(double* A, int64_t lda, Dim nd, int64_t k0, int b,
+                                             DevState* st, const int64_t* rdev, uint8_t* accepted,
+                                             double* Z, double* Tinv, int spd) {
   const int64_t n = eval_dim(nd, rdev);
   if (k0 >= n) return;
   const int bw = (int)((n - k0) < b ? (n - k0) : b);
@@ -271,6 +255,23 @@ __global__ void __launch_bounds__(1024) diag32_kernel(double* A, int64_t lda, Di
     }
   }
   if (!spd && accepted && threadIdx.x < bw) accepted[k0 + threadIdx.x] = (uint8_t)acc[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(1024) diag32_kernel(double* A, int64_t lda, Dim nd, int64_t k0,
+                                                      int b, DevState* st, const int64_t* rdev,
+                                                      uint8_t* accepted, double* Z, double* Tinv,
+                                                      int spd) {
+  diag32_block(A, lda, nd, k0, b, st, rdev, accepted, Z, Tinv, spd);
+}
+
+// One block per problem of a batch of equal-shaped problems (strides in
+// elements; st and the rank are per problem).
+__global__ void __launch_bounds__(1024) diag32_batched_kernel(DiagBatch p) {
+  const int64_t z = blockIdx.x;
+  DevState* st = p.st + z;
+  diag32_block(p.A + z * p.zA, p.lda, p.nd, p.k0, p.b, st, &st->rank,
+               p.accepted ? p.accepted + z * p.zAcc : nullptr, p.Z + z * p.zZ,
+               p.Tinv ? p.Tinv + z * p.zT : nullptr, p.spd);
 }
 
 // Prefix sum of the kept-pivot mask: colidx[c] = index of pivot c among the
@@ -381,6 +382,13 @@ cudaError_t launch_diag_factor(double* A, int64_t lda, Dim nd, int64_t k0, int b
     attr_set = true;
   }
   diag_factor_kernel<<<1, 256, smem, s>>>(A, lda, nd, k0, b, st, rdev, accepted, Z, Tinv, spd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag_batched(const DiagBatch& p, int nz, cudaStream_t s) {
+  if (p.b > 32 || p.b < 1) return cudaErrorInvalidValue;
+  if (nz <= 0) return cudaSuccess;
+  diag32_batched_kernel<<<nz, 1024, 0, s>>>(p);
   return cudaGetLastError();
 }
 

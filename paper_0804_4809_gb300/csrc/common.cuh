@@ -1,15 +1,18 @@
 // Shared definitions of the cpinv CUDA library (device side and host side).
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
 namespace cpinv {
 
-// A matrix dimension that may depend on the numerical rank r, which lives in
-// device memory (it is decided by the pivot tests on the GPU):
-//   value = clamp(off + sel * r, 0, max)
-// With sel = 0 it is the plain host value `off` (max >= off).
+// A matrix dimension that may depend on a value that lives in device memory,
+// such as the numerical rank r (it is decided by the pivot tests on the GPU):
+//   value = clamp(off + v, 0, max),  v = rdev[sel - 1] (0 when sel = 0)
+// where rdev points at a DevState (sel = 1: the rank; SEL_M / SEL_N: the
+// problem's own m and n in a batch).  With sel = 0 it is the plain host value
+// `off` (max >= off).
 struct Dim {
   int64_t off;
   int64_t max;
@@ -22,7 +25,7 @@ __host__ __device__ inline Dim hdim(int64_t v) { return Dim{v, v, 0, 0}; }
 __host__ __device__ inline Dim rdim(int64_t off, int64_t max) { return Dim{off, max, 1, 0}; }
 
 __device__ __forceinline__ int64_t eval_dim(const Dim& d, const int64_t* rdev) {
-  int64_t v = d.off + (d.sel ? *rdev : 0);
+  int64_t v = d.off + (d.sel ? rdev[d.sel - 1] : 0);
   v = v < 0 ? 0 : v;
   return v > d.max ? d.max : v;
 }
@@ -38,9 +41,17 @@ struct DevState {
   int32_t has_pos;  // 1 if some diagonal entry of A is > 0
   double tol;       // Appendix: rel_tol * min positive diagonal entry
   double min_pos;   // that minimum
-  int64_t pad[3];
+  int64_t dim_m;    // batched problems: this problem's m and n (else 0)
+  int64_t dim_n;
+  int64_t pad;
 };
 static_assert(sizeof(DevState) == 64, "DevState layout");
+// Dim::sel values that read DevState::dim_m and DevState::dim_n
+enum : int32_t { SEL_RANK = 1, SEL_M = 6, SEL_N = 7 };
+static_assert(offsetof(DevState, dim_m) == 8 * (SEL_M - 1), "SEL_M");
+static_assert(offsetof(DevState, dim_n) == 8 * (SEL_N - 1), "SEL_N");
+__host__ __device__ inline Dim mdim(int64_t max) { return Dim{0, max, SEL_M, 0}; }
+__host__ __device__ inline Dim ndim(int64_t off, int64_t max) { return Dim{off, max, SEL_N, 0}; }
 
 // Row-major matrix operand of a product C = alpha * op(A) op(B) + beta * C.
 // Element (i, k) of op(A) is  A[i*ld + k]  when !trans, else A[k*ld + i].
@@ -54,10 +65,17 @@ struct GemmParams {
   const int64_t* rdev;  // device rank, read when a Dim has sel = 1
   int32_t lower;        // 1: only C(i, j) with i >= j is computed and written
   int32_t pad;          // FP64 path: 1 if C aliases A or B (whole-row tiles)
-  // batch of nz products (FP64 path): product z uses A + z*zA, B + z*zB,
-  // C + z*zC and dimension offsets M.off + z*zM, N.off + z*zN, K.off + z*zK
+  // batch of nz products (FP64 path).  Index z = zi + nzi * zo when nzi > 1
+  // (two levels, e.g. the nodes of a level x the problems of a batch), else
+  // zi = z, zo = 0.  Product z uses A + zi*zA + zo*oA (B, C alike), rdev +
+  // zi*zR + zo*oR and dimension offsets M.off + zi*zM, N.off + zi*zN,
+  // K.off + zi*zK.
   int64_t zA, zB, zC;
   int32_t zM, zN, zK, nz;
+  int64_t zR;
+  int64_t oA, oB, oC, oR;
+  int32_t nzi;
+  int32_t pad2;
 };
 
 }  // namespace cpinv

@@ -22,13 +22,18 @@ template <bool TA, bool TB, int T>
 __global__ void __launch_bounds__(256) dgemm_kernel(GemmParams p) {
   constexpr int U = T / 16;
   if (blockIdx.z) {
-    const int64_t z = blockIdx.z;
-    p.A += z * p.zA;
-    p.B += z * p.zB;
-    p.C += z * p.zC;
+    int64_t z = blockIdx.z, zo = 0;
+    if (p.nzi > 1) {
+      zo = z / p.nzi;
+      z -= zo * p.nzi;
+    }
+    p.A += z * p.zA + zo * p.oA;
+    p.B += z * p.zB + zo * p.oB;
+    p.C += z * p.zC + zo * p.oC;
     p.M.off += z * p.zM;
     p.N.off += z * p.zN;
     p.K.off += z * p.zK;
+    p.rdev += z * p.zR + zo * p.oR;
   }
   const int64_t M = eval_dim(p.M, p.rdev);
   const int64_t N = eval_dim(p.N, p.rdev);

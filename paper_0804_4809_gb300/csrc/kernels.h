@@ -36,7 +36,8 @@ struct KernelTimer {
     if (!trace_on()) return f();
     const int rec = trace_begin(s);
     cudaError_t e = f();
-    trace_end(rec, s, kind, kind == KT_MMA || kind == KT_GEMM_FP64 ? gemm : nullptr, flops_mult);
+    trace_end(rec, s, kind, kind == KT_MMA || kind == KT_GEMM_FP64 || kind == KT_DIAG ? gemm : nullptr,
+              flops_mult);
     return e;
   }
 };
@@ -47,6 +48,10 @@ struct NoGraphScope {
   NoGraphScope();
   ~NoGraphScope();
 };
+bool graph_replay_allowed();  // CUDA graphs on, no NoGraphScope, no tracing
+void launches_add(int64_t n);  // kernels launched through a graph replay
+// flop counts of traced launches whose dims read the DevState at rdev
+cudaError_t trace_finish(cudaStream_t s, const int64_t* rdev);
 
 // One FP64-accurate product in the residue (exact-slice) arithmetic.
 struct CrtGemm {
@@ -101,6 +106,23 @@ cudaError_t launch_tol(const double* A, int64_t lda, int64_t n, double rel_tol, 
 cudaError_t launch_diag_factor(double* A, int64_t lda, Dim nd, int64_t k0, int b, DevState* st,
                                const int64_t* rdev, uint8_t* accepted, double* Z, double* Tinv,
                                int spd, cudaStream_t s);
+// Diagonal-block factorisation of panel k0 for a batch of nz equal-shaped
+// problems (b <= 32); problem z uses A + z*zA etc., st[z], rank st[z].rank.
+struct DiagBatch {
+  double* A;
+  int64_t lda, zA;
+  Dim nd;          // order of each problem's matrix (sel = 1: that problem's rank)
+  int64_t k0;
+  int32_t b, spd;
+  DevState* st;
+  uint8_t* accepted;
+  int64_t zAcc;
+  double* Z;
+  int64_t zZ;
+  double* Tinv;
+  int64_t zT;
+};
+cudaError_t launch_diag_batched(const DiagBatch& p, int nz, cudaStream_t s);
 cudaError_t launch_scan(const uint8_t* accepted, int64_t n, int32_t* colidx, DevState* st,
                         cudaStream_t s);
 cudaError_t launch_gather(const double* Lfull, int64_t lda, int64_t n, const int32_t* colidx,

@@ -92,24 +92,36 @@ class Problem:
     F: np.ndarray
 
 
-def batched_problems(P: int, seed: int, k: int = 4, m_range=(64, 1024),
-                     n_lo: int = 32, n_hi: int = 512):
-    """P rank-deficient least-squares problems of uneven size.
+def _rng_key(*keys: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(np.random.SeedSequence([int(k) for k in keys])))
 
-    m ~ U{m_lo..m_hi}, n ~ U{n_lo..min(m, n_hi)}, r ~ U{ceil(n/2)..n},
-    G = A(m x r) B(r x n) with N(0,1) factors, F m x k N(0,1).
-    """
-    g = _rng(seed)
-    out = []
-    for _ in range(P):
-        m = int(g.integers(m_range[0], m_range[1] + 1))
-        n = int(g.integers(n_lo, min(m, n_hi) + 1))
-        r = int(g.integers((n + 1) // 2, n + 1))
-        A = g.standard_normal((m, r))
-        B = g.standard_normal((r, n))
-        F = g.standard_normal((m, k))
-        out.append(Problem(m, n, r, np.ascontiguousarray(A @ B), F))
-    return out
+
+def batched_problem(seed: int, i: int, attempt: int = 0, k: int = 4, m_range=(64, 1024),
+                    n_lo: int = 32, n_hi: int = 512) -> "Problem":
+    """Problem slot i, draw ``attempt``, of ``batched_problems``: its own
+    stream keyed (seed, i, attempt); m ~ U{m_lo..m_hi}, n ~ U{n_lo..min(m,
+    n_hi)}, r ~ U{ceil(n/2)..n}, G = A(m x r) B(r x n) with N(0,1) factors,
+    F m x k N(0,1)."""
+    g = _rng_key(seed, i, attempt)
+    m = int(g.integers(m_range[0], m_range[1] + 1))
+    n = int(g.integers(n_lo, min(m, n_hi) + 1))
+    r = int(g.integers((n + 1) // 2, n + 1))
+    A = g.standard_normal((m, r))
+    B = g.standard_normal((r, n))
+    F = g.standard_normal((m, k))
+    return Problem(m, n, r, np.ascontiguousarray(A @ B), F)
+
+
+def batched_problems(P: int, seed: int, k: int = 4, m_range=(64, 1024),
+                     n_lo: int = 32, n_hi: int = 512, attempts: dict | None = None):
+    """P rank-deficient least-squares problems of uneven size (``batched_problem``
+    for slots 0..P-1).  ``attempts`` maps a slot to the draw to use (default
+    0): a re-drawn instance replaces one whose rank decision is too close to
+    the tolerance (the pivot-gap check is made by the test suite, which
+    stores the draws it chose)."""
+    attempts = attempts or {}
+    return [batched_problem(seed, i, attempts.get(i, 0), k, m_range, n_lo, n_hi)
+            for i in range(P)]
 
 
 # ---------------------------------------------------------------------------

@@ -103,3 +103,52 @@ def test_empty_sizes_need_no_gpu(lib):
         assert r.value == 0
         assert lib.cpinv_rank(None, m, n, max(n, 1), None, None, 0, ctypes.byref(o), ctypes.byref(r), None) == 0
         assert r.value == 0
+
+
+def test_batched_argument_checks_need_no_gpu(lib):
+    """cpinv_lstsq_batched validates every descriptor and option on the host
+    before any CUDA call."""
+    from paper_0804_4809_gb300 import cpinv
+    o = cpinv.make_opts("fp64")
+    fake = ctypes.c_void_p(0x100000)
+    P = cpinv.Problem
+
+    def arr(*ps):
+        a = (P * len(ps))()
+        for i, p in enumerate(ps):
+            a[i] = p
+        return a
+
+    good = P(100, 40, 4, fake, 40, fake, 4, fake, 4)
+    ws = lib.cpinv_lstsq_batched_workspace_size(1, arr(good), ctypes.byref(o))
+    assert ws > 100 * 40 * 8
+    # two problems in different n buckets need more than one
+    ws2 = lib.cpinv_lstsq_batched_workspace_size(2, arr(good, P(600, 300, 4, fake, 300, fake, 4, fake, 4)),
+                                                 ctypes.byref(o))
+    assert ws2 > ws
+    assert lib.cpinv_lstsq_batched(0, None, None, None, None, 0, ctypes.byref(o), None) == 0
+    assert lib.cpinv_lstsq_batched(1, None, None, None, fake, 1 << 30, ctypes.byref(o), None) == 1
+    ranks = (ctypes.c_int64 * 1)(5)
+    status = (ctypes.c_int32 * 1)(0)
+    cases = [
+        (P(100, 40, 4, None, 40, fake, 4, fake, 4), 1),     # G NULL
+        (P(100, 40, 4, fake, 39, fake, 4, fake, 4), 1),     # ldg < n
+        (P(100, 40, 0, fake, 40, fake, 4, fake, 4), 1),     # k = 0
+        (P(100, 40, 4, fake, 40, fake, 4, fake, 3), 1),     # ldw < k
+        (P(30, 40, 4, fake, 40, fake, 4, fake, 4), 6),      # n > m
+        (P(900, 513, 4, fake, 513, fake, 4, fake, 4), 6),   # n > 512
+        (P(900, 40, 257, fake, 40, fake, 257, fake, 257), 6),  # k > 256
+    ]
+    for p, code in cases:
+        assert lib.cpinv_lstsq_batched(1, arr(p), ranks, status, fake, 1 << 30, ctypes.byref(o), None) == code
+        assert ranks[0] == -1
+        assert lib.cpinv_lstsq_batched_workspace_size(1, arr(p), ctypes.byref(o)) == 0
+    # other arithmetic modes are not offered in the batch
+    ex = cpinv.make_opts("exact")
+    assert lib.cpinv_lstsq_batched(1, arr(good), None, None, fake, 1 << 30, ctypes.byref(ex), None) == 6
+    bad_panel = cpinv.make_opts("fp64", panel=24)
+    assert lib.cpinv_lstsq_batched(1, arr(good), None, None, fake, 1 << 30, ctypes.byref(bad_panel), None) == 1
+    # workspace misaligned or too small
+    assert lib.cpinv_lstsq_batched(1, arr(good), None, None, ctypes.c_void_p(0x100010), 1 << 30,
+                                   ctypes.byref(o), None) == 3
+    assert lib.cpinv_lstsq_batched(1, arr(good), None, None, fake, ws - 256, ctypes.byref(o), None) == 3
