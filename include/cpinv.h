@@ -106,6 +106,33 @@ int cpinv_lstsq(const double* G, int64_t m, int64_t n, int64_t ldg,
                 const cpinv_opts* o, int64_t* rank_out, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Adjoint of the least-squares weights (reverse mode): given the cotangent
+ * Wbar = dL/dW (n x k) of a scalar L of W = G+ F, returns
+ *   dG = dL/dG (m x n)  and, if dF != NULL, dF = dL/dF (m x k),
+ * the derivative of the function the Appendix computes with the kept-pivot
+ * set S held fixed (the rank decision is piecewise constant).  Steps: the
+ * chain of Theorem 1 reversed, the inverse of L'L, the full-rank Cholesky
+ * (kept rows: Cholesky adjoint; rejected rows: triangular solve, on the
+ * factor's structural pattern), and the Gram matrix A = G'G.  On inputs of
+ * exact rank whose rejected columns all follow the kept ones this equals
+ * the Golub-Pereyra derivative of G+.  The forward factors are recomputed
+ * (no state is kept between calls); W (if non-NULL) receives G+ F.
+ * Requires m >= n (else CPINV_ERR_UNSUPPORTED).  Arithmetic per opts->mode
+ * as for cpinv_lstsq.
+ *   dW : n x k, ld lddw >= k.  dG : m x n, ld lddg >= n.
+ *   dF : m x k, ld lddf >= k, or NULL.  W : n x k, ld ldw >= k, or NULL.
+ * ------------------------------------------------------------------------- */
+size_t cpinv_lstsq_backward_workspace_size(int64_t m, int64_t n, int64_t k,
+                                           const cpinv_opts* o);
+int cpinv_lstsq_backward(const double* G, int64_t m, int64_t n, int64_t ldg,
+                         const double* F, int64_t k, int64_t ldf,
+                         const double* dW, int64_t lddw,
+                         double* dG, int64_t lddg, double* dF, int64_t lddf,
+                         double* W, int64_t ldw,
+                         void* workspace, size_t workspace_bytes,
+                         const cpinv_opts* o, int64_t* rank_out, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Batched least squares: W_p = G_p+ F_p for P independent problems of
  * uneven size (Theorem 1 and the Appendix applied to each problem on its
  * own, with its own tolerance and rank), all enqueued on `stream` as one

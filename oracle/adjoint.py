@@ -50,11 +50,11 @@ def _phi(X: np.ndarray) -> np.ndarray:
     return P
 
 
-def _forward(G: np.ndarray, F: np.ndarray, rel_tol: float, exact_gram: bool):
+def _forward(G: np.ndarray, F: np.ndarray, rel_tol: float, exact_gram: bool, keep=None):
     """The forward quantities of the method for W = G+ F, m >= n."""
     A = gram(G, exact=exact_gram)
     tol = pivot_tolerance(A, rel_tol)
-    L, accepted, _ = full_rank_cholesky(A, tol)
+    L, accepted, _ = full_rank_cholesky(A, tol, keep=keep)
     N = L.T @ L
     M = np.linalg.inv(N) if L.shape[1] else np.zeros((0, 0))
     M = 0.5 * (M + M.T)
@@ -67,16 +67,17 @@ def _forward(G: np.ndarray, F: np.ndarray, rel_tol: float, exact_gram: bool):
 
 
 def lstsq_vjp(G: np.ndarray, F: np.ndarray, dW: np.ndarray, rel_tol: float = REL_TOL,
-              exact_gram: bool = True):
+              exact_gram: bool = True, keep=None):
     """(W, dG, dF) for W = G+ F and the cotangent dW (n x k): dG = dL/dG and
-    dF = dL/dF for any scalar L with dL/dW = dW, S held fixed."""
+    dF = dL/dF for any scalar L with dL/dW = dW, S held fixed (the pivot
+    test's, or ``keep`` when given)."""
     G = np.asarray(G, dtype=np.float64)
     F = np.asarray(F, dtype=np.float64)
     dW = np.asarray(dW, dtype=np.float64)
     m, n = G.shape
     if m < n:
-        return _vjp_transposed(G, F, dW, rel_tol, exact_gram)
-    fw = _forward(G, F, rel_tol, exact_gram)
+        return _vjp_transposed(G, F, dW, rel_tol, exact_gram, keep)
+    fw = _forward(G, F, rel_tol, exact_gram, keep)
     L, M, B = fw["L"], fw["M"], fw["B"]
     c1, c2, c3 = fw["c1"], fw["c2"], fw["c3"]
     acc = fw["accepted"]
@@ -121,14 +122,14 @@ def lstsq_vjp(G: np.ndarray, F: np.ndarray, dW: np.ndarray, rel_tol: float = REL
     return fw["W"], dG, dF
 
 
-def _vjp_transposed(G, F, dW, rel_tol, exact_gram):
+def _vjp_transposed(G, F, dW, rel_tol, exact_gram, keep=None):
     """m < n: the Appendix factors A = G G' (H = G', m x m Gram) and returns
     G+ = (H+)'; W = G+ F = G' (L M M L') F with L from A = H'H.  Chain:
     c1 = L'F, c2 = M c1, c3 = M c2, t = L c3, W = G' t."""
     H = G.T                                           # n x m, tall
     A = gram(H, exact=exact_gram)
     tol = pivot_tolerance(A, rel_tol)
-    L, acc, _ = full_rank_cholesky(A, tol)
+    L, acc, _ = full_rank_cholesky(A, tol, keep=keep)
     mA = A.shape[0]
     r = L.shape[1]
     if r == 0:

@@ -133,7 +133,7 @@ def pivot_tolerance(A: np.ndarray, rel_tol: float = REL_TOL):
     return float(pos.min()) * rel_tol
 
 
-def full_rank_cholesky(A: np.ndarray, tol, literal: bool = False):
+def full_rank_cholesky(A: np.ndarray, tol, literal: bool = False, keep=None):
     """Full-rank Cholesky of a symmetric positive semidefinite A (Appendix).
 
     Natural column order, no pivoting.  For k = 0..n-1, with r columns kept
@@ -147,6 +147,10 @@ def full_rank_cholesky(A: np.ndarray, tol, literal: bool = False):
     Returns ``(L, accepted, pivots)``: L is n x r (the kept columns, in
     order), ``accepted`` the boolean mask of kept pivot indices and
     ``pivots[k]`` the candidate value v[0] tested at step k.
+
+    ``keep`` (a boolean mask) replaces the pivot test by a given kept set:
+    the same function with S held fixed, whose derivative is the method's
+    derivative (``oracle.adjoint``).  A forced pivot must be positive.
     """
     A = np.asarray(A, dtype=np.float64)
     n = A.shape[0]
@@ -158,7 +162,7 @@ def full_rank_cholesky(A: np.ndarray, tol, literal: bool = False):
         # Matlab: L(k:n,r) = A(k:n,k) - L(k:n,1:(r-1))*L(k,1:(r-1))'
         v = A[k:, k] - L[k:, :r] @ L[k, :r]
         pivots[k] = v[0]
-        if tol is not None and v[0] > tol:
+        if (keep[k] and v[0] > 0) if keep is not None else (tol is not None and v[0] > tol):
             d = math.sqrt(v[0])
             L[k, r] = d
             if k + 1 < n:
@@ -173,12 +177,13 @@ def full_rank_cholesky(A: np.ndarray, tol, literal: bool = False):
 
 
 def geninv(G: np.ndarray, rel_tol: float = REL_TOL, literal: bool = False,
-           return_factors: bool = False, exact_gram: bool = True):
+           return_factors: bool = False, exact_gram: bool = True, keep=None):
     """Moore-Penrose inverse of any real rectangular G (Appendix ``geninv``).
 
     Returns Y = G+ (n x m).  With ``return_factors`` also returns a dict with
     the rank r, the accepted mask, L, M = inv(L'L), tol and whether the
-    transposed branch (m < n, A = G G') was taken.
+    transposed branch (m < n, A = G G') was taken.  ``keep`` forces the
+    kept-pivot set (see ``full_rank_cholesky``).
     """
     G = np.asarray(G, dtype=np.float64)
     if G.ndim != 2:
@@ -194,7 +199,7 @@ def geninv(G: np.ndarray, rel_tol: float = REL_TOL, literal: bool = False,
                    M=np.zeros((0, 0)), tol=None, transpose=transpose)
         return (Y, fac) if return_factors else Y
     tol = pivot_tolerance(A, rel_tol)
-    L, accepted, pivots = full_rank_cholesky(A, tol, literal=literal)
+    L, accepted, pivots = full_rank_cholesky(A, tol, literal=literal, keep=keep)
     r = L.shape[1]
     if r == 0:
         M = np.zeros((0, 0))
@@ -219,11 +224,11 @@ def rank(G: np.ndarray, rel_tol: float = REL_TOL, exact_gram: bool = True):
 
 
 def lstsq(G: np.ndarray, F: np.ndarray, rel_tol: float = REL_TOL,
-          exact_gram: bool = True) -> np.ndarray:
+          exact_gram: bool = True, keep=None) -> np.ndarray:
     """Minimum-norm least-squares weights W = G+ F (Sec. 1; the printed
     ``W = G+ W`` read as ``W = G+ F``)."""
     F = np.asarray(F, dtype=np.float64)
-    return geninv(G, rel_tol=rel_tol, exact_gram=exact_gram) @ F
+    return geninv(G, rel_tol=rel_tol, exact_gram=exact_gram, keep=keep) @ F
 
 
 def penrose_residuals(G: np.ndarray, Y: np.ndarray) -> dict:

@@ -69,6 +69,11 @@ SIGNATURES = {
     "cpinv_rank_workspace_size": (_c_sz, [_c_i64, _c_i64, ctypes.POINTER(Opts)]),
     "cpinv_rank": (ctypes.c_int, [_c_vp, _c_i64, _c_i64, _c_i64, _c_vp, _c_vp, _c_sz,
                                   ctypes.POINTER(Opts), ctypes.POINTER(_c_i64), _c_vp]),
+    "cpinv_lstsq_backward_workspace_size": (_c_sz, [_c_i64, _c_i64, _c_i64, ctypes.POINTER(Opts)]),
+    "cpinv_lstsq_backward": (ctypes.c_int, [_c_vp, _c_i64, _c_i64, _c_i64, _c_vp, _c_i64, _c_i64,
+                                            _c_vp, _c_i64, _c_vp, _c_i64, _c_vp, _c_i64, _c_vp,
+                                            _c_i64, _c_vp, _c_sz, ctypes.POINTER(Opts),
+                                            ctypes.POINTER(_c_i64), _c_vp]),
     "cpinv_lstsq_batched_workspace_size": (_c_sz, [ctypes.c_int32, ctypes.POINTER(Problem),
                                                    ctypes.POINTER(Opts)]),
     "cpinv_lstsq_batched": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(Problem),
@@ -204,6 +209,67 @@ def rank(G: torch.Tensor, mode="fp64", rel_tol: float = 1e-9, panel: int = 0, sl
                           _stream(G.device))
     _check(st)
     return int(r.value), mask
+
+
+def lstsq_backward(G: torch.Tensor, F: torch.Tensor, dW: torch.Tensor, mode="fp64",
+                   rel_tol: float = 1e-9, panel: int = 0, slices: int = 0, need_dF: bool = True,
+                   need_W: bool = False):
+    """Adjoint of W = G+ F: returns (dG, dF or None, W or None, rank) for the
+    cotangent dW = dL/dW, the kept-pivot set held fixed (m >= n)."""
+    G = _mat(G, "G")
+    F = _mat(F, "F")
+    dW = _mat(dW, "dW")
+    m, n = G.shape
+    k = F.shape[1]
+    if F.shape[0] != m or tuple(dW.shape) != (n, k):
+        raise ValueError("shapes: G m x n, F m x k, dW n x k")
+    o = make_opts(mode, rel_tol, panel, slices)
+    dG = torch.empty((m, n), dtype=torch.float64, device=G.device)
+    dF = torch.empty((m, k), dtype=torch.float64, device=G.device) if need_dF else None
+    W = torch.empty((n, k), dtype=torch.float64, device=G.device) if need_W else None
+    ws_bytes = lib().cpinv_lstsq_backward_workspace_size(m, n, k, ctypes.byref(o))
+    if ws_bytes == 0:
+        raise CpinvError(1, "invalid options or sizes")
+    ws = _workspace(ws_bytes, G.device)
+    r = _c_i64(-1)
+    st = lib().cpinv_lstsq_backward(
+        G.data_ptr(), m, n, _ld(G), F.data_ptr(), k, _ld(F), dW.data_ptr(), _ld(dW),
+        dG.data_ptr(), _ld(dG), dF.data_ptr() if dF is not None else None,
+        _ld(dF) if dF is not None else max(k, 1), W.data_ptr() if W is not None else None,
+        _ld(W) if W is not None else max(k, 1), ws.data_ptr(), ws.numel(), ctypes.byref(o),
+        ctypes.byref(r), _stream(G.device))
+    _check(st)
+    return dG, dF, W, int(r.value)
+
+
+class LstsqFunction(torch.autograd.Function):
+    """W = G+ F as a differentiable op: forward through cpinv_lstsq, backward
+    through the hand-written adjoint cpinv_lstsq_backward (kept-pivot set held
+    fixed)."""
+
+    @staticmethod
+    def forward(ctx, G, F, mode="fp64", rel_tol=1e-9):
+        W, r = lstsq(G, F, mode=mode, rel_tol=rel_tol)
+        ctx.save_for_backward(G, F)
+        ctx.mode = mode
+        ctx.rel_tol = rel_tol
+        ctx.rank = r
+        return W
+
+    @staticmethod
+    def backward(ctx, dW):
+        G, F = ctx.saved_tensors
+        need_G, need_F = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        if not (need_G or need_F):
+            return None, None, None, None
+        dG, dF, _, _ = lstsq_backward(G, F, dW.contiguous(), mode=ctx.mode, rel_tol=ctx.rel_tol,
+                                      need_dF=need_F)
+        return (dG if need_G else None), dF, None, None
+
+
+def lstsq_autograd(G: torch.Tensor, F: torch.Tensor, mode="fp64", rel_tol: float = 1e-9):
+    """Differentiable W = G+ F (see ``LstsqFunction``)."""
+    return LstsqFunction.apply(G, F, mode, rel_tol)
 
 
 class BatchedLstsq:

@@ -42,7 +42,7 @@ struct Arena {
 
 // (a batched problem's own m or n is not known here: its bound `max` stands in)
 int64_t eval_host(const Dim& d, int64_t r) {
-  int64_t v = d.off + (d.sel == SEL_RANK ? r : d.sel ? d.max : 0);
+  int64_t v = d.off + (d.sel == SEL_RANK ? r : d.sel == -SEL_RANK ? -r : d.sel ? d.max : 0);
   v = v < 0 ? 0 : v;
   return v > d.max ? d.max : v;
 }
@@ -124,7 +124,7 @@ void trace_end(int rec, cudaStream_t s, int kind, const GemmParams* g, double mu
 
 namespace {
 
-enum Job { JOB_RANK = 0, JOB_PINV = 1, JOB_LSTSQ = 2 };
+enum Job { JOB_RANK = 0, JOB_PINV = 1, JOB_LSTSQ = 2, JOB_BACKWARD = 3 };
 
 struct Plan {
   int64_t m, n, nA, k;
@@ -145,6 +145,20 @@ struct Plan {
   double* c1;    // lstsq: nA x k (also G'F)
   double* c2;
   double* c3;
+  // reverse pass (JOB_BACKWARD)
+  int32_t* pref;  // kept pivots among 0..i
+  int32_t* sidx;  // kept pivot indices, in order
+  int32_t* didx;  // rejected pivot indices, in order
+  double* e[5];   // nA x k: c3, cbar3, cbar2, cbar1, Bbar
+  double* Lb;     // nA x nA: Lbar
+  double* Mb;     // Mbar
+  double* LS;     // kept rows of L, then their Lbar
+  double* LbS;
+  double* LD;     // rejected rows of L, then their Lbar
+  double* LbD;
+  double* X;      // L_S^-1
+  double* S1;     // scratch
+  double* S2;
   void* crt;     // exact-slice scratch (residues, exponents)
   size_t crt_bytes;
 };
@@ -235,9 +249,16 @@ size_t crt_plan_bytes(const Plan& p, Job job) {
   mx(crt_need(p, S_CHAIN, nA, nA, nA, true));   // X X'
   mx(crt_need(p, S_CHAIN, nA, nA, nA, false));  // L M
   if (job == JOB_PINV) mx(crt_need(p, S_CHAIN, n, m, nA, false));  // G+ = K G' or G' K
-  if (job == JOB_LSTSQ) {
+  if (job == JOB_LSTSQ || job == JOB_BACKWARD) {
     mx(crt_need(p, S_CHAIN, n, p.k, m, false));   // G'F (or G't)
     mx(crt_need(p, S_CHAIN, nA, p.k, nA, false)); // L'c, M c, L c
+  }
+  if (job == JOB_BACKWARD) {
+    mx(crt_need(p, S_PROD, nA, nA, p.k, false));  // Wbar c3', B cbar1'
+    mx(crt_need(p, S_PROD, nA, nA, nA, false));   // the r x r products
+    mx(crt_need(p, S_CHAIN, m, n, n, false));     // Gbar = G (Abar + Abar')
+    mx(crt_need(p, S_CHAIN, m, n, p.k, false));   // + F Bbar'
+    mx(crt_need(p, S_CHAIN, m, p.k, n, false));   // Fbar = G Bbar
   }
   return need;
 }
@@ -258,11 +279,19 @@ void carve(Plan& p, Arena& a, Job job) {
   p.bufW = (double*)a.take(sizeof(double) * (size_t)(nA * nA));
   p.bufM = (double*)a.take(sizeof(double) * (size_t)(nA * nA));
   p.Tmp = (double*)a.take(sizeof(double) * (size_t)(b * nA));
-  if (job == JOB_LSTSQ) {
+  if (job == JOB_LSTSQ || job == JOB_BACKWARD) {
     const int64_t rows = p.n > p.m ? p.n : p.m;
     p.c1 = (double*)a.take(sizeof(double) * (size_t)(rows * p.k));
     p.c2 = (double*)a.take(sizeof(double) * (size_t)(nA * p.k));
     p.c3 = (double*)a.take(sizeof(double) * (size_t)(nA * p.k));
+  }
+  if (job == JOB_BACKWARD) {
+    p.pref = (int32_t*)a.take(sizeof(int32_t) * (size_t)nA);
+    p.sidx = (int32_t*)a.take(sizeof(int32_t) * (size_t)nA);
+    p.didx = (int32_t*)a.take(sizeof(int32_t) * (size_t)nA);
+    for (auto& x : p.e) x = (double*)a.take(sizeof(double) * (size_t)(nA * p.k));
+    double** sq[] = {&p.Lb, &p.Mb, &p.LS, &p.LbS, &p.LD, &p.LbD, &p.X, &p.S1, &p.S2};
+    for (double** q : sq) *q = (double*)a.take(sizeof(double) * (size_t)(nA * nA));
   }
 }
 
@@ -313,7 +342,7 @@ cudaError_t crt_product(const GemmParams& g, bool ta, bool tb, int bits, bool sa
     CrtGemm cg;
     cg.p = g;
     const int64_t kmax = K.max - k0 < kCrtMaxK ? K.max - k0 : kCrtMaxK;
-    cg.p.K = K.sel ? Dim{K.off - k0, kmax, 1, 0} : hdim(kmax < K.off - k0 ? kmax : K.off - k0);
+    cg.p.K = K.sel ? Dim{K.off - k0, kmax, K.sel, 0} : hdim(kmax < K.off - k0 ? kmax : K.off - k0);
     cg.p.A = ta ? g.A + k0 * g.lda : g.A + k0;
     cg.p.B = tb ? g.B + k0 : g.B + k0 * g.ldb;
     cg.p.beta = k0 == 0 ? g.beta : 1.0;
@@ -507,8 +536,8 @@ int front_rank(const Ctx& c, const double* G, int64_t ldg, bool compact) {
   return CPINV_OK;
 }
 
-// W = U^-1 for the lower-triangular U (order r <= nA) in bufA, given the
-// inverted b x b diagonal blocks already in W.  Recursive halving, done level
+// W = U^-1 for the lower-triangular U (order r <= nA, ld nA), given the
+// inverted b x b diagonal blocks already in W (ld nA); Tmp is nA x nA scratch.  Recursive halving, done level
 // by level from the smallest blocks up: a node [lo, lo + 2s) with children
 // [lo, mid) and [mid, mid + s) gets
 //   W21 = -W22 (U21 W11)        (bufM holds U21 W11)
@@ -516,7 +545,7 @@ int front_rank(const Ctx& c, const double* G, int64_t ldg, bool compact) {
 // power of two; nodes past the rank are empty), so a level is one batched
 // FP64 launch per product when its products are small, and per-node
 // tensor-core products when they are large.
-int tri_inverse(const Ctx& c) {
+int tri_inverse(const Ctx& c, const double* U, double* W, double* Tmp) {
   const Plan& p = *c.p;
   const int64_t nA = p.nA, b = p.b;
   int64_t nb = 1;
@@ -548,18 +577,18 @@ int tri_inverse(const Ctx& c) {
         return t.run(KT_GEMM_FP64, c.s, [&] { return launch_dgemm(g, false, false, c.s); });
       };
       // Tmp = U21 W11:  (rows mid.., cols lo..)
-      CK(batched(p.bufA + s * nA, p.bufW, p.bufM + s * nA, rows, cols, cols, 1.0));
+      CK(batched(U + s * nA, W, Tmp + s * nA, rows, cols, cols, 1.0));
       // W21 = -W22 Tmp
-      CK(batched(p.bufW + s * nA + s, p.bufM + s * nA, p.bufW + s * nA, rows, cols, rows, -1.0));
+      CK(batched(W + s * nA + s, Tmp + s * nA, W + s * nA, rows, cols, rows, -1.0));
     } else {
       for (int64_t z = 0; z < nodes; ++z) {
         const int64_t lo = 2 * s * z, mid = lo + s;
         if (mid >= nA) break;
         const Dim rz = rdim(-mid, s), cz = rdim(-lo, s);
-        CK(matmul(c, S_PROD, p.bufA + mid * nA + lo, nA, false, p.bufW + lo * nA + lo, nA, false,
-                  p.bufM + mid * nA + lo, nA, rz, cz, cz, 1.0, 0.0, 0));
-        CK(matmul(c, S_PROD, p.bufW + mid * nA + mid, nA, false, p.bufM + mid * nA + lo, nA, false,
-                  p.bufW + mid * nA + lo, nA, rz, cz, rz, -1.0, 0.0, 0));
+        CK(matmul(c, S_PROD, U + mid * nA + lo, nA, false, W + lo * nA + lo, nA, false,
+                  Tmp + mid * nA + lo, nA, rz, cz, cz, 1.0, 0.0, 0));
+        CK(matmul(c, S_PROD, W + mid * nA + mid, nA, false, Tmp + mid * nA + lo, nA, false,
+                  W + mid * nA + lo, nA, rz, cz, rz, -1.0, 0.0, 0));
       }
     }
   }
@@ -581,10 +610,109 @@ int front_inverse(const Ctx& c) {
   CK(KernelTimer().run(KT_AUX, c.s, [&] {
     return launch_tri_inv_init(p.bufW, nA, nA, c.rdev(), p.Tinv, b, c.s);
   }));
-  rc = tri_inverse(c);
+  rc = tri_inverse(c, p.bufA, p.bufW, p.bufM);
   if (rc) return rc;
   // M = W'W (full, symmetric)
   CK(matmul(c, S_PROD, p.bufW, nA, true, p.bufW, nA, false, p.bufM, nA, R, R, R, 1.0, 0.0, 0));
+  return CPINV_OK;
+}
+
+// Reverse pass of W = G+ F (m >= n) with the kept-pivot set S fixed, after
+// front_rank (with compaction) and front_inverse: L (n x r) in bufL, M =
+// (L'L)^-1 in bufM, the mask in acc, the kept index of each pivot in colidx.
+// Forward chain B = G'F, c1 = L'B, c2 = M c1, c3 = M c2, W = L c3, reversed:
+//   Lbar = Wbar c3' + B cbar1',  cbar3 = L'Wbar,  Mbar = cbar3 c2' + cbar2 c1',
+//   cbar2 = M cbar3,  cbar1 = M cbar2,  Bbar = L cbar1;
+//   Nbar = -M Mbar M,  Lbar += L (Nbar + Nbar');
+// the factor: Lbar masked to the factor's pattern (kept pivot c fills rows
+// from its own index down), split into kept rows (L_S, lower triangular,
+// L_S L_S' = A_SS) and rejected rows (L_D = A_DS L_S^-T on the pattern):
+//   Abar_DS = Lbar_D X,  Lbar_S -= X' (Lbar_D' L_D),  X = L_S^-1,
+//   Abar_SS = X' Phi(L_S' Lbar_S) X   (Phi: lower triangle, halved diagonal);
+// and A = G'G, B = G'F:  Gbar = G (Abar + Abar') + F Bbar',  Fbar = G Bbar.
+// Only the products with G or F (m rows) take the mode's tensor-core forms:
+// the r x r factors of the reverse pass (L_S^-1, Mbar, Nbar) span many
+// orders of magnitude within a row, where a fixed-point residue product of
+// 53 bits per row loses the small entries that FP64 keeps.
+int backward_body(const Ctx& c, const double* G, int64_t ldg, const double* F, int64_t ldf,
+                  const double* dW, int64_t lddw, double* dG, int64_t lddg, double* dF,
+                  int64_t lddf, double* W, int64_t ldw) {
+  const Plan& p = *c.p;
+  const int64_t n = p.n, m = p.m, k = p.k, nA = p.nA;
+  const Dim R = rdim(0, nA), Nn = hdim(n), Kk = hdim(k), Dd = ddim(nA, nA);
+  double* B = p.c1;                 // G'F        (n x k)
+  double* c1 = p.c2;                // L'B        (r x k)
+  double* c2 = p.c3;                // M c1
+  double* c3 = p.e[0];              // M c2
+  double *cb3 = p.e[1], *cb2 = p.e[2], *cb1 = p.e[3], *Bb = p.e[4];
+  // forward chain, keeping its intermediates
+  CK(matmul(c, S_CHAIN, G, ldg, true, F, ldf, false, B, k, Nn, Kk, hdim(m), 1.0, 0.0, 0));
+  CK(matmul(c, S_FP64, p.bufL, nA, true, B, k, false, c1, k, R, Kk, Nn, 1.0, 0.0, 0));
+  CK(matmul(c, S_FP64, p.bufM, nA, false, c1, k, false, c2, k, R, Kk, R, 1.0, 0.0, 0));
+  CK(matmul(c, S_FP64, p.bufM, nA, false, c2, k, false, c3, k, R, Kk, R, 1.0, 0.0, 0));
+  if (W) CK(matmul(c, S_FP64, p.bufL, nA, false, c3, k, false, W, ldw, Nn, Kk, R, 1.0, 0.0, 0));
+  // the chain, reversed
+  CK(matmul(c, S_FP64, p.bufL, nA, true, dW, lddw, false, cb3, k, R, Kk, Nn, 1.0, 0.0, 0));
+  CK(matmul(c, S_FP64, dW, lddw, false, c3, k, true, p.Lb, nA, Nn, R, Kk, 1.0, 0.0, 0));
+  CK(matmul(c, S_FP64, cb3, k, false, c2, k, true, p.Mb, nA, R, R, Kk, 1.0, 0.0, 0));
+  CK(matmul(c, S_FP64, p.bufM, nA, false, cb3, k, false, cb2, k, R, Kk, R, 1.0, 0.0, 0));
+  CK(matmul(c, S_FP64, cb2, k, false, c1, k, true, p.Mb, nA, R, R, Kk, 1.0, 1.0, 0));
+  CK(matmul(c, S_FP64, p.bufM, nA, false, cb2, k, false, cb1, k, R, Kk, R, 1.0, 0.0, 0));
+  CK(matmul(c, S_FP64, B, k, false, cb1, k, true, p.Lb, nA, Nn, R, Kk, 1.0, 1.0, 0));
+  CK(matmul(c, S_FP64, p.bufL, nA, false, cb1, k, false, Bb, k, Nn, Kk, R, 1.0, 0.0, 0));
+  // Nbar = -M Mbar M  (S1 = Mbar M, bufA = Nbar);  Lbar += L Nbar + L Nbar'
+  CK(matmul(c, S_FP64, p.Mb, nA, false, p.bufM, nA, false, p.S1, nA, R, R, R, 1.0, 0.0, 0));
+  CK(matmul(c, S_FP64, p.bufM, nA, false, p.S1, nA, false, p.bufA, nA, R, R, R, -1.0, 0.0, 0));
+  CK(matmul(c, S_FP64, p.bufL, nA, false, p.bufA, nA, false, p.Lb, nA, Nn, R, R, 1.0, 1.0, 0));
+  CK(matmul(c, S_FP64, p.bufL, nA, false, p.bufA, nA, true, p.Lb, nA, Nn, R, R, 1.0, 1.0, 0));
+  // the factor
+  KernelTimer t;
+  CK(t.run(KT_AUX, c.s,
+           [&] { return launch_pivot_lists(p.acc, nA, p.pref, p.sidx, p.didx, c.s); }));
+  CK(t.run(KT_AUX, c.s,
+           [&] { return launch_pattern_mask(p.Lb, nA, nA, p.pref, c.rdev(), c.s); }));
+  CK(t.run(KT_AUX, c.s, [&] {
+    cudaError_t e = launch_gather_rows(p.bufL, nA, p.sidx, nA, 0, c.rdev(), p.LS, nA, c.s);
+    if (e == cudaSuccess)
+      e = launch_gather_rows(p.Lb, nA, p.sidx, nA, 0, c.rdev(), p.LbS, nA, c.s);
+    if (e == cudaSuccess)
+      e = launch_gather_rows(p.bufL, nA, p.didx, nA, 1, c.rdev(), p.LD, nA, c.s);
+    if (e == cudaSuccess)
+      e = launch_gather_rows(p.Lb, nA, p.didx, nA, 1, c.rdev(), p.LbD, nA, c.s);
+    return e;
+  }));
+  // X = L_S^-1: inverted diagonal blocks, then the level-by-level recursion
+  const int b = p.b <= 32 ? p.b : 32;
+  CK(t.run(KT_AUX, c.s, [&] {
+    return launch_tri_block_inverse(p.LS, nA, nA, c.rdev(), b, p.Tinv, c.s);
+  }));
+  CK(t.run(KT_AUX, c.s,
+           [&] { return launch_tri_inv_init(p.X, nA, nA, c.rdev(), p.Tinv, b, c.s); }));
+  {
+    Plan q = p;
+    q.b = b;
+    q.mode = CPINV_MODE_FP64;  // see the note above on the r x r factors
+    const Ctx cq{c.s, &q};
+    if (int rc = tri_inverse(cq, p.LS, p.X, p.S1)) return rc;
+  }
+  // Abar_DS = Lbar_D X (into LD's place after its last use below: S2 first)
+  CK(matmul(c, S_FP64, p.LbD, nA, true, p.LD, nA, false, p.S1, nA, R, R, Dd, 1.0, 0.0, 0));
+  CK(matmul(c, S_FP64, p.X, nA, true, p.S1, nA, false, p.LbS, nA, R, R, R, -1.0, 1.0, 0));
+  CK(matmul(c, S_FP64, p.LbD, nA, false, p.X, nA, false, p.LD, nA, Dd, R, R, 1.0, 0.0, 0));
+  // Abar_SS = X' Phi(L_S' Lbar_S) X   (S1 = Phi(..), S2 = S1 X, LbD = X' S2)
+  CK(matmul(c, S_FP64, p.LS, nA, true, p.LbS, nA, false, p.S1, nA, R, R, R, 1.0, 0.0, 0));
+  CK(t.run(KT_AUX, c.s, [&] { return launch_phi(p.S1, nA, nA, c.rdev(), c.s); }));
+  CK(matmul(c, S_FP64, p.S1, nA, false, p.X, nA, false, p.S2, nA, R, R, R, 1.0, 0.0, 0));
+  CK(matmul(c, S_FP64, p.X, nA, true, p.S2, nA, false, p.LbD, nA, R, R, R, 1.0, 0.0, 0));
+  // As = Abar + Abar' (n x n, into S1)
+  CK(t.run(KT_AUX, c.s, [&] {
+    return launch_sym_scatter(p.LbD, nA, p.LD, nA, p.colidx, p.pref, nA, p.S1, nA, c.s);
+  }));
+  // Gbar = G As + F Bbar',  Fbar = G Bbar
+  CK(matmul(c, S_CHAIN, G, ldg, false, p.S1, nA, false, dG, lddg, hdim(m), Nn, Nn, 1.0, 0.0, 0));
+  CK(matmul(c, S_CHAIN, F, ldf, false, Bb, k, true, dG, lddg, hdim(m), Nn, Kk, 1.0, 1.0, 0));
+  if (dF)
+    CK(matmul(c, S_CHAIN, G, ldg, false, Bb, k, false, dF, lddf, hdim(m), Kk, Nn, 1.0, 0.0, 0));
   return CPINV_OK;
 }
 
@@ -598,10 +726,13 @@ int front_inverse(const Ctx& c) {
 // ---------------------------------------------------------------------------
 struct GraphKey {
   int32_t job, device, mode, panel;
-  int64_t m, n, k, ld1, ld2, ld3;
+  int64_t m, n, k, ld1, ld2, ld3, ld4, ld5, ld6;
   const void* p1;
   const void* p2;
   const void* p3;
+  const void* p4;
+  const void* p5;
+  const void* p6;
   void* ws;
   size_t ws_bytes;
   double rel_tol;
@@ -936,6 +1067,56 @@ int cpinv_lstsq(const double* G, int64_t m, int64_t n, int64_t ldg, const double
                 0));
     }
     return CPINV_OK;
+  });
+  if (rc) return rc;
+  return finish(Ctx{us, &p}, rank_out);
+}
+
+size_t cpinv_lstsq_backward_workspace_size(int64_t m, int64_t n, int64_t k, const cpinv_opts* o) {
+  Plan p{};
+  if (m < 0 || n < 0 || k < 0 || !make_plan(p, m, n, k, o)) return 0;
+  return plan_bytes(p, JOB_BACKWARD);
+}
+
+int cpinv_lstsq_backward(const double* G, int64_t m, int64_t n, int64_t ldg, const double* F,
+                         int64_t k, int64_t ldf, const double* dW, int64_t lddw, double* dG,
+                         int64_t lddg, double* dF, int64_t lddf, double* W, int64_t ldw,
+                         void* workspace, size_t workspace_bytes, const cpinv_opts* o,
+                         int64_t* rank_out, void* stream) {
+  if (rank_out) *rank_out = -1;
+  if (int rc = check_opts(o)) return rc;
+  if (m < 0 || n < 0 || k < 0 || ldg < n || ldf < k || lddw < k || lddg < n ||
+      (dF && lddf < k) || (W && ldw < k))
+    return CPINV_ERR_INVALID_ARG;
+  if (m < n) return CPINV_ERR_UNSUPPORTED;
+  cudaStream_t us = (cudaStream_t)stream;
+  if (m == 0 || n == 0 || k == 0) {
+    // W = 0 and both adjoints vanish
+    if (n > 0 && m > 0) {
+      if (!dG) return CPINV_ERR_INVALID_ARG;
+      CK(cudaMemset2DAsync(dG, (size_t)lddg * sizeof(double), 0, (size_t)n * sizeof(double),
+                           (size_t)m, us));
+    }
+    if (rank_out) *rank_out = 0;
+    if (k == 0 && m > 0 && n > 0 && rank_out)
+      return cpinv_rank(G, m, n, ldg, nullptr, workspace, workspace_bytes, o, rank_out, stream);
+    return CPINV_OK;
+  }
+  if (!G || !F || !dW || !dG) return CPINV_ERR_INVALID_ARG;
+  Plan p{};
+  if (!make_plan(p, m, n, k, o)) return CPINV_ERR_INVALID_ARG;
+  if (int rc = begin(p, JOB_BACKWARD, workspace, workspace_bytes)) return rc;
+  GraphKey key = make_key(JOB_BACKWARD, p, ldg, ldf, lddw, G, F, dW, workspace, workspace_bytes);
+  key.ld4 = lddg;
+  key.ld5 = dF ? lddf : 0;
+  key.ld6 = W ? ldw : 0;
+  key.p4 = dG;
+  key.p5 = dF;
+  key.p6 = W;
+  int rc = run_pipeline(p, us, key, [&](const Ctx& c) -> int {
+    if (int r = front_rank(c, G, ldg, true)) return r;
+    if (int r = front_inverse(c)) return r;
+    return backward_body(c, G, ldg, F, ldf, dW, lddw, dG, lddg, dF, lddf, W, ldw);
   });
   if (rc) return rc;
   return finish(Ctx{us, &p}, rank_out);

@@ -9,10 +9,11 @@ namespace cpinv {
 
 // A matrix dimension that may depend on a value that lives in device memory,
 // such as the numerical rank r (it is decided by the pivot tests on the GPU):
-//   value = clamp(off + v, 0, max),  v = rdev[sel - 1] (0 when sel = 0)
+//   value = clamp(off + v, 0, max),  v = rdev[sel - 1] for sel > 0,
+//                                    v = -rdev[-sel - 1] for sel < 0, 0 for sel = 0
 // where rdev points at a DevState (sel = 1: the rank; SEL_M / SEL_N: the
-// problem's own m and n in a batch).  With sel = 0 it is the plain host value
-// `off` (max >= off).
+// problem's own m and n in a batch; sel = -1: minus the rank, e.g. n - r).
+// With sel = 0 it is the plain host value `off` (max >= off).
 struct Dim {
   int64_t off;
   int64_t max;
@@ -23,9 +24,11 @@ struct Dim {
 __host__ __device__ inline Dim hdim(int64_t v) { return Dim{v, v, 0, 0}; }
 // r + off, clamped to [0, max]
 __host__ __device__ inline Dim rdim(int64_t off, int64_t max) { return Dim{off, max, 1, 0}; }
+// off - r, clamped to [0, max]
+__host__ __device__ inline Dim ddim(int64_t off, int64_t max) { return Dim{off, max, -1, 0}; }
 
 __device__ __forceinline__ int64_t eval_dim(const Dim& d, const int64_t* rdev) {
-  int64_t v = d.off + (d.sel ? rdev[d.sel - 1] : 0);
+  int64_t v = d.off + (d.sel > 0 ? rdev[d.sel - 1] : d.sel < 0 ? -rdev[-d.sel - 1] : 0);
   v = v < 0 ? 0 : v;
   return v > d.max ? d.max : v;
 }

@@ -132,4 +132,20 @@ cudaError_t launch_tri_inv_init(double* W, int64_t ldw, int64_t nmax, const int6
 cudaError_t launch_mirror(double* C, int64_t ldc, Dim nd, const int64_t* rdev, cudaStream_t s);
 cudaError_t launch_copy_mask(const uint8_t* src, uint8_t* dst, int64_t n, cudaStream_t s);
 
+
+// adjoint.cu (reverse pass of W = G+ F)
+cudaError_t launch_pivot_lists(const uint8_t* acc, int64_t n, int32_t* pref, int32_t* sidx,
+                               int32_t* didx, cudaStream_t s);
+cudaError_t launch_pattern_mask(double* Lb, int64_t ld, int64_t n, const int32_t* pref,
+                                const int64_t* rdev, cudaStream_t s);
+cudaError_t launch_gather_rows(const double* src, int64_t lds, const int32_t* idx, int64_t n,
+                               int count_rejected, const int64_t* rdev, double* dst, int64_t ldd,
+                               cudaStream_t s);
+cudaError_t launch_tri_block_inverse(const double* T, int64_t ld, int64_t nmax,
+                                     const int64_t* rdev, int b, double* Tinv, cudaStream_t s);
+cudaError_t launch_phi(double* P, int64_t ld, int64_t nmax, const int64_t* rdev, cudaStream_t s);
+cudaError_t launch_sym_scatter(const double* ASS, int64_t lss, const double* ADS, int64_t lds,
+                               const int32_t* colidx, const int32_t* pref, int64_t n, double* As,
+                               int64_t lda, cudaStream_t s);
+
 }  // namespace cpinv
