@@ -290,6 +290,7 @@ def ours(args):
     clocks = sampler.stop()
     e2e = run_e2e(modes[0], G_host, args.steps, device)
     batched = batched_bench(args, device, flush) if (not args.no_batched and ws == 1) else None
+    extras = rbf_and_adjoint_bench(args, device, flush) if (not args.no_batched and ws == 1) else None
 
     # max over ranks of the timed total
     head = modes[0]
@@ -394,6 +395,8 @@ def ours(args):
                                           f"4096x2048 input, median {t_cpu:.2f} s"}
     if batched is not None:
         line["batched"] = batched
+    if extras is not None:
+        line.update(extras)
     print(json.dumps(line), flush=True)
 
 
@@ -512,6 +515,37 @@ def batched_bench(args, device, flush, loop_steps: int = 2) -> dict:
         "algorithmic_gflop_per_batch": round(flops / 1e9, 3),
         "dtype": "f64",
     }
+
+
+def rbf_and_adjoint_bench(args, device, flush, steps: int = 3) -> dict:
+    """Device time per call of the RBF least-squares workload (16384 x 2048,
+    d = 8, k = 16) and of the adjoint workload (8192 x 1024 RBF, d = 4,
+    k = 8: forward W = G+ F plus the reverse pass) in each arithmetic mode."""
+    import torch
+
+    from paper_0804_4809_gb300 import cpinv, inputs
+    out = {"rbf_lstsq": {"workload": "RBF 16384 x 2048, d = 8, width 0.3, k = 16, seed 3"},
+           "adjoint": {"workload": "RBF 8192 x 1024, d = 4, width 0.3, k = 8, seed 5: "
+                                   "lstsq forward + cpinv_lstsq_backward"}}
+    G, F = inputs.workload_rbf()
+    Gd, Fd = torch.from_numpy(G).to(device), torch.from_numpy(F).to(device)
+    s = torch.cuda.current_stream(device)
+    for md in ("exact", "fp64", "bf16x3"):
+        W, r = cpinv.lstsq(Gd, Fd, mode=md)
+        ms = time_steps(lambda: cpinv.lstsq(Gd, Fd, mode=md, out=W, sync_rank=False), steps,
+                        flush, s)
+        t = sum(ms) / 1e3 / steps
+        out["rbf_lstsq"][md] = {"ms": round(t * 1e3, 3), "rank": r,
+                                "tflops": round(lstsq_flops(16384, 2048, r, 16) / t / 1e12, 3)}
+    G2, X2, _ = inputs.rbf_design(8192, 1024, 4, 0.3, 5)
+    F2 = inputs.smooth_targets(X2, 8, 5)
+    G2d, F2d = torch.from_numpy(G2).to(device), torch.from_numpy(F2).to(device)
+    dW = torch.ones((1024, 8), dtype=torch.float64, device=device)
+    for md in ("exact", "fp64", "bf16x3"):
+        _, _, _, r = cpinv.lstsq_backward(G2d, F2d, dW, mode=md)
+        ms = time_steps(lambda: cpinv.lstsq_backward(G2d, F2d, dW, mode=md), steps, flush, s)
+        out["adjoint"][md] = {"ms": round(sum(ms) / steps, 3), "rank": r}
+    return out
 
 
 def batched_main(args):
