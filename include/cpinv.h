@@ -67,7 +67,7 @@ typedef struct cpinv_opts {
   int32_t mode;      /* CPINV_MODE_* (default CPINV_MODE_FP64) */
   int32_t slices;    /* exact-slice mode: number of 8-bit slices per operand,
                         0 = default (7); ignored by the other modes */
-  int32_t panel;     /* Cholesky panel width, 0 = default; 16, 32 or 64 */
+  int32_t panel;     /* Cholesky panel width 1..32, 0 = default (32) */
   int32_t reserved;  /* must be 0 */
   double rel_tol;    /* pivot threshold factor; default 1e-9 (Appendix) */
 } cpinv_opts;

@@ -1,7 +1,6 @@
 // Small kernels of the reverse pass of W = G+ F (cpinv_lstsq_backward): the
 // bookkeeping of the kept-pivot set S (index lists, the factor's structural
-// pattern), row gathers, the inverse of the diagonal blocks of a triangular
-// factor, Phi (lower triangle with the diagonal halved) and the symmetrised
+// pattern), row gathers, Phi (lower triangle with the diagonal halved) and the symmetrised
 // scatter of the Gram adjoint.  The dense products of the pass go through the
 // library's FP64 / exact-slice / split products.
 #include "common.cuh"
@@ -79,39 +78,6 @@ __global__ void gather_rows_kernel(const double* src, int64_t lds, const int32_t
   }
 }
 
-// Inverse of each b x b diagonal block of the lower-triangular T (order r):
-// Tinv[q] (row-major b x b, zero-padded past r).  One CTA of 32 warps per
-// block; warp j solves T_qq w = e_j by forward substitution with shuffles.
-__global__ void __launch_bounds__(1024) tri_block_inverse_kernel(const double* T, int64_t ld,
-                                                                 const int64_t* rdev, int b,
-                                                                 double* Tinv) {
-  const int64_t r = *rdev;
-  const int64_t k0 = (int64_t)blockIdx.x * b;
-  double* out = Tinv + (int64_t)blockIdx.x * b * b;
-  const int i = threadIdx.x & 31, j = threadIdx.x >> 5;
-  if (k0 >= r) {
-    if (i < b && j < b) out[i * b + j] = 0.0;
-    return;
-  }
-  const int bw = (int)((r - k0) < b ? (r - k0) : b);
-  __shared__ double Ts[32][33];
-  Ts[i][j] = (i < bw && j < bw && j <= i) ? T[(k0 + i) * ld + (k0 + j)] : 0.0;
-  __syncthreads();
-  double w = 0.0;
-  if (j < bw) {
-    // w_i = (delta_ij - sum_{k<i} T_ik w_k) / T_ii, rows i = j.. in order
-    double x = 0.0;
-    for (int k = j; k < bw; ++k) {
-      double v = 0.0;
-      if (i == k) v = ((k == j ? 1.0 : 0.0) - x) / Ts[k][k];
-      const double wk = __shfl_sync(0xffffffffu, v, k);
-      if (i == k) w = wk;
-      if (i > k) x = fma(Ts[i][k], wk, x);
-    }
-  }
-  if (i < b && j < b) out[i * b + j] = (i < bw && j < bw && i >= j) ? w : 0.0;
-}
-
 // P = Phi(P): lower triangle with the diagonal halved, upper part zero
 // (order r).
 __global__ void phi_kernel(double* P, int64_t ld, const int64_t* rdev) {
@@ -167,14 +133,6 @@ cudaError_t launch_gather_rows(const double* src, int64_t lds, const int32_t* id
   if (n <= 0) return cudaSuccess;
   gather_rows_kernel<<<grid_n(n * n, 256), 256, 0, s>>>(src, lds, idx, n, count_rejected, rdev,
                                                          dst, ldd);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_tri_block_inverse(const double* T, int64_t ld, int64_t nmax,
-                                     const int64_t* rdev, int b, double* Tinv, cudaStream_t s) {
-  if (b < 1 || b > 32) return cudaErrorInvalidValue;
-  if (nmax <= 0) return cudaSuccess;
-  tri_block_inverse_kernel<<<(unsigned)((nmax + b - 1) / b), 1024, 0, s>>>(T, ld, rdev, b, Tinv);
   return cudaGetLastError();
 }
 

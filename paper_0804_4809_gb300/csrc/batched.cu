@@ -277,7 +277,7 @@ Layout make_layout(int P, const cpinv_problem* probs) {
     b.off_W = take(8 * nz * np * np);
     b.off_M = take(8 * nz * np * np);
     b.off_T = take(8 * nz * np * 32);  // (np / b) blocks of b x b, b <= 32
-    b.off_Z = take(8 * nz * 32 * 32);
+    b.off_Z = take(8 * nz * 32);       // 1/L_cc of the current block
     b.off_acc = take(nz * np);
     b.off_c1 = take(8 * nz * np * kp);
     b.off_c2 = take(8 * nz * np * kp);
@@ -349,46 +349,50 @@ struct BGemm {
 // Full-rank Cholesky of every problem of the bucket, right-looking by panels
 // of width b <= 32, in place on the lower triangles of A.  spd = 0: order n_z,
 // pivot test against the problem's tolerance, kept-pivot mask into acc.
-// spd = 1: order r_z, tolerance 0, block inverses into T.
+// spd = 1: order r_z, tolerance 0, inverses of the diagonal blocks into T.
 int bucket_factor(cudaStream_t s, const Bucket& bk, char* ws, int spd, int b) {
   const int nz = (int)bk.ids.size();
   const int64_t np = bk.np, nb = (np + b - 1) / b;
   double* A = (double*)(ws + bk.off_A);
   DevState* st = (DevState*)(ws + bk.off_st);
-  double* Z = (double*)(ws + bk.off_Z);
+  double* dinv = (double*)(ws + bk.off_Z);
   double* T = (double*)(ws + bk.off_T);
   uint8_t* acc = (uint8_t*)(ws + bk.off_acc);
   const int64_t zz = np * np;
   const int32_t sel = spd ? SEL_RANK : SEL_N;
-  for (int64_t k0 = 0, blk = 0; k0 < np; k0 += b, ++blk) {
+  const Dim nd{0, np, sel, 0};
+  for (int64_t k0 = 0; k0 < np; k0 += b) {
     DiagBatch d;
     std::memset(&d, 0, sizeof(d));
     d.A = A;
     d.lda = np;
     d.zA = zz;
-    d.nd = Dim{0, np, sel, 0};
+    d.nd = nd;
     d.k0 = k0;
     d.b = b;
     d.spd = spd;
     d.st = st;
     d.accepted = spd ? nullptr : acc;
     d.zAcc = np;
-    d.Z = Z;
-    d.zZ = (int64_t)b * b;
-    d.Tinv = spd ? T + blk * b * b : nullptr;
-    d.zT = nb * b * b;
+    d.dinv = dinv;
+    d.zDinv = 32;
     BK_CHECK(KernelTimer().run(KT_DIAG, s, [&] { return launch_diag_batched(d, nz, s); }));
     if (k0 + b >= np) continue;
+    PanelBatch pb;
+    std::memset(&pb, 0, sizeof(pb));
+    pb.A = A;
+    pb.lda = np;
+    pb.zA = zz;
+    pb.nd = nd;
+    pb.k0 = k0;
+    pb.b = b;
+    pb.dinv = dinv;
+    pb.zDinv = 32;
+    pb.st = st;
+    BK_CHECK(KernelTimer().run(KT_AUX, s, [&] { return launch_panel_solve_batched(pb, nz, s); }));
     double* panel = A + (k0 + b) * np + k0;
     double* trail = A + (k0 + b) * np + (k0 + b);
     const Dim below{-(k0 + b), np - k0 - b, sel, 0}, bw{-k0, b, sel, 0};
-    // L = A Z below the diagonal block (in place), then the trailing update
-    BK_CHECK(BGemm(nz, st)
-                 .a(panel, np, zz, false)
-                 .b(Z, b, (int64_t)b * b, false)
-                 .c(panel, np, zz)
-                 .dims(below, bw, bw)
-                 .run(s, 1.0, 0.0, 0));
     BK_CHECK(BGemm(nz, st)
                  .a(panel, np, zz, false)
                  .b(panel, np, zz, true)
@@ -396,6 +400,12 @@ int bucket_factor(cudaStream_t s, const Bucket& bk, char* ws, int spd, int b) {
                  .dims(below, below, bw)
                  .run(s, -1.0, 1.0, 1));
   }
+  if (spd)
+    BK_CHECK(KernelTimer().run(KT_AUX, s, [&] {
+      return launch_tri_block_inverse_batched(A, np, zz, np, &st->rank,
+                                              (int64_t)(sizeof(DevState) / sizeof(int64_t)), b, T,
+                                              nb * b * b, nz, s);
+    }));
   return CPINV_OK;
 }
 

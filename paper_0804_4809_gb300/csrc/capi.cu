@@ -135,7 +135,7 @@ struct Plan {
   DevState* st;
   uint8_t* acc;
   int32_t* colidx;
-  double* Z;
+  double* dinv;  // 1/L_cc of the current diagonal block (0: rejected)
   double* Tinv;
   double* bufA;  // A -> L_full -> N -> U -> K
   double* bufL;  // compact L (nA x nA, r columns used)
@@ -271,7 +271,7 @@ void carve(Plan& p, Arena& a, Job job) {
   p.crt = p.crt_bytes ? a.take(p.crt_bytes) : nullptr;
   p.acc = (uint8_t*)a.take((size_t)(nA > 0 ? nA : 1));
   p.colidx = (int32_t*)a.take(sizeof(int32_t) * (size_t)(nA > 0 ? nA : 1));
-  p.Z = (double*)a.take(sizeof(double) * (size_t)(b * b));
+  p.dinv = (double*)a.take(sizeof(double) * (size_t)b);
   p.bufA = (double*)a.take(sizeof(double) * (size_t)(nA * nA));
   if (job == JOB_RANK) return;
   p.Tinv = (double*)a.take(sizeof(double) * (size_t)(nb * b * b));
@@ -307,7 +307,7 @@ bool make_plan(Plan& p, int64_t m, int64_t n, int64_t k, const cpinv_opts* o) {
   p.b = o->panel ? o->panel : 32;
   p.mode = o->mode;
   p.rel_tol = o->rel_tol;
-  if (p.b < 1 || p.b > 64) return false;
+  if (p.b < 1 || p.b > 32) return false;
   if (!(p.rel_tol >= 0.0) || !std::isfinite(p.rel_tol)) return false;
   if (o->mode != CPINV_MODE_FP64 && o->mode != CPINV_MODE_EXACT_SLICE &&
       o->mode != CPINV_MODE_SPLIT_BF16X3)
@@ -429,19 +429,23 @@ DiagTimer diag_timer(const Ctx& c, int64_t k0, int b, int spd) {
 
 // Blocked full-rank Cholesky, in place on the lower triangle of a (ld = lda).
 // spd = 0: order nA (host), pivot test against the Appendix tolerance, mask
-//          written to acc.  spd = 1: order r (device), tolerance 0, block
-//          inverses stored in Tinv.
+//          written to acc.  spd = 1: order r (device), tolerance 0, and the
+//          inverses of the b x b diagonal blocks stored in Tinv at the end.
 int factor(const Ctx& c, double* a, int64_t lda, int spd) {
   const Plan& p = *c.p;
   const int64_t nA = p.nA;
   const int b = p.b;
-  for (int64_t k0 = 0, blk = 0; k0 < nA; k0 += b, ++blk) {
-    const Dim nd = spd ? rdim(0, nA) : hdim(nA);
+  const Dim nd = spd ? rdim(0, nA) : hdim(nA);
+  for (int64_t k0 = 0; k0 < nA; k0 += b) {
     CK(diag_timer(c, k0, b, spd).run(KT_DIAG, c.s, [&] {
-      return launch_diag_factor(a, lda, nd, k0, b, p.st, c.rdev(), spd ? nullptr : p.acc, p.Z,
-                                spd ? p.Tinv + blk * b * b : nullptr, spd, c.s);
+      return launch_diag_factor(a, lda, nd, k0, b, p.st, c.rdev(), spd ? nullptr : p.acc, p.dinv,
+                                spd, c.s);
     }));
     if (k0 + b >= nA) continue;
+    // panel below the block: forward substitution against the block factor
+    CK(KernelTimer().run(KT_AUX, c.s, [&] {
+      return launch_panel_solve(a, lda, nd, c.rdev(), k0, b, p.dinv, c.s);
+    }));
     double* panel = a + (k0 + b) * lda + k0;
     double* trail = a + (k0 + b) * lda + (k0 + b);
     Dim below, bw;
@@ -452,13 +456,14 @@ int factor(const Ctx& c, double* a, int64_t lda, int spd) {
       below = hdim(nA - k0 - b);
       bw = hdim(b);
     }
-    // panel below the block: L = A Z (in place; one column tile covers the panel)
-    CK(matmul(c, S_FP64, panel, lda, false, p.Z, b, false, panel, lda, below, bw, bw, 1.0, 0.0,
-              0));
     // trailing update, lower triangle
     CK(matmul(c, S_FP64, panel, lda, false, panel, lda, true, trail, lda, below, below, bw, -1.0,
               1.0, 1));
   }
+  if (spd)
+    CK(KernelTimer().run(KT_AUX, c.s, [&] {
+      return launch_tri_block_inverse(a, lda, nA, c.rdev(), b, p.Tinv, c.s);
+    }));
   return CPINV_OK;
 }
 
@@ -484,7 +489,7 @@ int factor_exact(const Ctx& c, double* a, int64_t lda, int spd) {
   KernelTimer t;
   CK(t.run(KT_AUX, c.s, [&] { return launch_rowscale(a, lda, nd, c.rdev(), Ly.rows, E, c.s); }));
   CK(cudaMemsetAsync(RL, 0, Ly.rl_bytes, c.s));
-  for (int64_t k0 = 0, blk = 0; k0 < nA; k0 += b, ++blk) {
+  for (int64_t k0 = 0; k0 < nA; k0 += b) {
     if (k0 > 0) {
       // A(k0:n, P) -= L(k0:n, 0:k0) L(P, 0:k0)'   exactly, from the residue planes
       const Dim M = spd ? rdim(-k0, nA - k0) : hdim(nA - k0);
@@ -501,14 +506,18 @@ int factor_exact(const Ctx& c, double* a, int64_t lda, int spd) {
                          -1.0, 1.0, a + k0 * lda + k0, lda, 1, Ly.n_mod, c.s, &t));
     }
     CK(diag_timer(c, k0, b, spd).run(KT_DIAG, c.s, [&] {
-      return launch_diag_factor(a, lda, nd, k0, b, p.st, c.rdev(), spd ? nullptr : p.acc, p.Z,
-                                spd ? p.Tinv + blk * b * b : nullptr, spd, c.s);
+      return launch_diag_factor(a, lda, nd, k0, b, p.st, c.rdev(), spd ? nullptr : p.acc, p.dinv,
+                                spd, c.s);
     }));
     CK(t.run(KT_AUX, c.s, [&] {
-      return launch_panel_solve_split(a, lda, nd, c.rdev(), k0, b, p.Z, E, Ly.n_mod, kCholBits,
-                                      RL, Ly.rows, Ly.kpad, c.s);
+      return launch_panel_solve_split(a, lda, nd, c.rdev(), k0, b, p.dinv, E, Ly.n_mod,
+                                      kCholBits, RL, Ly.rows, Ly.kpad, c.s);
     }));
   }
+  if (spd)
+    CK(t.run(KT_AUX, c.s, [&] {
+      return launch_tri_block_inverse(a, lda, nA, c.rdev(), b, p.Tinv, c.s);
+    }));
   return CPINV_OK;
 }
 
@@ -939,7 +948,7 @@ static int check_opts(const cpinv_opts* o) {
   if (o->mode != CPINV_MODE_FP64 && o->mode != CPINV_MODE_EXACT_SLICE &&
       o->mode != CPINV_MODE_SPLIT_BF16X3)
     return CPINV_ERR_INVALID_ARG;
-  if (o->panel < 0 || o->panel > 64 || o->reserved != 0) return CPINV_ERR_INVALID_ARG;
+  if (o->panel < 0 || o->panel > 32 || o->reserved != 0) return CPINV_ERR_INVALID_ARG;
   if (!(o->rel_tol >= 0.0) || !std::isfinite(o->rel_tol)) return CPINV_ERR_INVALID_ARG;
   return CPINV_OK;
 }

@@ -1,5 +1,5 @@
 // Full-rank Cholesky factorisation with device-side pivot tests (Appendix of
-// the paper), blocked by panels of width b <= 64, plus the small kernels
+// the paper), blocked by panels of width b <= 32, plus the small kernels
 // around it: the pivot tolerance, the column compaction and the diagonal
 // blocks of the triangular inverse.
 //
@@ -9,17 +9,18 @@
 // pivot c is rejected.  Every launch therefore has a host-known shape; the
 // kept columns are gathered into the compact n x r factor L afterwards.
 //
-// Panel p (columns k0 .. k0+bw-1), right-looking:
-//   1. diag_factor_kernel: one CTA factors the bw x bw diagonal block in
-//      shared memory column by column -- pivot d = A_cc minus the earlier
+// Panel p (columns k0 .. k0+bw-1):
+//   1. diag kernel: one CTA of four warps factors the bw x bw diagonal block
+//      in registers, column by column -- pivot d = A_cc minus the earlier
 //      in-block terms; kept iff d > tol (strict, NaN rejected, Appendix);
 //      L_cc = sqrt(d) and the column below is divided by it; a rejected
-//      column is zeroed.  It then forms Z, the bw x bw matrix with
-//      L_full(below, panel) = A(below, panel) Z, i.e. Z = (T^-1)' on the kept
-//      rows/columns (T = the kept rows and columns of the block factor) and 0
-//      elsewhere, so the panel below the block is one matrix product.
-//   2. A(below, panel) := A(below, panel) Z          (product, in place)
-//   3. A(trailing) -= L_full(trailing, panel) L_full(trailing, panel)'  (lower)
+//      column is zeroed.  It records 1/L_cc (0 for a rejected pivot).
+//   2. panel kernel: every row below the block solves x T' = a by forward
+//      substitution against the block factor T (one warp per row, many
+//      CTAs), so L_full(below, panel) needs no explicit block inverse.
+//   3. trailing update A(trailing) -= L_full(trailing, panel) L_full(..)'
+//      (right-looking FP64 form) or, in the exact-slice form, the next
+//      panel's left-looking update from residue planes (chol_exact.cu).
 #include <cmath>
 
 #include "common.cuh"
@@ -28,8 +29,6 @@
 namespace cpinv {
 
 namespace {
-
-constexpr int MAXB = 64;
 
 // tol = rel_tol * min{A_jj : A_jj > 0}; flags non-finite diagonal entries
 // (a NaN or Inf anywhere in G reaches the diagonal of its Gram column/row).
@@ -65,104 +64,11 @@ __global__ void tol_kernel(const double* A, int64_t lda, int64_t n, double rel_t
   }
 }
 
-// One CTA factors the diagonal block of panel `k0` (see the file comment).
-// `nd` is the order of the matrix being factored (host value, or the device
-// rank when factoring N = L'L).  spd = 1: tolerance 0 and every pivot must be
-// kept (else ST_NUMERICAL); the block inverse T^-1 is stored in Tinv.
-__global__ void __launch_bounds__(256) diag_factor_kernel(double* A, int64_t lda, Dim nd,
-                                                          int64_t k0, int b, DevState* st,
-                                                          const int64_t* rdev, uint8_t* accepted,
-                                                          double* Z, double* Tinv, int spd) {
-  const int64_t n = eval_dim(nd, rdev);
-  if (k0 >= n) return;
-  const int bw = (int)((n - k0) < b ? (n - k0) : b);
-  // dynamic shared memory: S and Wi (b x (b+1) doubles each), then acc (b ints)
-  extern __shared__ double smem[];
-  const int ls = b + 1;
-  double* Sm = smem;
-  double* Wm = smem + b * ls;
-  int* acc = (int*)(smem + 2 * b * ls);
-#define S(i, j) Sm[(i) * ls + (j)]
-#define Wi(i, j) Wm[(i) * ls + (j)]
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const double tol = spd ? 0.0 : st->tol;
-
-  for (int e = tid; e < bw * bw; e += nt) {
-    const int i = e / bw, j = e % bw;
-    S(i, j) = (j <= i) ? A[(k0 + i) * lda + (k0 + j)] : 0.0;
-  }
-  __syncthreads();
-
-  for (int c = 0; c < bw; ++c) {
-    const double d = S(c, c);
-    const bool ok = d > tol;  // false for NaN
-    __syncthreads();
-    if (ok) {
-      const double piv = sqrt(d);
-      for (int i = c + 1 + tid; i < bw; i += nt) S(i, c) /= piv;
-      if (tid == 0) S(c, c) = piv;
-      __syncthreads();
-      const int rem = bw - c - 1;
-      for (int e = tid; e < rem * rem; e += nt) {
-        const int ii = e / rem, jj = e % rem;
-        if (jj <= ii) S(c + 1 + ii, c + 1 + jj) -= S(c + 1 + ii, c) * S(c + 1 + jj, c);
-      }
-    } else {
-      for (int i = c + tid; i < bw; i += nt) S(i, c) = 0.0;
-    }
-    if (tid == 0) acc[c] = ok ? 1 : 0;
-    __syncthreads();
-  }
-
-  // Inverse of T' := the block factor with every rejected row replaced by the
-  // identity row; on the kept rows/columns it equals T^-1.  Column j by thread j.
-  if (tid < bw) {
-    const int j = tid;
-    for (int i = 0; i < j; ++i) Wi(i, j) = 0.0;
-    const double djj = acc[j] ? S(j, j) : 1.0;
-    Wi(j, j) = 1.0 / djj;
-    for (int i = j + 1; i < bw; ++i) {
-      double v;
-      if (acc[i]) {
-        double s = 0.0;
-        for (int k = j; k < i; ++k) s = fma(S(i, k), Wi(k, j), s);
-        v = -s / S(i, i);
-      } else {
-        v = 0.0;
-      }
-      Wi(i, j) = v;
-    }
-  }
-  __syncthreads();
-
-  // Write back the block of L_full (lower part), Z, the mask and T^-1.
-  for (int e = tid; e < bw * bw; e += nt) {
-    const int i = e / bw, j = e % bw;
-    if (j <= i) A[(k0 + i) * lda + (k0 + j)] = S(i, j);
-    // Z(c, j) = (T^-1)(j, c) on kept c and j, else 0.
-    const int c = i;
-    Z[c * b + j] = (acc[c] && acc[j]) ? Wi(j, c) : 0.0;
-    if (spd && Tinv) Tinv[i * b + j] = Wi(i, j);
-  }
-  if (tid == 0) {
-    int kept = 0;
-    for (int c = 0; c < bw; ++c) kept += acc[c];
-    if (spd) {
-      if (kept != bw) atomicOr(&st->status, ST_NUMERICAL);
-      atomicAdd((unsigned long long*)&st->rank_n, (unsigned long long)kept);
-    }
-  }
-  if (!spd && accepted)
-    for (int c = tid; c < bw; c += nt) accepted[k0 + c] = (uint8_t)acc[c];
-}
-#undef S
-#undef Wi
-
 // 1/sqrt(d) for d > 0 by Newton's iteration y <- y (3 - d y^2) / 2 from a
 // single-precision seed (about 22 correct bits); two FP64 steps bring it to
 // full double precision (each step doubles the correct bits).  Ranges beyond
 // float are handled by scaling d with an even power of two.
-__device__ __forceinline__ double rsqrt_newton(double d) {
+__device__ __noinline__ double rsqrt_newton(double d) {
   int e2 = 0;
   double ds = d;
   if (d > 1e36 || d < 1e-36) {
@@ -176,102 +82,226 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
   return e2 ? scalbn(y, -e2 / 2) : y;
 }
 
-// The same factorisation for b <= 32, one warp per column of the block and
-// one lane per row: thread (lane i, warp j) keeps A(i, j) in a register.  The
-// FP64 pipe of one SM is narrow, so the mapping keeps the FP64 instructions
-// per pivot to a minimum: the pivot (one lane), the column scaling (one warp
-// instruction), and one fused multiply-add per trailing column warp; two
-// barriers per column.  The inverse of the identity-patched block factor is
-// then 32 independent forward substitutions, warp j solving T w = e_j with
-// shuffles only.
-__device__ __forceinline__ void diag32_block(double* A, int64_t lda, Dim nd, int64_t k0, int b,
-                                             DevState* st, const int64_t* rdev, uint8_t* accepted,
-                                             double* Z, double* Tinv, int spd) {
+// Named barriers 1 and 2 (0 is __syncthreads): producer / consumer hand-off
+// of one column between the four warps of the diagonal-block kernel.
+__device__ __forceinline__ void bar_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+constexpr int kDiagWarps = 4;
+constexpr int kDiagThreads = 32 * kDiagWarps;
+
+// Factorisation of the diagonal block of panel k0 (b <= 32) by one CTA of
+// four warps.  Lane i holds row i; warp w holds the columns j = w (mod 4).
+// Column c is finished by its owner warp (pivot test, square root, scaling)
+// and handed to the others through a triple-buffered shared column and a
+// named barrier: the owner arrives, the others wait.  Look-ahead: the owner
+// of column c+1 applies the update of column c to that column first and
+// finishes it before its other updates, so the hand-off of every column
+// waits for one update and one pivot only.  The columns are processed in
+// groups of four (one per warp); after each group every warp's registers
+// shift by one column, so register indices stay compile-time constants in a
+// loop that is not unrolled (a fully unrolled factorisation is long enough
+// to stall on instruction fetch).  The sequence of operations on every entry
+// (updates in column order, the pivot, the scaling) is that of the plain
+// column-by-column algorithm.
+__device__ __forceinline__ void diag_chol_block(double* A, int64_t lda, Dim nd, int64_t k0, int b,
+                                                DevState* st, const int64_t* rdev,
+                                                uint8_t* accepted, double* dinv, int spd) {
   const int64_t n = eval_dim(nd, rdev);
   if (k0 >= n) return;
   const int bw = (int)((n - k0) < b ? (n - k0) : b);
-  __shared__ double Ls[32][33];   // Ls[row][col] = L(row, col)
-  __shared__ double colc[32];
-  __shared__ double dinv[32];
-  __shared__ int acc[32];
-  __shared__ int ok_s;
-  const int i = threadIdx.x & 31;   // row (lane)
-  const int j = threadIdx.x >> 5;   // column (warp)
-  const bool in = i < bw && j < bw && j <= i;
+  __shared__ double colbuf[3][32];
+  __shared__ double dinv_s[32];
+  __shared__ int acc_s[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const double tol = spd ? 0.0 : st->tol;
-  double a = in ? A[(k0 + i) * lda + (k0 + j)] : 0.0;
-
-  for (int c = 0; c < bw; ++c) {
-    if (j == c) {
-      // warp c: pivot in lane c, then the column
-      const double d = __shfl_sync(0xffffffffu, a, c);
-      const bool ok = d > tol;  // false for NaN
-      double y = 0.0;
-      if (ok) y = rsqrt_newton(d);
-      if (i == c) {
-        a = ok ? d * y : 0.0;   // sqrt(d)
-        ok_s = ok ? 1 : 0;
-        acc[c] = ok ? 1 : 0;
-        dinv[c] = ok ? y : 1.0;  // 1 / L_cc (1 on a rejected row: identity patch)
-      } else if (i > c) {
-        a = ok ? a * y : 0.0;
+  // a[q]: this lane's entry of column 4 (t + q) + w during group t
+  double a[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int j = w + kDiagWarps * q;
+    a[q] = (lane < bw && j < bw && j <= lane) ? A[(k0 + lane) * lda + (k0 + j)] : 0.0;
+  }
+  // Finishes column c held in `acol` (owner warp only); returns L(lane, c).
+  // The pivot test and 1/sqrt run on lane c alone (the FP64 pipe is narrow:
+  // a full-warp FP64 instruction costs many issue cycles), then y is
+  // broadcast and the column is scaled in one multiply.
+  auto pivot = [&](int c, double acol) -> double {
+    double y = 0.0;
+    int ok = 0;
+    if (lane == c) {
+      ok = acol > tol;  // false for NaN
+      if (ok) y = rsqrt_newton(acol);
+    }
+    y = __shfl_sync(0xffffffffu, y, c);
+    ok = __shfl_sync(0xffffffffu, ok, c);
+    const double l = (ok && lane >= c) ? acol * y : 0.0;  // lane c: d y = sqrt(d)
+    colbuf[c % 3][lane] = l;
+    if (lane == c) {
+      acc_s[c] = ok;
+      dinv_s[c] = y;
+    }
+    return l;
+  };
+  if (w == 0) {
+    a[0] = pivot(0, a[0]);
+    __syncwarp();
+    __threadfence_block();
+    bar_arrive(1, kDiagThreads);
+  }
+#pragma unroll 1
+  for (int t = 0; kDiagWarps * t < bw; ++t) {
+#pragma unroll
+    for (int u = 0; u < kDiagWarps; ++u) {
+      const int c = kDiagWarps * t + u;
+      if (c >= bw) break;
+      const int buf = c % 3;
+      if (w != u) bar_sync(1 + (c & 1), kDiagThreads);
+      else __syncwarp();
+      const double li = colbuf[buf][lane];
+      const int nxt = c + 1;
+      // the owner of column c+1 is warp (u+1) mod 4; the column is its a[0]
+      // within this group, its a[1] when it opens the next group
+      const int qn = (u + 1 < kDiagWarps) ? 0 : 1;
+      const bool ahead = nxt < bw && w == ((u + 1) & (kDiagWarps - 1));
+      if (ahead) {
+        if (lane >= nxt) a[qn] = fma(-li, colbuf[buf][nxt], a[qn]);
+        a[qn] = pivot(nxt, a[qn]);
+        __syncwarp();
+        __threadfence_block();
+        bar_arrive(1 + (nxt & 1), kDiagThreads);
       }
-      colc[i] = (i >= c) ? a : 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (q == 0 && w <= u) continue;  // column 4t + w is not after c
+        if (ahead && q == qn) continue;
+        const int j = kDiagWarps * (t + q) + w;
+        if (j < bw && lane >= j) a[q] = fma(-li, colbuf[buf][j], a[q]);
+      }
     }
-    __syncthreads();
-    if (ok_s && j > c && i >= j && i < bw) a = fma(-colc[i], colc[j], a);
-    __syncthreads();
+    // column 4t + w is final: store it, then shift the registers by one column
+    const int j0 = kDiagWarps * t + w;
+    if (j0 < bw && lane < bw && lane >= j0) A[(k0 + lane) * lda + (k0 + j0)] = a[0];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) a[q] = a[q + 1];
+    a[7] = 0.0;
   }
-  // a = L(i, j) for j <= i (rejected columns zero).  The inverse below works
-  // on T~(i, k) = T(i, k) / T(k, k) of the patched factor T (rejected rows
-  // are identity rows): with r the running right-hand side, r_i -= T~(i, k) r_k
-  // once r_k is final, and W(i, j) = r_i / T(i, i) at the end.
-  Ls[i][j] = (in && acc[i]) ? a * dinv[j] : 0.0;
   __syncthreads();
-
-  // warp j: column j of W = inverse of the patched factor, by forward
-  // substitution with shuffles only; lane i ends with W(i, j).
-  double w = 0.0;
-  if (j < bw) {
-    double r = (i == j) ? 1.0 : 0.0;
-    for (int k = j; k < bw; ++k) {
-      const double rk = __shfl_sync(0xffffffffu, r, k);
-      if (i > k) r = fma(-Ls[i][k], rk, r);
-    }
-    if (i >= j && i < bw) w = r * dinv[i];
-  }
-  if (i < bw && j < bw) {
-    if (j <= i) A[(k0 + i) * lda + (k0 + j)] = a;
-    // Z(c, jj) = W(jj, c) on kept c and jj: this thread's W(i, j) is Z(j, i)
-    Z[j * b + i] = (acc[i] && acc[j]) ? w : 0.0;
-    if (spd && Tinv) Tinv[i * b + j] = w;
+  if (threadIdx.x < bw) {
+    dinv[threadIdx.x] = dinv_s[threadIdx.x];
+    if (!spd && accepted) accepted[k0 + threadIdx.x] = (uint8_t)acc_s[threadIdx.x];
   }
   if (threadIdx.x == 0) {
     int kept = 0;
-    for (int c = 0; c < bw; ++c) kept += acc[c];
+    for (int c = 0; c < bw; ++c) kept += acc_s[c];
     if (spd) {
       if (kept != bw) atomicOr(&st->status, ST_NUMERICAL);
       atomicAdd((unsigned long long*)&st->rank_n, (unsigned long long)kept);
     }
   }
-  if (!spd && accepted && threadIdx.x < bw) accepted[k0 + threadIdx.x] = (uint8_t)acc[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(1024) diag32_kernel(double* A, int64_t lda, Dim nd, int64_t k0,
-                                                      int b, DevState* st, const int64_t* rdev,
-                                                      uint8_t* accepted, double* Z, double* Tinv,
-                                                      int spd) {
-  diag32_block(A, lda, nd, k0, b, st, rdev, accepted, Z, Tinv, spd);
+__global__ void __launch_bounds__(kDiagThreads) diag_chol_kernel(double* A, int64_t lda, Dim nd,
+                                                                 int64_t k0, int b, DevState* st,
+                                                                 const int64_t* rdev,
+                                                                 uint8_t* accepted, double* dinv,
+                                                                 int spd) {
+  diag_chol_block(A, lda, nd, k0, b, st, rdev, accepted, dinv, spd);
 }
 
 // One block per problem of a batch of equal-shaped problems (strides in
 // elements; st and the rank are per problem).
-__global__ void __launch_bounds__(1024) diag32_batched_kernel(DiagBatch p) {
+__global__ void __launch_bounds__(kDiagThreads) diag_chol_batched_kernel(DiagBatch p) {
   const int64_t z = blockIdx.x;
   DevState* st = p.st + z;
-  diag32_block(p.A + z * p.zA, p.lda, p.nd, p.k0, p.b, st, &st->rank,
-               p.accepted ? p.accepted + z * p.zAcc : nullptr, p.Z + z * p.zZ,
-               p.Tinv ? p.Tinv + z * p.zT : nullptr, p.spd);
+  diag_chol_block(p.A + z * p.zA, p.lda, p.nd, p.k0, p.b, st, &st->rank,
+                  p.accepted ? p.accepted + z * p.zAcc : nullptr, p.dinv + z * p.zDinv, p.spd);
+}
+
+// Rows below the diagonal block of panel k0: L(i, P) solves L(i, P) T' =
+// A(i, P) by forward substitution, T = the factored block (rejected
+// columns zero, 1/T_cc = dinv[c], 0 when rejected).  One warp per row, lane
+// c for column c; in place.
+constexpr int kPanelRows = 8;
+
+__device__ __forceinline__ void panel_solve_rows(double* A, int64_t lda, Dim nd,
+                                                 const int64_t* rdev, int64_t k0, int b,
+                                                 const double* dinv) {
+  const int64_t n = eval_dim(nd, rdev);
+  if (k0 >= n) return;
+  const int bw = (int)((n - k0) < b ? (n - k0) : b);
+  __shared__ double Ts[32][33];
+  __shared__ double dv[32];
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int r = e >> 5, c = e & 31;
+    Ts[r][c] = (r < bw && c <= r) ? A[(k0 + r) * lda + (k0 + c)] : 0.0;
+  }
+  if (threadIdx.x < 32) dv[threadIdx.x] = threadIdx.x < bw ? dinv[threadIdx.x] : 0.0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t i = k0 + bw + (int64_t)blockIdx.x * kPanelRows + (threadIdx.x >> 5);
+  if (i >= n) return;
+  double acc = lane < bw ? A[i * lda + k0 + lane] : 0.0;
+  double x = 0.0;
+  for (int c = 0; c < bw; ++c) {
+    const double xc = __shfl_sync(0xffffffffu, acc, c) * dv[c];
+    if (lane == c) x = xc;
+    if (lane > c) acc = fma(-xc, Ts[lane][c], acc);
+  }
+  if (lane < bw) A[i * lda + k0 + lane] = x;
+}
+
+__global__ void __launch_bounds__(32 * kPanelRows) panel_solve_kernel(double* A, int64_t lda,
+                                                                      Dim nd, const int64_t* rdev,
+                                                                      int64_t k0, int b,
+                                                                      const double* dinv) {
+  panel_solve_rows(A, lda, nd, rdev, k0, b, dinv);
+}
+
+__global__ void __launch_bounds__(32 * kPanelRows) panel_solve_batched_kernel(PanelBatch p) {
+  const int64_t z = blockIdx.y;
+  panel_solve_rows(p.A + z * p.zA, p.lda, p.nd, &p.st[z].rank, p.k0, p.b, p.dinv + z * p.zDinv);
+}
+
+// Inverse of each b x b diagonal block of the lower-triangular T (order r):
+// Tinv[q] (row-major b x b, zero past r).  One CTA of 32 warps per block,
+// grid.y over a batch; warp j solves T_qq w = e_j by forward substitution.
+__global__ void __launch_bounds__(1024) tri_block_inverse_kernel(const double* T, int64_t ld,
+                                                                 int64_t zT, const int64_t* rdev,
+                                                                 int64_t zR, int b, double* Tinv,
+                                                                 int64_t zTinv) {
+  const int64_t z = blockIdx.y;
+  T += z * zT;
+  Tinv += z * zTinv;
+  const int64_t r = rdev[z * zR];
+  const int64_t k0 = (int64_t)blockIdx.x * b;
+  double* out = Tinv + (int64_t)blockIdx.x * b * b;
+  const int i = threadIdx.x & 31, j = threadIdx.x >> 5;
+  if (k0 >= r) {
+    if (i < b && j < b) out[i * b + j] = 0.0;
+    return;
+  }
+  const int bw = (int)((r - k0) < b ? (r - k0) : b);
+  __shared__ double Ts[32][33];
+  Ts[i][j] = (i < bw && j < bw && j <= i) ? T[(k0 + i) * ld + (k0 + j)] : 0.0;
+  __syncthreads();
+  double w = 0.0;
+  if (j < bw) {
+    // w_k = (delta_kj - sum_{l<k} T_kl w_l) / T_kk for k = j..bw-1
+    double x = 0.0;
+    for (int k = j; k < bw; ++k) {
+      double v = 0.0;
+      if (i == k) v = ((k == j ? 1.0 : 0.0) - x) / Ts[k][k];
+      const double wk = __shfl_sync(0xffffffffu, v, k);
+      if (i == k) w = wk;
+      if (i > k) x = fma(Ts[i][k], wk, x);
+    }
+  }
+  if (i < b && j < b) out[i * b + j] = (i < bw && j < bw && i >= j) ? w : 0.0;
 }
 
 // Prefix sum of the kept-pivot mask: colidx[c] = index of pivot c among the
@@ -365,30 +395,54 @@ cudaError_t launch_tol(const double* A, int64_t lda, int64_t n, double rel_tol, 
 }
 
 cudaError_t launch_diag_factor(double* A, int64_t lda, Dim nd, int64_t k0, int b, DevState* st,
-                               const int64_t* rdev, uint8_t* accepted, double* Z, double* Tinv,
-                               int spd, cudaStream_t s) {
-  if (b > MAXB || b < 1) return cudaErrorInvalidValue;
-  if (b <= 32) {
-    diag32_kernel<<<1, 1024, 0, s>>>(A, lda, nd, k0, b, st, rdev, accepted, Z, Tinv, spd);
-    return cudaGetLastError();
-  }
-  const size_t smem = sizeof(double) * 2 * b * (b + 1) + sizeof(int) * b;
-  static bool attr_set = false;
-  if (!attr_set) {
-    const size_t maxsmem = sizeof(double) * 2 * MAXB * (MAXB + 1) + sizeof(int) * MAXB;
-    cudaError_t e = cudaFuncSetAttribute(diag_factor_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxsmem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  diag_factor_kernel<<<1, 256, smem, s>>>(A, lda, nd, k0, b, st, rdev, accepted, Z, Tinv, spd);
+                               const int64_t* rdev, uint8_t* accepted, double* dinv, int spd,
+                               cudaStream_t s) {
+  if (b > 32 || b < 1) return cudaErrorInvalidValue;
+  diag_chol_kernel<<<1, kDiagThreads, 0, s>>>(A, lda, nd, k0, b, st, rdev, accepted, dinv, spd);
   return cudaGetLastError();
 }
 
 cudaError_t launch_diag_batched(const DiagBatch& p, int nz, cudaStream_t s) {
   if (p.b > 32 || p.b < 1) return cudaErrorInvalidValue;
   if (nz <= 0) return cudaSuccess;
-  diag32_batched_kernel<<<nz, 1024, 0, s>>>(p);
+  diag_chol_batched_kernel<<<nz, kDiagThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_panel_solve(double* A, int64_t lda, Dim nd, const int64_t* rdev, int64_t k0,
+                               int b, const double* dinv, cudaStream_t s) {
+  if (b > 32 || b < 1) return cudaErrorInvalidValue;
+  const int64_t rows = nd.max - k0 - b;
+  if (rows <= 0) return cudaSuccess;
+  panel_solve_kernel<<<(unsigned)((rows + kPanelRows - 1) / kPanelRows), 32 * kPanelRows, 0, s>>>(
+      A, lda, nd, rdev, k0, b, dinv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_panel_solve_batched(const PanelBatch& p, int nz, cudaStream_t s) {
+  if (p.b > 32 || p.b < 1) return cudaErrorInvalidValue;
+  const int64_t rows = p.nd.max - p.k0 - p.b;
+  if (rows <= 0 || nz <= 0) return cudaSuccess;
+  if (nz > 65535) return cudaErrorInvalidConfiguration;
+  dim3 grid((unsigned)((rows + kPanelRows - 1) / kPanelRows), (unsigned)nz);
+  panel_solve_batched_kernel<<<grid, 32 * kPanelRows, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tri_block_inverse(const double* T, int64_t ld, int64_t nmax,
+                                     const int64_t* rdev, int b, double* Tinv, cudaStream_t s) {
+  return launch_tri_block_inverse_batched(T, ld, 0, nmax, rdev, 0, b, Tinv, 0, 1, s);
+}
+
+cudaError_t launch_tri_block_inverse_batched(const double* T, int64_t ld, int64_t zT,
+                                             int64_t nmax, const int64_t* rdev, int64_t zR, int b,
+                                             double* Tinv, int64_t zTinv, int nz,
+                                             cudaStream_t s) {
+  if (b < 1 || b > 32) return cudaErrorInvalidValue;
+  if (nmax <= 0 || nz <= 0) return cudaSuccess;
+  if (nz > 65535) return cudaErrorInvalidConfiguration;
+  dim3 grid((unsigned)((nmax + b - 1) / b), (unsigned)nz);
+  tri_block_inverse_kernel<<<grid, 1024, 0, s>>>(T, ld, zT, rdev, zR, b, Tinv, zTinv);
   return cudaGetLastError();
 }
 

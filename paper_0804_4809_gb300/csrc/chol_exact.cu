@@ -38,44 +38,47 @@ __global__ void rowscale_kernel(const double* A, int64_t lda, Dim nd, const int6
   }
 }
 
-// Rows [k0, n) of panel k0: below the diagonal block, L(i, P) = A(i, P) Z (in
-// place); every row of the panel (diagonal block included) is then cut into
-// residues with the row scale E[i] and written to RL[j][i][k0 + c].
-// One 8-row x 32-column block of threads per 8 rows (many CTAs: the FP64
-// pipe of each SM is narrow).
+// Rows [k0, n) of panel k0: below the diagonal block, L(i, P) solves
+// L(i, P) T' = A(i, P) by forward substitution against the factored block T
+// (1/T_cc = dinv[c], 0 for a rejected pivot; in place); every row of the
+// panel (diagonal block included) is then cut into residues with the row
+// scale E[i] and written to RL[j][i][k0 + c].  One warp per row, lane c for
+// column c; many CTAs (the FP64 pipe of each SM is narrow).
 constexpr int kPanelRows = 8;
 
 __global__ void __launch_bounds__(256) panel_solve_split_kernel(
-    double* A, int64_t lda, Dim nd, const int64_t* rdev, int64_t k0, int b, const double* Z,
+    double* A, int64_t lda, Dim nd, const int64_t* rdev, int64_t k0, int b, const double* dinv,
     const int32_t* E, int n_mod, int beta, __nv_bfloat16* RL, int64_t rl_rows, int64_t rl_kpad) {
   const int64_t n = eval_dim(nd, rdev);
   if (k0 >= n) return;
   const int bw = (int)((n - k0) < b ? (n - k0) : b);
-  __shared__ double Zs[32][33];
-  __shared__ double Arow[kPanelRows][33];
-  const int ri = threadIdx.x >> 5, c = threadIdx.x & 31;
+  __shared__ double Ts[32][33];
+  __shared__ double dv[32];
   for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
-    const int zr = e >> 5, zc = e & 31;
-    Zs[zr][zc] = (zr < bw && zc < bw) ? Z[zr * b + zc] : 0.0;
+    const int r = e >> 5, c = e & 31;
+    Ts[r][c] = (r < bw && c <= r) ? A[(k0 + r) * lda + (k0 + c)] : 0.0;
   }
-  const int64_t i = k0 + (int64_t)blockIdx.x * kPanelRows + ri;
-  const bool row_ok = i < n;
-  const bool below = i >= k0 + bw;
-  double v = 0.0;
-  if (row_ok && c < bw) v = A[i * lda + k0 + c];
-  Arow[ri][c] = v;
+  if (threadIdx.x < 32) dv[threadIdx.x] = threadIdx.x < bw ? dinv[threadIdx.x] : 0.0;
   __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t i = k0 + (int64_t)blockIdx.x * kPanelRows + (threadIdx.x >> 5);
+  if (i >= n) return;
   double l = 0.0;
-  if (row_ok && c < bw) {
-    if (below) {
-      for (int k = 0; k < bw; ++k) l = fma(Arow[ri][k], Zs[k][c], l);
-      A[i * lda + k0 + c] = l;
-    } else {
-      l = (c <= i - k0) ? v : 0.0;  // diagonal block: already the factor
+  if (i >= k0 + bw) {
+    double acc = lane < bw ? A[i * lda + k0 + lane] : 0.0;
+    for (int c = 0; c < bw; ++c) {
+      const double xc = __shfl_sync(0xffffffffu, acc, c) * dv[c];
+      if (lane == c) l = xc;
+      if (lane > c) acc = fma(-xc, Ts[lane][c], acc);
     }
+    if (lane < bw) A[i * lda + k0 + lane] = l;
+  } else {
+    l = Ts[i - k0][lane];  // diagonal block: already the factor (zero above)
+  }
+  if (lane < bw) {
     const uint64_t bits = (uint64_t)__double_as_longlong(l);
     const uint64_t a = crt::integerize(bits, E[i], beta);
-    crt::store_residues(a, (bits >> 63) != 0, n_mod, RL + (size_t)i * rl_kpad + (k0 + c),
+    crt::store_residues(a, (bits >> 63) != 0, n_mod, RL + (size_t)i * rl_kpad + (k0 + lane),
                         (size_t)rl_rows * (size_t)rl_kpad);
   }
 }
@@ -95,14 +98,14 @@ cudaError_t launch_rowscale(const double* A, int64_t lda, Dim nd, const int64_t*
 }
 
 cudaError_t launch_panel_solve_split(double* A, int64_t lda, Dim nd, const int64_t* rdev,
-                                     int64_t k0, int b, const double* Z, const int32_t* E,
+                                     int64_t k0, int b, const double* dinv, const int32_t* E,
                                      int n_mod, int beta, void* RL, int64_t rl_rows,
                                      int64_t rl_kpad, cudaStream_t s) {
   if (b > 32) return cudaErrorInvalidValue;
   const int64_t rows = nd.max - k0;
   if (rows <= 0) return cudaSuccess;
   panel_solve_split_kernel<<<(unsigned)((rows + kPanelRows - 1) / kPanelRows), 256, 0, s>>>(
-      A, lda, nd, rdev, k0, b, Z, E, n_mod, beta, (__nv_bfloat16*)RL, rl_rows, rl_kpad);
+      A, lda, nd, rdev, k0, b, dinv, E, n_mod, beta, (__nv_bfloat16*)RL, rl_rows, rl_kpad);
   return cudaGetLastError();
 }
 

@@ -93,7 +93,7 @@ cudaError_t crt_reconstruct(const uint8_t* R, int64_t Mpad, int64_t Npad, Dim M,
 cudaError_t launch_rowscale(const double* A, int64_t lda, Dim nd, const int64_t* rdev,
                             int64_t rows_max, int32_t* E, cudaStream_t s);
 cudaError_t launch_panel_solve_split(double* A, int64_t lda, Dim nd, const int64_t* rdev,
-                                     int64_t k0, int b, const double* Z, const int32_t* E,
+                                     int64_t k0, int b, const double* dinv, const int32_t* E,
                                      int n_mod, int beta, void* RL, int64_t rl_rows,
                                      int64_t rl_kpad, cudaStream_t s);
 
@@ -103,26 +103,51 @@ cudaError_t launch_dgemm(const GemmParams& p, bool transA, bool transB, cudaStre
 // chol.cu
 cudaError_t launch_tol(const double* A, int64_t lda, int64_t n, double rel_tol, DevState* st,
                        cudaStream_t s);
+// Diagonal block of panel k0 (b <= 32): factor in place, 1/L_cc into dinv[c]
+// (0 for a rejected pivot), kept mask into accepted (spd = 0).  spd = 1:
+// tolerance 0, every pivot must be kept (else ST_NUMERICAL), kept count
+// added to st->rank_n.
 cudaError_t launch_diag_factor(double* A, int64_t lda, Dim nd, int64_t k0, int b, DevState* st,
-                               const int64_t* rdev, uint8_t* accepted, double* Z, double* Tinv,
-                               int spd, cudaStream_t s);
-// Diagonal-block factorisation of panel k0 for a batch of nz equal-shaped
-// problems (b <= 32); problem z uses A + z*zA etc., st[z], rank st[z].rank.
+                               const int64_t* rdev, uint8_t* accepted, double* dinv, int spd,
+                               cudaStream_t s);
+// The same for a batch of nz equal-shaped problems (b <= 32); problem z uses
+// A + z*zA etc., st[z] and the dims' device values of st[z].
 struct DiagBatch {
   double* A;
   int64_t lda, zA;
-  Dim nd;          // order of each problem's matrix (sel = 1: that problem's rank)
+  Dim nd;          // order of each problem's matrix
   int64_t k0;
   int32_t b, spd;
   DevState* st;
   uint8_t* accepted;
   int64_t zAcc;
-  double* Z;
-  int64_t zZ;
-  double* Tinv;
-  int64_t zT;
+  double* dinv;
+  int64_t zDinv;
 };
 cudaError_t launch_diag_batched(const DiagBatch& p, int nz, cudaStream_t s);
+// Rows below the diagonal block of panel k0: L(i, P) T' = A(i, P) by forward
+// substitution against the factored block (in place).
+cudaError_t launch_panel_solve(double* A, int64_t lda, Dim nd, const int64_t* rdev, int64_t k0,
+                               int b, const double* dinv, cudaStream_t s);
+struct PanelBatch {
+  double* A;
+  int64_t lda, zA;
+  Dim nd;
+  int64_t k0;
+  int32_t b, pad;
+  const double* dinv;
+  int64_t zDinv;
+  const DevState* st;
+};
+cudaError_t launch_panel_solve_batched(const PanelBatch& p, int nz, cudaStream_t s);
+// Inverses of the b x b diagonal blocks of a lower-triangular matrix of
+// order r = *rdev (b <= 32), Tinv[q] row-major b x b; batched form: problem z
+// uses T + z*zT, rdev[z*zR], Tinv + z*zTinv.
+cudaError_t launch_tri_block_inverse(const double* T, int64_t ld, int64_t nmax,
+                                     const int64_t* rdev, int b, double* Tinv, cudaStream_t s);
+cudaError_t launch_tri_block_inverse_batched(const double* T, int64_t ld, int64_t zT,
+                                             int64_t nmax, const int64_t* rdev, int64_t zR, int b,
+                                             double* Tinv, int64_t zTinv, int nz, cudaStream_t s);
 cudaError_t launch_scan(const uint8_t* accepted, int64_t n, int32_t* colidx, DevState* st,
                         cudaStream_t s);
 cudaError_t launch_gather(const double* Lfull, int64_t lda, int64_t n, const int32_t* colidx,
@@ -141,8 +166,6 @@ cudaError_t launch_pattern_mask(double* Lb, int64_t ld, int64_t n, const int32_t
 cudaError_t launch_gather_rows(const double* src, int64_t lds, const int32_t* idx, int64_t n,
                                int count_rejected, const int64_t* rdev, double* dst, int64_t ldd,
                                cudaStream_t s);
-cudaError_t launch_tri_block_inverse(const double* T, int64_t ld, int64_t nmax,
-                                     const int64_t* rdev, int b, double* Tinv, cudaStream_t s);
 cudaError_t launch_phi(double* P, int64_t ld, int64_t nmax, const int64_t* rdev, cudaStream_t s);
 cudaError_t launch_sym_scatter(const double* ASS, int64_t lss, const double* ADS, int64_t lds,
                                const int32_t* colidx, const int32_t* pref, int64_t n, double* As,

@@ -61,7 +61,7 @@ def test_workspace_sizes(lib):
     # the transposed branch factors the m x m Gram matrix
     assert lib.cpinv_pinv_workspace_size(2048, 4096, ctypes.byref(o)) == s_pinv
     assert lib.cpinv_pinv_workspace_size(-1, 5, ctypes.byref(o)) == 0
-    bad = cpinv.make_opts("fp64", panel=65)
+    bad = cpinv.make_opts("fp64", panel=33)
     assert lib.cpinv_pinv_workspace_size(10, 5, ctypes.byref(bad)) == 0
 
 

@@ -51,7 +51,7 @@ SHAPES = [
 
 
 @pytest.mark.parametrize("mode", MODES)
-@pytest.mark.parametrize("panel", [16, 32, 64])
+@pytest.mark.parametrize("panel", [8, 16, 32])
 @pytest.mark.parametrize("shape", SHAPES)
 def test_shapes_and_panels(cp, mode, panel, shape):
     m, n, r = shape
