@@ -66,20 +66,27 @@ __global__ void tol_kernel(const double* A, int64_t lda, int64_t n, double rel_t
 
 // 1/sqrt(d) for d > 0 by Newton's iteration y <- y (3 - d y^2) / 2 from a
 // single-precision seed (about 22 correct bits); two FP64 steps bring it to
-// full double precision (each step doubles the correct bits).  Ranges beyond
-// float are handled by scaling d with an even power of two.
+// full double precision (each step doubles the correct bits).  The seed is
+// formed with integer operations on the bit patterns (FP64 <-> FP32
+// conversions are slow on this part): d = 2^(2k) f with f in [1, 4) taken
+// to float by truncating its significand, rsqrt(d) ~ 2^-k rsqrtf(f).  A
+// subnormal d is scaled by 2^108 first and the result by 2^54 at the end.
 __device__ __noinline__ double rsqrt_newton(double d) {
-  int e2 = 0;
-  double ds = d;
-  if (d > 1e36 || d < 1e-36) {
-    e2 = (ilogb(d) / 2) * 2;
-    ds = scalbn(d, -e2);
-  }
-  double y = (double)rsqrtf((float)ds);
-  const double h = 0.5 * ds;
+  const bool sub = (((uint64_t)__double_as_longlong(d) >> 52) & 0x7FF) == 0;
+  const double dd = sub ? d * 0x1p108 : d;  // subnormal: work on d 2^108
+  const uint64_t bits = (uint64_t)__double_as_longlong(dd);
+  const int E = (int)((bits >> 52) & 0x7FF) - 1023;
+  const int k = E >> 1;  // floor(E / 2)
+  const uint32_t fbits =
+      ((uint32_t)(127 + (E - 2 * k)) << 23) | (uint32_t)((bits >> 29) & 0x7FFFFF);
+  const uint32_t sb = __float_as_uint(rsqrtf(__uint_as_float(fbits)));
+  const int es = (int)((sb >> 23) & 0xFF) - 127 - k;  // exponent of the seed
+  double y = __longlong_as_double(
+      (long long)(((uint64_t)(es + 1023) << 52) | ((uint64_t)(sb & 0x7FFFFF) << 29)));
+  const double h = 0.5 * dd;
   y = y * fma(-h * y, y, 1.5);
   y = y * fma(-h * y, y, 1.5);
-  return e2 ? scalbn(y, -e2 / 2) : y;
+  return sub ? y * 0x1p54 : y;
 }
 
 // Named barriers 1 and 2 (0 is __syncthreads): producer / consumer hand-off
@@ -234,25 +241,26 @@ __device__ __forceinline__ void panel_solve_rows(double* A, int64_t lda, Dim nd,
   const int64_t n = eval_dim(nd, rdev);
   if (k0 >= n) return;
   const int bw = (int)((n - k0) < b ? (n - k0) : b);
+  // Ts[r][c] = T(r, c) / T(c, c): the substitution chain is then one shuffle
+  // and one fused multiply-add per column, x_c = acc_c / T(c, c) at the end
   __shared__ double Ts[32][33];
   __shared__ double dv[32];
+  if (threadIdx.x < 32) dv[threadIdx.x] = threadIdx.x < bw ? dinv[threadIdx.x] : 0.0;
+  __syncthreads();
   for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
     const int r = e >> 5, c = e & 31;
-    Ts[r][c] = (r < bw && c <= r) ? A[(k0 + r) * lda + (k0 + c)] : 0.0;
+    Ts[r][c] = (r < bw && c < r) ? A[(k0 + r) * lda + (k0 + c)] * dv[c] : 0.0;
   }
-  if (threadIdx.x < 32) dv[threadIdx.x] = threadIdx.x < bw ? dinv[threadIdx.x] : 0.0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t i = k0 + bw + (int64_t)blockIdx.x * kPanelRows + (threadIdx.x >> 5);
   if (i >= n) return;
   double acc = lane < bw ? A[i * lda + k0 + lane] : 0.0;
-  double x = 0.0;
   for (int c = 0; c < bw; ++c) {
-    const double xc = __shfl_sync(0xffffffffu, acc, c) * dv[c];
-    if (lane == c) x = xc;
-    if (lane > c) acc = fma(-xc, Ts[lane][c], acc);
+    const double ac = __shfl_sync(0xffffffffu, acc, c);
+    if (lane > c) acc = fma(-ac, Ts[lane][c], acc);
   }
-  if (lane < bw) A[i * lda + k0 + lane] = x;
+  if (lane < bw) A[i * lda + k0 + lane] = acc * dv[lane];
 }
 
 __global__ void __launch_bounds__(32 * kPanelRows) panel_solve_kernel(double* A, int64_t lda,

@@ -52,13 +52,15 @@ __global__ void __launch_bounds__(256) panel_solve_split_kernel(
   const int64_t n = eval_dim(nd, rdev);
   if (k0 >= n) return;
   const int bw = (int)((n - k0) < b ? (n - k0) : b);
+  // Ts[r][c] = T(r, c) / T(c, c) below the diagonal (see panel_solve_rows)
   __shared__ double Ts[32][33];
   __shared__ double dv[32];
+  if (threadIdx.x < 32) dv[threadIdx.x] = threadIdx.x < bw ? dinv[threadIdx.x] : 0.0;
+  __syncthreads();
   for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
     const int r = e >> 5, c = e & 31;
-    Ts[r][c] = (r < bw && c <= r) ? A[(k0 + r) * lda + (k0 + c)] : 0.0;
+    Ts[r][c] = (r < bw && c < r) ? A[(k0 + r) * lda + (k0 + c)] * dv[c] : 0.0;
   }
-  if (threadIdx.x < 32) dv[threadIdx.x] = threadIdx.x < bw ? dinv[threadIdx.x] : 0.0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t i = k0 + (int64_t)blockIdx.x * kPanelRows + (threadIdx.x >> 5);
@@ -67,13 +69,13 @@ __global__ void __launch_bounds__(256) panel_solve_split_kernel(
   if (i >= k0 + bw) {
     double acc = lane < bw ? A[i * lda + k0 + lane] : 0.0;
     for (int c = 0; c < bw; ++c) {
-      const double xc = __shfl_sync(0xffffffffu, acc, c) * dv[c];
-      if (lane == c) l = xc;
-      if (lane > c) acc = fma(-xc, Ts[lane][c], acc);
+      const double ac = __shfl_sync(0xffffffffu, acc, c);
+      if (lane > c) acc = fma(-ac, Ts[lane][c], acc);
     }
+    l = acc * dv[lane];
     if (lane < bw) A[i * lda + k0 + lane] = l;
-  } else {
-    l = Ts[i - k0][lane];  // diagonal block: already the factor (zero above)
+  } else if (lane < bw && lane <= i - k0) {
+    l = A[i * lda + k0 + lane];  // diagonal block: already the factor
   }
   if (lane < bw) {
     const uint64_t bits = (uint64_t)__double_as_longlong(l);

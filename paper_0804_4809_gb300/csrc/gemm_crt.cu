@@ -874,6 +874,78 @@ __global__ void __launch_bounds__(256, 2) reconstruct_kernel(ReconParams p, int 
   }
 }
 
+// The same reconstruction for small outputs (the panel updates of the
+// factorisation): four lanes share one output, each summing every fourth
+// modulus, and the partial sums meet by shuffles, so an output's latency
+// chain is a quarter of the moduli long and four times as many threads run.
+constexpr int kRecLanes = 4;
+
+__global__ void __launch_bounds__(256) reconstruct_split_kernel(ReconParams p, int n_mod) {
+  const crt::Consts& c = g_crt_consts[n_mod];
+  __shared__ CrtShared sh;
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&c.tab[0][0]);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&sh.tab[0][0]);
+    for (int e = threadIdx.x; e < n_mod * 32; e += blockDim.x) dst[e] = src[e];
+    for (int e = threadIdx.x; e < n_mod * crt::kLimbs; e += blockDim.x)
+      sh.Mj[e / crt::kLimbs][e % crt::kLimbs] = c.Mj[e / crt::kLimbs][e % crt::kLimbs];
+  }
+  if (threadIdx.x < crt::kLimbs) {
+    sh.P[threadIdx.x] = c.P[threadIdx.x];
+    sh.halfP[threadIdx.x] = c.halfP[threadIdx.x];
+  }
+  __syncthreads();
+  const int n = n_mod;
+  const int64_t M = eval_dim(p.M, p.rdev), N = eval_dim(p.N, p.rdev);
+  const int64_t total = M * N * kRecLanes;
+  const size_t plane = (size_t)p.Mpad * (size_t)p.Npad;
+  const int lane = threadIdx.x & 31, g = lane & (kRecLanes - 1);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // warp-uniform trip count: every lane reaches the shuffles
+  for (int64_t wb = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); wb < total;
+       wb += stride) {
+    const int64_t idx = wb + lane;
+    const int64_t o = idx / kRecLanes;
+    const int64_t i = o / (N > 0 ? N : 1), j = o - i * N;
+    const bool active = idx < total && !(p.lower && j > i);
+    uint64_t acc[crt::kLimbs];
+#pragma unroll
+    for (int l = 0; l < crt::kLimbs; ++l) acc[l] = 0;
+    if (active) {
+      const uint8_t* r = p.R + i * p.Npad + j;
+#pragma unroll
+      for (int t = 0; t < crt::kMaxMod / kRecLanes; ++t) {
+        const int m = g + kRecLanes * t;
+        if (m < n) {
+          const uint32_t tv = sh.tab[m][r[(size_t)m * plane]];
+#pragma unroll
+          for (int l = 0; l < crt::kLimbs; ++l) acc[l] += (uint64_t)tv * sh.Mj[m][l];
+        }
+      }
+    }
+#pragma unroll
+    for (int off = 1; off < kRecLanes; off <<= 1)
+#pragma unroll
+      for (int l = 0; l < crt::kLimbs; ++l)
+        acc[l] += __shfl_xor_sync(0xffffffffu, acc[l], off);
+    if (!active || g != 0) continue;
+    uint32_t S[crt::kLimbs];
+    uint64_t carry = 0;
+#pragma unroll
+    for (int l = 0; l < crt::kLimbs; ++l) {
+      const uint64_t v = acc[l] + carry;
+      S[l] = (uint32_t)v;
+      carry = v >> 32;
+    }
+    double v = crt_finish(S, sh.P, sh.halfP, c.shift, c.inv_ptop,
+                          p.EA[i] - 1022 - p.betaA + p.EB[j] - 1022 - p.betaB);
+    double* cp = p.C + i * p.ldc + j;
+    if (p.alpha != 1.0) v *= p.alpha;
+    if (p.beta != 0.0) v = fma(p.beta, *cp, v);
+    *cp = v;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -1064,9 +1136,14 @@ cudaError_t crt_reconstruct(const uint8_t* R, int64_t Mpad, int64_t Npad, Dim M,
   rp.ldc = ldc;
   rp.lower = lower;
   rp.pad = 0;
+  // small outputs (factorisation panels): latency-bound, four lanes per output
+  const bool small = M.max * N.max <= ((int64_t)1 << 19);
   return timer->run(KT_RECON, s, [&] {
-    reconstruct_kernel<<<grid1d(M.max * ((N.max + kRecW - 1) / kRecW), 256), 256, 0, s>>>(rp,
-                                                                                        n_mod);
+    if (small)
+      reconstruct_split_kernel<<<grid1d(M.max * N.max * kRecLanes, 256), 256, 0, s>>>(rp, n_mod);
+    else
+      reconstruct_kernel<<<grid1d(M.max * ((N.max + kRecW - 1) / kRecW), 256), 256, 0, s>>>(
+          rp, n_mod);
     return cudaGetLastError();
   });
 }
