@@ -548,6 +548,48 @@ def rbf_and_adjoint_bench(args, device, flush, steps: int = 3) -> dict:
     return out
 
 
+# the paper's own family (Sec. 3, Table 1): m = 2n, r = 7n/8, U[-1,1]
+PAPER_TABLE1_S = {32: 0.007, 64: 0.022, 128: 0.105, 256: 0.768, 512: 6.445, 1024: 54.137}
+
+
+def paper_bench(args) -> dict:
+    """Device time of one pseudoinverse per n of the paper's family, in the
+    exact and FP64 modes (graph replay), with the Penrose residuals of the
+    result, beside the paper's Table 1 times (another machine: context)."""
+    import numpy as np
+    import torch
+
+    from paper_0804_4809_gb300 import build, cpinv, inputs
+    build.build()
+    dev = torch.device("cuda", 0)
+    s = torch.cuda.current_stream(dev)
+    rows = []
+    for n in (32, 64, 128, 256, 512, 1024):
+        m, r = 2 * n, 7 * n // 8
+        Gh = inputs.paper_family(n, seed=n)
+        G = torch.from_numpy(Gh).to(dev)
+        row = {"n": n, "m": m, "r": r, "paper_s": PAPER_TABLE1_S[n]}
+        for md in ("exact", "fp64"):
+            plan = cpinv.PinvPlan(m, n, dev, mode=md)
+            out = torch.empty((n, m), dtype=torch.float64, device=dev)
+            rank = plan(G, out, sync_rank=True)
+            for _ in range(max(3, args.warmup)):
+                plan(G, out)
+            ms = time_steps(lambda: plan(G, out), max(5, args.steps), lambda: None, s)
+            Y = out.cpu().numpy()
+            GY, YG = Gh @ Y, Y @ Gh
+            pen = max(float(np.max(np.abs(GY @ Gh - Gh))), float(np.max(np.abs(Y @ GY - Y))),
+                      float(np.max(np.abs(GY - GY.T))), float(np.max(np.abs(YG - YG.T))))
+            t = sum(ms) / len(ms) / 1e3
+            row[md] = {"ms": round(t * 1e3, 4), "rank": rank, "penrose_max_abs": pen,
+                       "tflops": round(pinv_flops(m, n, r) / t / 1e12, 4),
+                       "speedup_vs_paper": round(PAPER_TABLE1_S[n] / t, 1)}
+        rows.append(row)
+    return {"workload": "paper family m = 2n, r = 7n/8, U[-1,1] factors, seed n",
+            "table": rows,
+            "note": "paper_s: Table 1, Matlab 6.5.1 on a PC of its time (context only)"}
+
+
 def batched_main(args):
     import torch
 
@@ -612,7 +654,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-baseline", action="store_true",
                     help="run only the selected mode (profiling runs)")
-    ap.add_argument("--workload", default="pinv", choices=["pinv", "gemm", "batched"],
+    ap.add_argument("--workload", default="pinv", choices=["pinv", "gemm", "batched", "paper"],
                     help="gemm: the exact-slice product alone, at the G+ = K G' shape; "
                          "batched: 512 uneven least-squares problems vs a per-matrix loop")
     ap.add_argument("--no-batched", action="store_true",
@@ -628,6 +670,9 @@ def main():
         return gemm_bench(args)
     if args.workload == "batched":
         return batched_main(args)
+    if args.workload == "paper":
+        print(json.dumps(paper_bench(args)), flush=True)
+        return None
     return ours(args)
 
 

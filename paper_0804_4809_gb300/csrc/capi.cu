@@ -489,9 +489,11 @@ int factor_exact(const Ctx& c, double* a, int64_t lda, int spd) {
   KernelTimer t;
   CK(t.run(KT_AUX, c.s, [&] { return launch_rowscale(a, lda, nd, c.rdev(), Ly.rows, E, c.s); }));
   CK(cudaMemsetAsync(RL, 0, Ly.rl_bytes, c.s));
+  const crt::Consts* consts = crt_consts_device();
+  if (!consts) return CPINV_ERR_CUDA;
   for (int64_t k0 = 0; k0 < nA; k0 += b) {
     if (k0 > 0) {
-      // A(k0:n, P) -= L(k0:n, 0:k0) L(P, 0:k0)'   exactly, from the residue planes
+      // residues of L(k0:n, 0:k0) L(P, 0:k0)', exactly, from the residue planes
       const Dim M = spd ? rdim(-k0, nA - k0) : hdim(nA - k0);
       const Dim N = spd ? rdim(-k0, b) : hdim(nA - k0 < b ? nA - k0 : b);
       GemmParams fl;
@@ -502,17 +504,35 @@ int factor_exact(const Ctx& c, double* a, int64_t lda, int spd) {
       fl.rdev = c.rdev();
       CK(crt_mma(RL, Ly.rows, (int)k0, RL, Ly.rows, (int)k0, Ly.kpad, k0, Ly.n_mod, M, N, c.rdev(),
                  0, R, Ly.rows, 256, &p.st->status, c.s, &t, &fl));
-      CK(crt_reconstruct(R, Ly.rows, 256, M, N, c.rdev(), E + k0, E + k0, kCholBits, kCholBits,
-                         -1.0, 1.0, a + k0 * lda + k0, lda, 1, Ly.n_mod, c.s, &t));
     }
-    CK(diag_timer(c, k0, b, spd).run(KT_DIAG, c.s, [&] {
-      return launch_diag_factor(a, lda, nd, k0, b, p.st, c.rdev(), spd ? nullptr : p.acc, p.dinv,
-                                spd, c.s);
-    }));
-    CK(t.run(KT_AUX, c.s, [&] {
-      return launch_panel_solve_split(a, lda, nd, c.rdev(), k0, b, p.dinv, E, Ly.n_mod,
-                                      kCholBits, RL, Ly.rows, Ly.kpad, c.s);
-    }));
+    // A(k0:n, P) -= that update, the diagonal block, the rows below, residues
+    PanelExactParams pp;
+    std::memset(&pp, 0, sizeof(pp));
+    pp.R = R;
+    pp.Mpad = Ly.rows;
+    pp.Npad = 256;
+    pp.has_update = k0 > 0;
+    pp.n_upd = Ly.n_mod;
+    pp.consts = consts;
+    pp.A = a;
+    pp.lda = lda;
+    pp.nd = nd;
+    pp.rdev = c.rdev();
+    pp.k0 = k0;
+    pp.b = b;
+    pp.spd = spd;
+    pp.st = p.st;
+    pp.accepted = spd ? nullptr : p.acc;
+    pp.dinv = p.dinv;
+    pp.E = E;
+    pp.n_mod = Ly.n_mod;
+    pp.beta = kCholBits;
+    pp.RL = (__nv_bfloat16*)RL;
+    pp.rl_rows = Ly.rows;
+    pp.rl_kpad = Ly.kpad;
+    pp.epoch = 1 + k0 / b + (spd ? ((int64_t)1 << 32) : 0);
+    CK(diag_timer(c, k0, b, spd).run(KT_DIAG, c.s,
+                                     [&] { return launch_chol_panel_exact(pp, c.s); }));
   }
   if (spd)
     CK(t.run(KT_AUX, c.s, [&] {

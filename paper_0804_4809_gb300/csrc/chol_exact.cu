@@ -11,6 +11,7 @@
 // one CRT reconstruction that subtracts the exactly summed update from A.
 #include <cmath>
 
+#include "chol_device.cuh"
 #include "common.cuh"
 #include "crt.h"
 #include "crt_device.cuh"
@@ -85,6 +86,184 @@ __global__ void __launch_bounds__(256) panel_solve_split_kernel(
   }
 }
 
+// One launch per panel of the exact-slice factorisation: the panel's update
+// (the CRT reconstruction of the exact residue product of the factor's
+// earlier columns), the factorisation of the diagonal block, the solve of
+// the rows below it and their residue split, fused.  CTA 0 takes the
+// diagonal block: it applies the update, factors the block on four warps,
+// writes the block's residues, and publishes the block (release store of
+// the panel's number into the call's state).  Every other CTA applies the
+// update to its eight rows (one warp per row, lane c = column c), waits for
+// the publication (bounded: on expiry it records ST_TIMEOUT and returns),
+// and solves its rows by forward substitution against the published block.
+// The grid is small (at most 1 + n/8 CTAs of 256 threads), so every CTA is
+// resident at once and CTA 0, launched first, is never starved.
+constexpr uint32_t kFlagSpinLimit = 1u << 22;
+
+// The waiters poll with relaxed loads (an acquire load per poll would
+// invalidate the SM's L1 each time, slowing every CTA on that SM, the
+// publishing one included) and order their later reads with one fence.
+__device__ __forceinline__ int64_t ld_relaxed(const int64_t* p) {
+  int64_t v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int64_t* p, int64_t v) {
+  asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// A(k0 + ir, k0 + jc) - X(ir, jc), X the exact update (residues in R), the
+// difference rounded once.
+__device__ __forceinline__ double apply_update(const PanelExactParams& p,
+                                               const crt::CrtShared& sh, int shift,
+                                               float inv_ptop, int64_t ir, int64_t jc,
+                                               double a_old) {
+  const size_t plane = (size_t)p.Mpad * (size_t)p.Npad;
+  const uint8_t* r = p.R + ir * p.Npad + jc;
+  // every residue load in flight at once: one memory latency per output
+  uint32_t rv[crt::kMaxMod];
+#pragma unroll
+  for (int m = 0; m < crt::kMaxMod; ++m) rv[m] = m < p.n_upd ? r[(size_t)m * plane] : 0u;
+  uint64_t acc[crt::kLimbs];
+#pragma unroll
+  for (int l = 0; l < crt::kLimbs; ++l) acc[l] = 0;
+#pragma unroll
+  for (int m = 0; m < crt::kMaxMod; ++m) {
+    if (m >= p.n_upd) break;
+    const uint32_t t = sh.tab[m][rv[m]];
+#pragma unroll
+    for (int l = 0; l < crt::kLimbs; ++l) acc[l] += (uint64_t)t * sh.Mj[m][l];
+  }
+  uint32_t S[crt::kLimbs];
+  uint64_t carry = 0;
+#pragma unroll
+  for (int l = 0; l < crt::kLimbs; ++l) {
+    const uint64_t v = acc[l] + carry;
+    S[l] = (uint32_t)v;
+    carry = v >> 32;
+  }
+  const int scale = p.E[p.k0 + ir] - 1022 - p.beta + p.E[p.k0 + jc] - 1022 - p.beta;
+  const double x = crt::crt_finish(S, sh.P, sh.halfP, shift, inv_ptop, scale);
+  return fma(1.0, a_old, -x);
+}
+
+__device__ __forceinline__ void split_store(const PanelExactParams& p, int64_t row, int64_t col,
+                                            double l) {
+  const uint64_t bits = (uint64_t)__double_as_longlong(l);
+  const uint64_t a = crt::integerize(bits, p.E[row], p.beta);
+  crt::store_residues(a, (bits >> 63) != 0, p.n_mod, p.RL + (size_t)row * p.rl_kpad + col,
+                      (size_t)p.rl_rows * (size_t)p.rl_kpad);
+}
+
+__global__ void __launch_bounds__(256, 4) chol_panel_exact_kernel(PanelExactParams p) {
+  const int64_t n = eval_dim(p.nd, p.rdev);
+  const int64_t k0 = p.k0;
+  if (k0 >= n) return;
+  const int bw = (int)((n - k0) < p.b ? (n - k0) : p.b);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row0 = k0 + bw + (int64_t)(blockIdx.x - 1) * kPanelRows;
+  if (blockIdx.x > 0 && row0 >= n) return;  // no row of this CTA exists
+  __shared__ crt::CrtShared sh;
+  __shared__ double Ts[32][33];
+  __shared__ double dv[32];
+  __shared__ int go;
+  int shift = 0;
+  float inv_ptop = 0.f;
+  if (p.has_update) {
+    const crt::Consts& c = p.consts[p.n_upd];
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&c.tab[0][0]);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&sh.tab[0][0]);
+    for (int e = threadIdx.x; e < p.n_upd * 32; e += blockDim.x) dst[e] = src[e];
+    for (int e = threadIdx.x; e < p.n_upd * crt::kLimbs; e += blockDim.x)
+      sh.Mj[e / crt::kLimbs][e % crt::kLimbs] = c.Mj[e / crt::kLimbs][e % crt::kLimbs];
+    if (threadIdx.x < crt::kLimbs) {
+      sh.P[threadIdx.x] = c.P[threadIdx.x];
+      sh.halfP[threadIdx.x] = c.halfP[threadIdx.x];
+    }
+    shift = c.shift;
+    inv_ptop = c.inv_ptop;
+    __syncthreads();
+  }
+  double* A = p.A;
+  const int64_t lda = p.lda;
+  if (blockIdx.x == 0) {
+    // the diagonal block: update (lower part), factor, residues, publish
+    if (p.has_update) {
+      // the lower triangle, entry o = i (i + 1) / 2 + j
+      const int tri = bw * (bw + 1) / 2;
+      for (int o = threadIdx.x; o < tri; o += blockDim.x) {
+        int i = (int)((sqrtf(8.0f * (float)o + 1.0f) - 1.0f) * 0.5f);
+        if ((i + 1) * (i + 2) / 2 <= o) ++i;
+        if (i * (i + 1) / 2 > o) --i;
+        const int j = o - i * (i + 1) / 2;
+        double* a = A + (k0 + i) * lda + (k0 + j);
+        *a = apply_update(p, sh, shift, inv_ptop, i, j, *a);
+      }
+      __syncthreads();
+    }
+    if (warp < chol::kDiagWarps)
+      chol::diag_chol_block(A, lda, p.nd, k0, p.b, p.st, p.rdev, p.accepted, p.dinv, p.spd);
+    // publish the block (factor and 1/T_cc written by warps 0-3) ...
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) st_release(&p.st->panel_flag, p.epoch);
+    // ... then its residues, while the other CTAs solve their rows
+    const int tri = bw * (bw + 1) / 2;
+    for (int o = threadIdx.x; o < tri; o += blockDim.x) {
+      int i = (int)((sqrtf(8.0f * (float)o + 1.0f) - 1.0f) * 0.5f);
+      if ((i + 1) * (i + 2) / 2 <= o) ++i;
+      if (i * (i + 1) / 2 > o) --i;
+      const int j = o - i * (i + 1) / 2;
+      split_store(p, k0 + i, k0 + j, A[(k0 + i) * lda + (k0 + j)]);
+    }
+    return;
+  }
+  // rows below the block: the update first, then wait for the block
+  const int64_t i = row0 + warp;
+  const bool row_ok = i < n;
+  double acc = 0.0;
+  if (row_ok && lane < bw) {
+    acc = A[i * lda + k0 + lane];
+    if (p.has_update) acc = apply_update(p, sh, shift, inv_ptop, i - k0, lane, acc);
+  }
+  if (threadIdx.x == 0) {
+    int ok = 0;
+    for (uint32_t it = 0; it < kFlagSpinLimit; ++it) {
+      if (ld_relaxed(&p.st->panel_flag) >= p.epoch) {
+        ok = 1;
+        break;
+      }
+      __nanosleep(it < 64 ? 32 : 256);
+    }
+    if (!ok) atomicOr(&p.st->status, ST_TIMEOUT);
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    go = ok;
+  }
+  __syncthreads();
+  if (!go) return;
+  // Ts[r][c] = T(r, c) / T(c, c) below the diagonal (see panel_solve_rows);
+  // L2 loads (the block was written by another CTA in this launch), all in
+  // one round trip, scaled in shared memory afterwards
+  if (threadIdx.x < 32) dv[threadIdx.x] = threadIdx.x < bw ? __ldcg(p.dinv + threadIdx.x) : 0.0;
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int r = e >> 5, c = e & 31;
+    Ts[r][c] = (r < bw && c < r) ? __ldcg(A + (k0 + r) * lda + (k0 + c)) : 0.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) Ts[e >> 5][e & 31] *= dv[e & 31];
+  __syncthreads();
+  if (!row_ok) return;
+  for (int c = 0; c < bw; ++c) {
+    const double ac = __shfl_sync(0xffffffffu, acc, c);
+    if (lane > c) acc = fma(-ac, Ts[lane][c], acc);
+  }
+  if (lane < bw) {
+    const double l = acc * dv[lane];
+    A[i * lda + k0 + lane] = l;
+    split_store(p, i, k0 + lane, l);
+  }
+}
+
 inline unsigned grid1d(int64_t total, int threads) {
   int64_t g = (total + threads - 1) / threads;
   if (g > 152 * 8) g = 152 * 8;
@@ -92,6 +271,14 @@ inline unsigned grid1d(int64_t total, int threads) {
 }
 
 }  // namespace
+
+cudaError_t launch_chol_panel_exact(const PanelExactParams& p, cudaStream_t s) {
+  if (p.b > 32 || p.b < 1 || (p.has_update && !p.consts)) return cudaErrorInvalidValue;
+  const int64_t below = p.nd.max - p.k0 - p.b;
+  const int64_t ctas = 1 + (below > 0 ? (below + kPanelRows - 1) / kPanelRows : 0);
+  chol_panel_exact_kernel<<<(unsigned)ctas, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_rowscale(const double* A, int64_t lda, Dim nd, const int64_t* rdev,
                             int64_t rows_max, int32_t* E, cudaStream_t s) {

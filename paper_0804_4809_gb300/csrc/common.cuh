@@ -46,7 +46,7 @@ struct DevState {
   double min_pos;   // that minimum
   int64_t dim_m;    // batched problems: this problem's m and n (else 0)
   int64_t dim_n;
-  int64_t pad;
+  int64_t panel_flag;  // last panel whose diagonal block is published (exact factorisation)
 };
 static_assert(sizeof(DevState) == 64, "DevState layout");
 // Dim::sel values that read DevState::dim_m and DevState::dim_n

@@ -29,17 +29,20 @@ __device__ __forceinline__ uint64_t integerize(uint64_t b, int Emax, int beta) {
   return (m + half) >> rs;
 }
 
-// Balanced residues (|v| <= 64) of the signed integer (neg ? -a : a) modulo
-// the first n_mod moduli, as BF16 at o[j * plane].
+// Balanced residues (|v| <= 64) of the signed integer (neg ? -a : a), a <
+// 2^63, modulo the first n_mod moduli, as BF16 at o[j * plane].  a is cut
+// into 21-bit chunks once; each residue is then one reduction of a value
+// below 2^29.
 __device__ __forceinline__ void store_residues(uint64_t a, bool neg, int n_mod, __nv_bfloat16* o,
                                                size_t plane) {
-  const uint32_t ahi = (uint32_t)(a >> 32), alo = (uint32_t)a;
+  const uint32_t a0 = (uint32_t)(a & 0x1FFFFF), a1 = (uint32_t)((a >> 21) & 0x1FFFFF),
+                 a2 = (uint32_t)(a >> 42);
 #pragma unroll
   for (int j = 0; j < kMaxMod; ++j) {
     if (j >= n_mod) break;
     const uint32_t p = (uint32_t)modulus(j);
-    const uint32_t two32 = (uint32_t)((((uint64_t)1) << 32) % p);
-    uint32_t r = ((ahi % p) * two32 + (alo % p)) % p;
+    const uint32_t c1 = (uint32_t)((1ull << 21) % p), c2 = (uint32_t)((1ull << 42) % p);
+    uint32_t r = (a2 * c2 + a1 * c1 + a0) % p;
     if (neg && r) r = p - r;
     const int v = (int)r > (int)(p / 2) ? (int)r - (int)p : (int)r;
     o[j * plane] = __float2bfloat16_rn((float)v);
@@ -64,6 +67,148 @@ __device__ __forceinline__ int residue21(uint32_t a0, uint32_t a1, uint32_t a2, 
   uint32_t r = (a2 * c2 + a1 * c1 + a0) % p;
   if (neg && r) r = p - r;
   return (int)r > (int)(p / 2) ? (int)r - (int)p : (int)r;
+}
+
+
+// ---------------------------------------------------------------------------
+// CRT reconstruction: exact integer (5 x 32-bit limbs) -> FP64
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double compose_double(bool neg, const uint32_t (&mag)[crt::kLimbs],
+                                                 int scale) {
+  // correctly rounded mag * 2^scale (mag < 2^160), via integer operations
+  int top = -1;
+#pragma unroll
+  for (int i = crt::kLimbs - 1; i >= 0; --i)
+    if (top < 0 && mag[i]) top = 32 * i + 31 - __clz(mag[i]);
+  if (top < 0) return neg ? -0.0 : 0.0;
+  // 64 bits starting at bit (top - 63), sticky below
+  const int lo_bit = top - 63;
+  uint64_t t = 0;
+  bool sticky = false;
+#pragma unroll
+  for (int i = 0; i < crt::kLimbs; ++i) {
+    const int base = 32 * i;  // bits base .. base+31 of mag
+    const uint64_t w = mag[i];
+    const int off = base - lo_bit;  // where bit `base` lands in t
+    if (off >= 64 || off <= -32) {
+      if (off <= -32 && w) sticky = true;
+      continue;
+    }
+    if (off >= 0) t |= w << off;
+    else {
+      t |= w >> (-off);
+      if (w & ((1ull << (-off)) - 1ull)) sticky = true;
+    }
+  }
+  uint64_t mant = t >> 11;
+  const uint64_t rem = t & 0x7FFull;
+  if (rem > 0x400ull || (rem == 0x400ull && (sticky || (mant & 1ull)))) ++mant;
+  int e = top;  // value = mant * 2^(top - 52)
+  if (mant >> 53) {
+    mant >>= 1;
+    ++e;
+  }
+  const int biased = e + scale + 1023;
+  if (biased <= 0 || biased >= 2047) {
+    // out of the normal range: let the FP64 unit handle under/overflow
+    const double d = ldexp((double)mant, e - 52 + scale);
+    return neg ? -d : d;
+  }
+  const uint64_t bits = ((uint64_t)neg << 63) | ((uint64_t)biased << 52) | (mant & 0xFFFFFFFFFFFFFull);
+  return __longlong_as_double((long long)bits);
+}
+
+// select S[k] for a uniform runtime k without local memory
+__device__ __forceinline__ uint32_t limb_at(const uint32_t (&S)[crt::kLimbs], int k) {
+  uint32_t w = 0;
+#pragma unroll
+  for (int l = 0; l < crt::kLimbs; ++l) w = (l == k) ? S[l] : w;
+  return w;
+}
+
+struct CrtShared {
+  uint8_t tab[crt::kMaxMod][128];
+  uint32_t Mj[crt::kMaxMod][crt::kLimbs];
+  uint32_t P[crt::kLimbs];
+  uint32_t halfP[crt::kLimbs];
+};
+
+// S (the CRT sum, < n P) -> centred X = S mod P in (-P/2, P/2] -> FP64,
+// correctly rounded, times 2^scale.
+__device__ __forceinline__ double crt_finish(const uint32_t (&S)[crt::kLimbs],
+                                             const uint32_t* P, const uint32_t* halfP, int shift,
+                                             float inv_ptop, int scale) {
+  // q = floor(S / P) in [0, n): estimate from the top bits, then correct
+  uint64_t stop = 0;
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    const int pos = shift + 32 * b;  // 32-bit chunk of S >> shift
+    const int li = pos >> 5, off = pos & 31;
+    uint32_t w = limb_at(S, li) >> off;
+    if (off) w |= limb_at(S, li + 1) << (32 - off);
+    stop |= (uint64_t)w << (32 * b);
+  }
+  int qe = (int)floorf((float)stop * inv_ptop);
+  qe = qe < 0 ? 0 : qe;
+  // X = S - qe * P  (signed, two's complement over the limbs)
+  int64_t borrow = 0;
+  uint32_t X[crt::kLimbs];
+#pragma unroll
+  for (int l = 0; l < crt::kLimbs; ++l) {
+    const int64_t v = (int64_t)S[l] - (int64_t)((uint64_t)qe * P[l]) + borrow;
+    X[l] = (uint32_t)v;
+    borrow = v >> 32;  // arithmetic
+  }
+  // fix-up: bring X into [0, P) (the estimate is off by at most one)
+#pragma unroll
+  for (int pass = 0; pass < 1; ++pass) {
+    if ((int32_t)X[crt::kLimbs - 1] < 0) {  // X < 0: X += P
+      uint64_t cc = 0;
+#pragma unroll
+      for (int l = 0; l < crt::kLimbs; ++l) {
+        const uint64_t v = (uint64_t)X[l] + P[l] + cc;
+        X[l] = (uint32_t)v;
+        cc = v >> 32;
+      }
+    } else {
+      bool ge = true, decided = false;  // X >= P ?
+#pragma unroll
+      for (int l = crt::kLimbs - 1; l >= 0; --l) {
+        if (!decided && X[l] != P[l]) {
+          ge = X[l] > P[l];
+          decided = true;
+        }
+      }
+      if (ge) {
+        int64_t bb = 0;
+#pragma unroll
+        for (int l = 0; l < crt::kLimbs; ++l) {
+          const int64_t v = (int64_t)X[l] - (int64_t)P[l] + bb;
+          X[l] = (uint32_t)v;
+          bb = v >> 32;
+        }
+      }
+    }
+  }
+  // centre: X > P/2 -> X - P (negative); magnitude and sign
+  bool gt = false, decided = false;
+#pragma unroll
+  for (int l = crt::kLimbs - 1; l >= 0; --l) {
+    if (!decided && X[l] != halfP[l]) {
+      gt = X[l] > halfP[l];
+      decided = true;
+    }
+  }
+  uint32_t mag[crt::kLimbs];
+  int64_t bb = 0;
+#pragma unroll
+  for (int l = 0; l < crt::kLimbs; ++l) {
+    const int64_t v = (int64_t)P[l] - (int64_t)X[l] + bb;
+    mag[l] = gt ? (uint32_t)v : X[l];
+    bb = v >> 32;
+  }
+  return compose_double(gt, mag, scale);
 }
 
 }  // namespace crt

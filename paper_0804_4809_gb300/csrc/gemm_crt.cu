@@ -652,146 +652,9 @@ struct ReconParams {
   int32_t pad;
 };
 
-__device__ __forceinline__ double compose_double(bool neg, const uint32_t (&mag)[crt::kLimbs],
-                                                 int scale) {
-  // correctly rounded mag * 2^scale (mag < 2^160), via integer operations
-  int top = -1;
-#pragma unroll
-  for (int i = crt::kLimbs - 1; i >= 0; --i)
-    if (top < 0 && mag[i]) top = 32 * i + 31 - __clz(mag[i]);
-  if (top < 0) return neg ? -0.0 : 0.0;
-  // 64 bits starting at bit (top - 63), sticky below
-  const int lo_bit = top - 63;
-  uint64_t t = 0;
-  bool sticky = false;
-#pragma unroll
-  for (int i = 0; i < crt::kLimbs; ++i) {
-    const int base = 32 * i;  // bits base .. base+31 of mag
-    const uint64_t w = mag[i];
-    const int off = base - lo_bit;  // where bit `base` lands in t
-    if (off >= 64 || off <= -32) {
-      if (off <= -32 && w) sticky = true;
-      continue;
-    }
-    if (off >= 0) t |= w << off;
-    else {
-      t |= w >> (-off);
-      if (w & ((1ull << (-off)) - 1ull)) sticky = true;
-    }
-  }
-  uint64_t mant = t >> 11;
-  const uint64_t rem = t & 0x7FFull;
-  if (rem > 0x400ull || (rem == 0x400ull && (sticky || (mant & 1ull)))) ++mant;
-  int e = top;  // value = mant * 2^(top - 52)
-  if (mant >> 53) {
-    mant >>= 1;
-    ++e;
-  }
-  const int biased = e + scale + 1023;
-  if (biased <= 0 || biased >= 2047) {
-    // out of the normal range: let the FP64 unit handle under/overflow
-    const double d = ldexp((double)mant, e - 52 + scale);
-    return neg ? -d : d;
-  }
-  const uint64_t bits = ((uint64_t)neg << 63) | ((uint64_t)biased << 52) | (mant & 0xFFFFFFFFFFFFFull);
-  return __longlong_as_double((long long)bits);
-}
-
 // CRT constants of every moduli count, in device memory (uploaded once per
 // device): blocks read them with coalesced loads.
 __device__ crt::Consts g_crt_consts[crt::kMaxMod + 1];
-
-// select S[k] for a uniform runtime k without local memory
-__device__ __forceinline__ uint32_t limb_at(const uint32_t (&S)[crt::kLimbs], int k) {
-  uint32_t w = 0;
-#pragma unroll
-  for (int l = 0; l < crt::kLimbs; ++l) w = (l == k) ? S[l] : w;
-  return w;
-}
-
-struct CrtShared {
-  uint8_t tab[crt::kMaxMod][128];
-  uint32_t Mj[crt::kMaxMod][crt::kLimbs];
-  uint32_t P[crt::kLimbs];
-  uint32_t halfP[crt::kLimbs];
-};
-
-// S (the CRT sum, < n P) -> centred X = S mod P in (-P/2, P/2] -> FP64,
-// correctly rounded, times 2^scale.
-__device__ __forceinline__ double crt_finish(const uint32_t (&S)[crt::kLimbs],
-                                             const uint32_t* P, const uint32_t* halfP, int shift,
-                                             float inv_ptop, int scale) {
-  // q = floor(S / P) in [0, n): estimate from the top bits, then correct
-  uint64_t stop = 0;
-#pragma unroll
-  for (int b = 0; b < 2; ++b) {
-    const int pos = shift + 32 * b;  // 32-bit chunk of S >> shift
-    const int li = pos >> 5, off = pos & 31;
-    uint32_t w = limb_at(S, li) >> off;
-    if (off) w |= limb_at(S, li + 1) << (32 - off);
-    stop |= (uint64_t)w << (32 * b);
-  }
-  int qe = (int)floorf((float)stop * inv_ptop);
-  qe = qe < 0 ? 0 : qe;
-  // X = S - qe * P  (signed, two's complement over the limbs)
-  int64_t borrow = 0;
-  uint32_t X[crt::kLimbs];
-#pragma unroll
-  for (int l = 0; l < crt::kLimbs; ++l) {
-    const int64_t v = (int64_t)S[l] - (int64_t)((uint64_t)qe * P[l]) + borrow;
-    X[l] = (uint32_t)v;
-    borrow = v >> 32;  // arithmetic
-  }
-  // fix-up: bring X into [0, P) (the estimate is off by at most one)
-#pragma unroll
-  for (int pass = 0; pass < 1; ++pass) {
-    if ((int32_t)X[crt::kLimbs - 1] < 0) {  // X < 0: X += P
-      uint64_t cc = 0;
-#pragma unroll
-      for (int l = 0; l < crt::kLimbs; ++l) {
-        const uint64_t v = (uint64_t)X[l] + P[l] + cc;
-        X[l] = (uint32_t)v;
-        cc = v >> 32;
-      }
-    } else {
-      bool ge = true, decided = false;  // X >= P ?
-#pragma unroll
-      for (int l = crt::kLimbs - 1; l >= 0; --l) {
-        if (!decided && X[l] != P[l]) {
-          ge = X[l] > P[l];
-          decided = true;
-        }
-      }
-      if (ge) {
-        int64_t bb = 0;
-#pragma unroll
-        for (int l = 0; l < crt::kLimbs; ++l) {
-          const int64_t v = (int64_t)X[l] - (int64_t)P[l] + bb;
-          X[l] = (uint32_t)v;
-          bb = v >> 32;
-        }
-      }
-    }
-  }
-  // centre: X > P/2 -> X - P (negative); magnitude and sign
-  bool gt = false, decided = false;
-#pragma unroll
-  for (int l = crt::kLimbs - 1; l >= 0; --l) {
-    if (!decided && X[l] != halfP[l]) {
-      gt = X[l] > halfP[l];
-      decided = true;
-    }
-  }
-  uint32_t mag[crt::kLimbs];
-  int64_t bb = 0;
-#pragma unroll
-  for (int l = 0; l < crt::kLimbs; ++l) {
-    const int64_t v = (int64_t)P[l] - (int64_t)X[l] + bb;
-    mag[l] = gt ? (uint32_t)v : X[l];
-    bb = v >> 32;
-  }
-  return compose_double(gt, mag, scale);
-}
 
 // Two adjacent columns per thread: the residue bytes of a modulus come in one
 // 16-bit load and each multiplier P/p_j is read once for both sums.
@@ -799,7 +662,7 @@ constexpr int kRecW = 2;
 
 __global__ void __launch_bounds__(256, 2) reconstruct_kernel(ReconParams p, int n_mod) {
   const crt::Consts& c = g_crt_consts[n_mod];
-  __shared__ CrtShared sh;
+  __shared__ crt::CrtShared sh;
   {
     const uint32_t* src = reinterpret_cast<const uint32_t*>(&c.tab[0][0]);
     uint32_t* dst = reinterpret_cast<uint32_t*>(&sh.tab[0][0]);
@@ -865,7 +728,7 @@ __global__ void __launch_bounds__(256, 2) reconstruct_kernel(ReconParams p, int 
         S[l] = (uint32_t)v;
         carry = v >> 32;
       }
-      double v = crt_finish(S, sh.P, sh.halfP, shift, inv_ptop, sa + p.EB[j] - 1022 - p.betaB);
+      double v = crt::crt_finish(S, sh.P, sh.halfP, shift, inv_ptop, sa + p.EB[j] - 1022 - p.betaB);
       double* cp = p.C + i * p.ldc + j;
       if (p.alpha != 1.0) v *= p.alpha;
       if (p.beta != 0.0) v = fma(p.beta, *cp, v);
@@ -882,7 +745,7 @@ constexpr int kRecLanes = 4;
 
 __global__ void __launch_bounds__(256) reconstruct_split_kernel(ReconParams p, int n_mod) {
   const crt::Consts& c = g_crt_consts[n_mod];
-  __shared__ CrtShared sh;
+  __shared__ crt::CrtShared sh;
   {
     const uint32_t* src = reinterpret_cast<const uint32_t*>(&c.tab[0][0]);
     uint32_t* dst = reinterpret_cast<uint32_t*>(&sh.tab[0][0]);
@@ -937,7 +800,7 @@ __global__ void __launch_bounds__(256) reconstruct_split_kernel(ReconParams p, i
       S[l] = (uint32_t)v;
       carry = v >> 32;
     }
-    double v = crt_finish(S, sh.P, sh.halfP, c.shift, c.inv_ptop,
+    double v = crt::crt_finish(S, sh.P, sh.halfP, c.shift, c.inv_ptop,
                           p.EA[i] - 1022 - p.betaA + p.EB[j] - 1022 - p.betaB);
     double* cp = p.C + i * p.ldc + j;
     if (p.alpha != 1.0) v *= p.alpha;
@@ -1097,28 +960,31 @@ cudaError_t crt_mma(const void* SA, int64_t a_rows, int a_row0, const void* SB, 
   });
 }
 
+// The CRT tables of every moduli count, uploaded once per device (outside
+// any stream capture: the first call of an argument set always runs
+// directly); returns their device address, indexed by the moduli count.
+const crt::Consts* crt_consts_device() {
+  static std::mutex mu;
+  static std::vector<std::pair<int, const crt::Consts*>> done;
+  std::lock_guard<std::mutex> lock(mu);
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  for (auto& d : done)
+    if (d.first == dev) return d.second;
+  static crt::Consts host[crt::kMaxMod + 1];
+  for (int k = 1; k <= crt::kMaxMod; ++k) crt::make_consts(k, &host[k]);
+  if (cudaMemcpyToSymbol(g_crt_consts, host, sizeof(host)) != cudaSuccess) return nullptr;
+  void* ptr = nullptr;
+  if (cudaGetSymbolAddress(&ptr, g_crt_consts) != cudaSuccess || !ptr) return nullptr;
+  done.push_back({dev, (const crt::Consts*)ptr});
+  return (const crt::Consts*)ptr;
+}
+
 cudaError_t crt_reconstruct(const uint8_t* R, int64_t Mpad, int64_t Npad, Dim M, Dim N,
                             const int64_t* rdev, const int32_t* EA, const int32_t* EB, int betaA,
                             int betaB, double alpha, double beta, double* C, int64_t ldc,
                             int lower, int n_mod, cudaStream_t s, KernelTimer* timer) {
-  {
-    // upload the tables of every moduli count once per device (outside any
-    // stream capture: the first call of an argument set always runs directly)
-    static std::mutex mu;
-    static std::vector<int> done;
-    std::lock_guard<std::mutex> lock(mu);
-    int dev = -1;
-    cudaGetDevice(&dev);
-    bool have = false;
-    for (int d : done) have |= (d == dev);
-    if (!have) {
-      static crt::Consts host[crt::kMaxMod + 1];
-      for (int k = 1; k <= crt::kMaxMod; ++k) crt::make_consts(k, &host[k]);
-      cudaError_t e = cudaMemcpyToSymbol(g_crt_consts, host, sizeof(host));
-      if (e != cudaSuccess) return e;
-      done.push_back(dev);
-    }
-  }
+  if (!crt_consts_device()) return cudaErrorInitializationError;
   ReconParams rp;
   rp.R = R;
   rp.Mpad = Mpad;

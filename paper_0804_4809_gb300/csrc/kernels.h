@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -69,6 +70,8 @@ int crt_moduli_for(int64_t Kmax, int betaA, int betaB);
 size_t split_workspace_bytes(int64_t Mmax, int64_t Nmax, int64_t Kmax, bool same_operand);
 cudaError_t launch_split_gemm(const CrtGemm& g, cudaStream_t s, KernelTimer* timer);
 int crt_block_k();  // K granularity of the residue planes (64)
+namespace crt { struct Consts; }
+const crt::Consts* crt_consts_device();  // CRT tables [moduli count], device address
 int crt_block_m();  // rows of an output tile (128)
 // The three stages of an exact product, for callers that keep residues:
 //   row exponents (atomicMax into a zeroed array), residue planes
@@ -96,6 +99,30 @@ cudaError_t launch_panel_solve_split(double* A, int64_t lda, Dim nd, const int64
                                      int64_t k0, int b, const double* dinv, const int32_t* E,
                                      int n_mod, int beta, void* RL, int64_t rl_rows,
                                      int64_t rl_kpad, cudaStream_t s);
+
+// One fused launch per panel of the exact-slice factorisation (update
+// reconstruction, diagonal block, rows below, residue split).
+struct PanelExactParams {
+  const uint8_t* R;   // update residues R[j][row][col] (rows from k0)
+  int64_t Mpad, Npad;
+  int32_t has_update, n_upd;  // moduli count of the update
+  const crt::Consts* consts;  // crt_consts_device()
+  double* A;
+  int64_t lda;
+  Dim nd;
+  const int64_t* rdev;
+  int64_t k0;
+  int32_t b, spd;
+  DevState* st;
+  uint8_t* accepted;
+  double* dinv;
+  const int32_t* E;   // row scales (biased exponent bounds)
+  int32_t n_mod, beta;  // residues of the factor: moduli count and bits
+  __nv_bfloat16* RL;
+  int64_t rl_rows, rl_kpad;
+  int64_t epoch;      // published into st->panel_flag when the block is done
+};
+cudaError_t launch_chol_panel_exact(const PanelExactParams& p, cudaStream_t s);
 
 // gemm_fp64.cu
 cudaError_t launch_dgemm(const GemmParams& p, bool transA, bool transB, cudaStream_t s);
