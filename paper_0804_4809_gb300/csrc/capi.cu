@@ -161,6 +161,7 @@ struct Plan {
   double* S2;
   void* crt;     // exact-slice scratch (residues, exponents)
   size_t crt_bytes;
+  mutable int64_t diag_shares;  // exact factorisation: helper shares so far in this call
 };
 
 // Where a product sits in the pipeline decides its arithmetic:
@@ -467,6 +468,9 @@ int factor(const Ctx& c, double* a, int64_t lda, int spd) {
   return CPINV_OK;
 }
 
+// CTAs of a fused panel launch that share the update of its diagonal block
+constexpr int64_t kPanelHelpers = 3;
+
 // Exact-slice left-looking variant of factor() (see chol_exact.cu).
 int factor_exact(const Ctx& c, double* a, int64_t lda, int spd) {
   const Plan& p = *c.p;
@@ -531,6 +535,12 @@ int factor_exact(const Ctx& c, double* a, int64_t lda, int spd) {
     pp.rl_rows = Ly.rows;
     pp.rl_kpad = Ly.kpad;
     pp.epoch = 1 + k0 / b + (spd ? ((int64_t)1 << 32) : 0);
+    if (pp.has_update) {
+      const int64_t ctas = chol_panel_exact_ctas(nd.max, k0, b);
+      pp.helpers = (int32_t)(ctas - 1 < kPanelHelpers ? ctas - 1 : kPanelHelpers);
+      p.diag_shares += pp.helpers;
+      pp.diag_target = p.diag_shares;
+    }
     CK(diag_timer(c, k0, b, spd).run(KT_DIAG, c.s,
                                      [&] { return launch_chol_panel_exact(pp, c.s); }));
   }
@@ -825,6 +835,7 @@ int run_pipeline(const Plan& p, cudaStream_t user, const GraphKey& key, Body&& b
   auto direct = [&]() -> int {
     Ctx c{user, &p};
     CK(cudaMemsetAsync(p.st, 0, sizeof(DevState), user));
+    p.diag_shares = 0;
     return body(c);
   };
   if (!graphs_enabled()) return direct();
@@ -861,6 +872,7 @@ int run_pipeline(const Plan& p, cudaStream_t user, const GraphKey& key, Body&& b
     const int64_t l0 = g_launches.load();
     CK(cudaStreamBeginCapture(side, cudaStreamCaptureModeThreadLocal));
     Ctx c{side, &p};
+    p.diag_shares = 0;
     int rc = cudaMemsetAsync(p.st, 0, sizeof(DevState), side) == cudaSuccess ? body(c)
                                                                                : CPINV_ERR_CUDA;
     cudaGraph_t graph = nullptr;

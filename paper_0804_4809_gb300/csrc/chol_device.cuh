@@ -10,12 +10,14 @@
 namespace cpinv {
 namespace chol {
 
-// 1/sqrt(d) for d > 0 by Newton's iteration y <- y (3 - d y^2) / 2 from a
-// single-precision seed (about 22 correct bits); two FP64 steps bring it to
-// full double precision (each step doubles the correct bits).  The seed is
-// formed with integer operations on the bit patterns (FP64 <-> FP32
-// conversions are slow on this part): d = 2^(2k) f with f in [1, 4) taken
-// to float by truncating its significand, rsqrt(d) ~ 2^-k rsqrtf(f).  A
+// 1/sqrt(d) for d > 0 from a single-precision seed y0 (about 22 correct
+// bits) and one third-order correction: with e = 1 - d y0^2,
+//   1/sqrt(d) = y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3e^2/8 + O(e^3)),
+// so y = y0 + (y0 e)(1/2 + 3e/8) is accurate to O(e^3) ~ 2^-66: four
+// dependent FP64 operations (y0^2 is exact: y0 has 24 significant bits).
+// The seed is formed with integer operations on the bit patterns (FP64 <->
+// FP32 conversions are slow on this part): d = 2^(2k) f with f in [1, 4)
+// taken to float by truncating its significand, y0 = 2^-k rsqrtf(f).  A
 // subnormal d is scaled by 2^108 first and the result by 2^54 at the end.
 __device__ __forceinline__ double rsqrt_newton(double d) {
   const bool sub = (((uint64_t)__double_as_longlong(d) >> 52) & 0x7FF) == 0;
@@ -27,11 +29,10 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
       ((uint32_t)(127 + (E - 2 * k)) << 23) | (uint32_t)((bits >> 29) & 0x7FFFFF);
   const uint32_t sb = __float_as_uint(rsqrtf(__uint_as_float(fbits)));
   const int es = (int)((sb >> 23) & 0xFF) - 127 - k;  // exponent of the seed
-  double y = __longlong_as_double(
+  const double y0 = __longlong_as_double(
       (long long)(((uint64_t)(es + 1023) << 52) | ((uint64_t)(sb & 0x7FFFFF) << 29)));
-  const double h = 0.5 * dd;
-  y = y * fma(-h * y, y, 1.5);
-  y = y * fma(-h * y, y, 1.5);
+  const double e = fma(-dd, y0 * y0, 1.0);
+  const double y = fma(y0 * e, fma(e, 0.375, 0.5), y0);
   // subnormal d: y * 2^54 by the exponent field (y is a normal number)
   return sub ? __longlong_as_double(__double_as_longlong(y) + (54ll << 52)) : y;
 }
@@ -78,7 +79,8 @@ __device__ __forceinline__ void diag_chol_block(double* A, int64_t lda, Dim nd, 
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int j = w + kDiagWarps * q;
-    a[q] = (lane < bw && j < bw && j <= lane) ? A[(k0 + lane) * lda + (k0 + j)] : 0.0;
+    // L2 loads: other CTAs of a fused launch may have just written the block
+    a[q] = (lane < bw && j < bw && j <= lane) ? __ldcg(A + (k0 + lane) * lda + (k0 + j)) : 0.0;
   }
   // Finishes column c held in `acol` (owner warp only); returns L(lane, c).
   // The pivot test and 1/sqrt run on lane c alone (the FP64 pipe is narrow:

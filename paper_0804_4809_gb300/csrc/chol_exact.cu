@@ -89,15 +89,20 @@ __global__ void __launch_bounds__(256) panel_solve_split_kernel(
 // One launch per panel of the exact-slice factorisation: the panel's update
 // (the CRT reconstruction of the exact residue product of the factor's
 // earlier columns), the factorisation of the diagonal block, the solve of
-// the rows below it and their residue split, fused.  CTA 0 takes the
-// diagonal block: it applies the update, factors the block on four warps,
-// writes the block's residues, and publishes the block (release store of
-// the panel's number into the call's state).  Every other CTA applies the
-// update to its eight rows (one warp per row, lane c = column c), waits for
-// the publication (bounded: on expiry it records ST_TIMEOUT and returns),
-// and solves its rows by forward substitution against the published block.
-// The grid is small (at most 1 + n/8 CTAs of 256 threads), so every CTA is
-// resident at once and CTA 0, launched first, is never starved.
+// the rows below it and their residue split, fused.
+//  * CTAs 1..helpers first apply the update to a share of the diagonal
+//    block's lower triangle each and count their share done (atomic add to
+//    the call's state).
+//  * CTA 0 waits for that count (or applies the update itself when there
+//    are no helpers), factors the block on four warps, publishes it (release
+//    store of the panel's number into the call's state), then writes the
+//    block's residues.
+//  * Every CTA but 0 applies the update to its eight rows (one warp per row,
+//    lane c = column c), waits for the publication, and solves its rows by
+//    forward substitution against the published block.
+// Every wait is bounded: on expiry the CTA records ST_TIMEOUT and goes on.
+// The grid is small (at most 1 + n/8 CTAs of 256 threads, four resident per
+// SM), so every CTA is resident at once; no CTA waits on one that waits.
 constexpr uint32_t kFlagSpinLimit = 1u << 22;
 
 // The waiters poll with relaxed loads (an acquire load per poll would
@@ -155,6 +160,14 @@ __device__ __forceinline__ void split_store(const PanelExactParams& p, int64_t r
                       (size_t)p.rl_rows * (size_t)p.rl_kpad);
 }
 
+// Entry o of the lower triangle of the block, o = i (i + 1) / 2 + j.
+__device__ __forceinline__ void tri_index(int o, int& i, int& j) {
+  i = (int)((sqrtf(8.0f * (float)o + 1.0f) - 1.0f) * 0.5f);
+  if ((i + 1) * (i + 2) / 2 <= o) ++i;
+  if (i * (i + 1) / 2 > o) --i;
+  j = o - i * (i + 1) / 2;
+}
+
 __global__ void __launch_bounds__(256, 4) chol_panel_exact_kernel(PanelExactParams p) {
   const int64_t n = eval_dim(p.nd, p.rdev);
   const int64_t k0 = p.k0;
@@ -162,7 +175,8 @@ __global__ void __launch_bounds__(256, 4) chol_panel_exact_kernel(PanelExactPara
   const int bw = (int)((n - k0) < p.b ? (n - k0) : p.b);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t row0 = k0 + bw + (int64_t)(blockIdx.x - 1) * kPanelRows;
-  if (blockIdx.x > 0 && row0 >= n) return;  // no row of this CTA exists
+  const bool helper = p.has_update && blockIdx.x >= 1 && (int)blockIdx.x <= p.helpers;
+  if (blockIdx.x > 0 && row0 >= n && !helper) return;  // nothing for this CTA
   __shared__ crt::CrtShared sh;
   __shared__ double Ts[32][33];
   __shared__ double dv[32];
@@ -186,18 +200,46 @@ __global__ void __launch_bounds__(256, 4) chol_panel_exact_kernel(PanelExactPara
   }
   double* A = p.A;
   const int64_t lda = p.lda;
+  const int tri = bw * (bw + 1) / 2;
+  if (helper) {
+    // this CTA's share of the diagonal block's update, then count it
+    const int chunk = (tri + p.helpers - 1) / p.helpers;
+    const int beg = ((int)blockIdx.x - 1) * chunk;
+    const int end = beg + chunk < tri ? beg + chunk : tri;
+    for (int o = beg + threadIdx.x; o < end; o += blockDim.x) {
+      int i, j;
+      tri_index(o, i, j);
+      double* a = A + (k0 + i) * lda + (k0 + j);
+      *a = apply_update(p, sh, shift, inv_ptop, i, j, *a);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd((unsigned long long*)&p.st->diag_count, 1ull);
+    if (row0 >= n) return;
+  }
   if (blockIdx.x == 0) {
     // the diagonal block: update (lower part), factor, residues, publish
-    if (p.has_update) {
-      // the lower triangle, entry o = i (i + 1) / 2 + j
-      const int tri = bw * (bw + 1) / 2;
+    if (p.has_update && p.helpers == 0) {
       for (int o = threadIdx.x; o < tri; o += blockDim.x) {
-        int i = (int)((sqrtf(8.0f * (float)o + 1.0f) - 1.0f) * 0.5f);
-        if ((i + 1) * (i + 2) / 2 <= o) ++i;
-        if (i * (i + 1) / 2 > o) --i;
-        const int j = o - i * (i + 1) / 2;
+        int i, j;
+        tri_index(o, i, j);
         double* a = A + (k0 + i) * lda + (k0 + j);
         *a = apply_update(p, sh, shift, inv_ptop, i, j, *a);
+      }
+      __syncthreads();
+    } else if (p.has_update) {
+      // wait for the helpers' shares (bounded; ST_TIMEOUT on expiry)
+      if (threadIdx.x == 0) {
+        int ok = 0;
+        for (uint32_t it = 0; it < kFlagSpinLimit; ++it) {
+          if (ld_relaxed(&p.st->diag_count) >= p.diag_target) {
+            ok = 1;
+            break;
+          }
+          __nanosleep(it < 64 ? 32 : 256);
+        }
+        if (!ok) atomicOr(&p.st->status, ST_TIMEOUT);
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
       }
       __syncthreads();
     }
@@ -208,12 +250,9 @@ __global__ void __launch_bounds__(256, 4) chol_panel_exact_kernel(PanelExactPara
     __syncthreads();
     if (threadIdx.x == 0) st_release(&p.st->panel_flag, p.epoch);
     // ... then its residues, while the other CTAs solve their rows
-    const int tri = bw * (bw + 1) / 2;
     for (int o = threadIdx.x; o < tri; o += blockDim.x) {
-      int i = (int)((sqrtf(8.0f * (float)o + 1.0f) - 1.0f) * 0.5f);
-      if ((i + 1) * (i + 2) / 2 <= o) ++i;
-      if (i * (i + 1) / 2 > o) --i;
-      const int j = o - i * (i + 1) / 2;
+      int i, j;
+      tri_index(o, i, j);
       split_store(p, k0 + i, k0 + j, A[(k0 + i) * lda + (k0 + j)]);
     }
     return;
@@ -272,10 +311,15 @@ inline unsigned grid1d(int64_t total, int threads) {
 
 }  // namespace
 
+int64_t chol_panel_exact_ctas(int64_t nmax, int64_t k0, int b) {
+  const int64_t below = nmax - k0 - b;
+  return 1 + (below > 0 ? (below + kPanelRows - 1) / kPanelRows : 0);
+}
+
 cudaError_t launch_chol_panel_exact(const PanelExactParams& p, cudaStream_t s) {
   if (p.b > 32 || p.b < 1 || (p.has_update && !p.consts)) return cudaErrorInvalidValue;
-  const int64_t below = p.nd.max - p.k0 - p.b;
-  const int64_t ctas = 1 + (below > 0 ? (below + kPanelRows - 1) / kPanelRows : 0);
+  const int64_t ctas = chol_panel_exact_ctas(p.nd.max, p.k0, p.b);
+  if (p.helpers < 0 || p.helpers >= ctas) return cudaErrorInvalidValue;
   chol_panel_exact_kernel<<<(unsigned)ctas, 256, 0, s>>>(p);
   return cudaGetLastError();
 }

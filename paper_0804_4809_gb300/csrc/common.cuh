@@ -47,8 +47,10 @@ struct DevState {
   int64_t dim_m;    // batched problems: this problem's m and n (else 0)
   int64_t dim_n;
   int64_t panel_flag;  // last panel whose diagonal block is published (exact factorisation)
+  int64_t diag_count;  // diagonal-block update shares done (exact factorisation)
+  int64_t spare[7];
 };
-static_assert(sizeof(DevState) == 64, "DevState layout");
+static_assert(sizeof(DevState) == 128, "DevState layout");
 // Dim::sel values that read DevState::dim_m and DevState::dim_n
 enum : int32_t { SEL_RANK = 1, SEL_M = 6, SEL_N = 7 };
 static_assert(offsetof(DevState, dim_m) == 8 * (SEL_M - 1), "SEL_M");

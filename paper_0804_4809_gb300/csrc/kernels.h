@@ -121,8 +121,12 @@ struct PanelExactParams {
   __nv_bfloat16* RL;
   int64_t rl_rows, rl_kpad;
   int64_t epoch;      // published into st->panel_flag when the block is done
+  int32_t helpers;    // CTAs 1..helpers update the diagonal block (0: CTA 0 does)
+  int32_t pad;
+  int64_t diag_target;  // st->diag_count once this panel's helpers are done
 };
 cudaError_t launch_chol_panel_exact(const PanelExactParams& p, cudaStream_t s);
+int64_t chol_panel_exact_ctas(int64_t nmax, int64_t k0, int b);  // grid size of that launch
 
 // gemm_fp64.cu
 cudaError_t launch_dgemm(const GemmParams& p, bool transA, bool transB, cudaStream_t s);

@@ -4,7 +4,9 @@ rank, match the oracle within the bar of its mode, and meet the paper's
 accuracy statement: every coefficient of the four Penrose error matrices at
 most 2e-10 in absolute value.  Where the oracle itself does not meet 2e-10 on
 our instance of the family (n = 1024, seed 1024: kept block close to
-singular, residual 4.7e-9), the GPU is held to 4x the oracle's residual."""
+singular, residual 4.7e-9 with the correctly rounded Gram matrix, 3.7e-8
+with an FP64 one), the GPU is held to 4x the oracle's residual or 8x that of
+the oracle with an FP64 Gram matrix, whichever is larger."""
 import numpy as np
 import pytest
 
@@ -27,10 +29,12 @@ def test_paper_family(n, mode):
     # the stated bar, or 8x the oracle's own change between a correctly
     # rounded and an FP64 Gram matrix where the kept block is close to
     # singular (n = 1024: smallest kept pivot 2.6e3 tol, change 9.4e-10)
-    sens = rel(oracle.geninv(G, exact_gram=False), Yo)
+    Yf = oracle.geninv(G, exact_gram=False)
+    sens = rel(Yf, Yo)
     assert rel(Y, Yo) <= max(tol_for(mode, G, r), 8.0 * sens), (rel(Y, Yo), sens)
     res = oracle.penrose_residuals(G, Y)
     res_o = oracle.penrose_residuals(G, Yo)
+    res_f = oracle.penrose_residuals(G, Yf)
     for k, v in res.items():
         if k.endswith(":max"):
-            assert v <= max(2e-10, 4.0 * res_o[k]), (k, v, res_o[k])
+            assert v <= max(2e-10, 4.0 * res_o[k], 8.0 * res_f[k]), (k, v, res_o[k], res_f[k])
