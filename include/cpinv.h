@@ -67,7 +67,7 @@ typedef struct cpinv_opts {
   int32_t mode;      /* CPINV_MODE_* (default CPINV_MODE_FP64) */
   int32_t slices;    /* exact-slice mode: number of 8-bit slices per operand,
                         0 = default (7); ignored by the other modes */
-  int32_t panel;     /* Cholesky panel width 1..32, 0 = default (32) */
+  int32_t panel;     /* Cholesky panel width: 1, 2, 4, 8, 16 or 32; 0 = default (32) */
   int32_t reserved;  /* must be 0 */
   double rel_tol;    /* pivot threshold factor; default 1e-9 (Appendix) */
 } cpinv_opts;
@@ -268,6 +268,17 @@ int cpinv_profile_enable(int on);
  * are (may exceed max_entries), and clears the records.  Returns -1 on a CUDA
  * error. */
 int cpinv_profile_read(cpinv_profile_entry* out, int max_entries);
+/* The same records as a timeline, without clearing them: for each traced
+ * launch in launch order, its kernel class and the device times (ms) of its
+ * two events relative to the first record's start.  Writes up to
+ * max_entries, returns the number of records (or -1 on a CUDA error).  Call
+ * it before cpinv_profile_read. */
+typedef struct cpinv_timeline_entry {
+  char name[32];     /* kernel class, as in cpinv_profile_entry */
+  double start_ms;
+  double end_ms;
+} cpinv_timeline_entry;
+int cpinv_profile_timeline(cpinv_timeline_entry* out, int max_entries);
 /* Number of kernels the library has launched in this process. */
 int64_t cpinv_launch_count(void);
 

@@ -46,6 +46,11 @@ class Problem(ctypes.Structure):
                 ("W", ctypes.c_void_p), ("ldw", ctypes.c_int64)]
 
 
+class TimelineEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("start_ms", ctypes.c_double),
+                ("end_ms", ctypes.c_double)]
+
+
 class CpinvError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"cpinv status {status}: {msg}")
@@ -89,6 +94,7 @@ SIGNATURES = {
                                     ctypes.c_int32, _c_vp]),
     "cpinv_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "cpinv_profile_read": (ctypes.c_int, [ctypes.POINTER(ProfileEntry), ctypes.c_int]),
+    "cpinv_profile_timeline": (ctypes.c_int, [ctypes.POINTER(TimelineEntry), ctypes.c_int]),
     "cpinv_launch_count": (ctypes.c_int64, []),
 }
 
@@ -339,6 +345,17 @@ def profile_read() -> dict:
         raise CpinvError(4, "profile read failed")
     return {arr[i].name.decode(): {"launches": int(arr[i].launches), "ms": float(arr[i].ms),
                                    "flops": float(arr[i].flops)} for i in range(min(n, 16))}
+
+
+def profile_timeline(max_entries: int = 100000) -> list:
+    """Per traced launch (launch order): (class, start_ms, end_ms) relative
+    to the first traced launch.  Call before ``profile_read``."""
+    arr = (TimelineEntry * max_entries)()
+    n = lib().cpinv_profile_timeline(arr, max_entries)
+    if n < 0:
+        raise CpinvError(4, "profile timeline failed")
+    return [(arr[i].name.decode(), float(arr[i].start_ms), float(arr[i].end_ms))
+            for i in range(min(n, max_entries))]
 
 
 def launch_count() -> int:

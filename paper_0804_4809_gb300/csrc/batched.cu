@@ -810,7 +810,7 @@ int check_opts(const cpinv_opts* o, double* rel_tol, int* panel) {
   if (!o) o = &d;
   if (o->reserved != 0) return CPINV_ERR_INVALID_ARG;
   if (!(o->rel_tol >= 0.0) || !std::isfinite(o->rel_tol)) return CPINV_ERR_INVALID_ARG;
-  if (o->panel != 0 && o->panel != 16 && o->panel != 32) return CPINV_ERR_INVALID_ARG;
+  if (o->panel != 0 && o->panel != 16 && o->panel != 32) return CPINV_ERR_INVALID_ARG;  // tuned set
   if (o->mode != CPINV_MODE_FP64) return CPINV_ERR_UNSUPPORTED;
   *rel_tol = o->rel_tol;
   *panel = o->panel;

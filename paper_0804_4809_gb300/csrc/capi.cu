@@ -236,7 +236,7 @@ CholLayout chol_layout(const Plan& p) {
 size_t chol_need(const Plan& p) {
   if (!chol_exact_ok(p)) return 0;
   const CholLayout L = chol_layout(p);
-  return L.rl_bytes + L.r_bytes + L.e_bytes + 3 * 1024;
+  return L.rl_bytes + 2 * L.r_bytes + L.e_bytes + 4 * 1024;
 }
 
 size_t crt_plan_bytes(const Plan& p, Job job) {
@@ -308,7 +308,7 @@ bool make_plan(Plan& p, int64_t m, int64_t n, int64_t k, const cpinv_opts* o) {
   p.b = o->panel ? o->panel : 32;
   p.mode = o->mode;
   p.rel_tol = o->rel_tol;
-  if (p.b < 1 || p.b > 32) return false;
+  if (p.b < 1 || p.b > 32 || 64 % p.b != 0) return false;  // a divisor of 64, at most 32
   if (!(p.rel_tol >= 0.0) || !std::isfinite(p.rel_tol)) return false;
   if (o->mode != CPINV_MODE_FP64 && o->mode != CPINV_MODE_EXACT_SLICE &&
       o->mode != CPINV_MODE_SPLIT_BF16X3)
@@ -471,6 +471,50 @@ int factor(const Ctx& c, double* a, int64_t lda, int spd) {
 // CTAs of a fused panel launch that share the update of its diagonal block
 constexpr int64_t kPanelHelpers = 3;
 
+// A second library stream per device, with the events of the look-ahead
+// (reused cyclically: each wait is enqueued right after the record it
+// refers to, before that event is recorded again).
+constexpr int kSideEvents = 4;
+// CTAs of the look-ahead residue product: it overlaps the previous panel's
+// launch, which needs free SMs for its row CTAs
+constexpr int kLookaheadCtas = 152;
+struct SideStream {
+  int device;
+  std::mutex mu;  // one enqueuing thread at a time (the events are shared)
+  cudaStream_t s;
+  cudaEvent_t fork, join, mma[kSideEvents], done[kSideEvents];
+};
+std::mutex g_side_mu;
+std::vector<SideStream*> g_side;
+
+SideStream* side_stream() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lock(g_side_mu);
+  for (auto* x : g_side)
+    if (x->device == dev) return x;
+  auto* x = new SideStream();
+  x->device = dev;
+  // the highest priority: when a look-ahead product and a panel launch become
+  // ready together, the product's CTAs are placed first (one per SM), and the
+  // panel's CTAs fill the room left beside them
+  int lo = 0, hi = 0;
+  bool ok = cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithPriority(&x->s, cudaStreamNonBlocking, hi) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&x->fork, cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&x->join, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < kSideEvents && ok; ++i) {
+    ok = cudaEventCreateWithFlags(&x->mma[i], cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&x->done[i], cudaEventDisableTiming) == cudaSuccess;
+  }
+  if (!ok) {
+    delete x;
+    return nullptr;
+  }
+  g_side.push_back(x);
+  return x;
+}
+
 // Exact-slice left-looking variant of factor() (see chol_exact.cu).
 int factor_exact(const Ctx& c, double* a, int64_t lda, int spd) {
   const Plan& p = *c.p;
@@ -486,7 +530,7 @@ int factor_exact(const Ctx& c, double* a, int64_t lda, int spd) {
     return q;
   };
   void* RL = take(Ly.rl_bytes);
-  uint8_t* R = (uint8_t*)take(Ly.r_bytes);
+  uint8_t* Rbuf[2] = {(uint8_t*)take(Ly.r_bytes), (uint8_t*)take(Ly.r_bytes)};
   int32_t* E = (int32_t*)take(Ly.e_bytes);
   if (off > p.crt_bytes) return CPINV_ERR_WORKSPACE;
   const Dim nd = spd ? rdim(0, nA) : hdim(nA);
@@ -495,27 +539,47 @@ int factor_exact(const Ctx& c, double* a, int64_t lda, int spd) {
   CK(cudaMemsetAsync(RL, 0, Ly.rl_bytes, c.s));
   const crt::Consts* consts = crt_consts_device();
   if (!consts) return CPINV_ERR_CUDA;
-  for (int64_t k0 = 0; k0 < nA; k0 += b) {
-    if (k0 > 0) {
-      // residues of L(k0:n, 0:k0) L(P, 0:k0)', exactly, from the residue planes
+  // Look-ahead: the update of panel p splits into the columns 0 .. kb (kb a
+  // multiple of the residue planes' K block, kb <= k0 - b), whose residue
+  // product runs on a second stream as soon as panel p - 2 is done, i.e.
+  // while panel p - 1 is factored, and the last columns kb .. k0, summed
+  // exactly inside panel p's own launch.  Two residue buffers alternate.
+  SideStream* side = side_stream();
+  if (!side) return CPINV_ERR_CUDA;
+  std::lock_guard<std::mutex> side_lock(side->mu);
+  cudaStream_t s2 = side->s;
+  CK(cudaEventRecord(side->fork, c.s));
+  CK(cudaStreamWaitEvent(s2, side->fork, 0));
+  const int64_t kblk = crt_block_k();
+  for (int64_t k0 = 0, pi = 0; k0 < nA; k0 += b, ++pi) {
+    const int64_t kb = k0 >= b ? (k0 - b) / kblk * kblk : 0;
+    uint8_t* R = Rbuf[pi & 1];
+    if (kb > 0) {
+      // residues of L(k0:n, 0:kb) L(P, 0:kb)', exactly, from the residue planes
+      if (pi >= 2) CK(cudaStreamWaitEvent(s2, side->done[(pi - 2) % kSideEvents], 0));
       const Dim M = spd ? rdim(-k0, nA - k0) : hdim(nA - k0);
       const Dim N = spd ? rdim(-k0, b) : hdim(nA - k0 < b ? nA - k0 : b);
       GemmParams fl;
       std::memset(&fl, 0, sizeof(fl));
       fl.M = M;
       fl.N = N;
-      fl.K = spd ? rdim(0, k0) : hdim(k0);
+      fl.K = spd ? rdim(0, kb) : hdim(kb);
       fl.rdev = c.rdev();
-      CK(crt_mma(RL, Ly.rows, (int)k0, RL, Ly.rows, (int)k0, Ly.kpad, k0, Ly.n_mod, M, N, c.rdev(),
-                 0, R, Ly.rows, 256, &p.st->status, c.s, &t, &fl));
+      CK(crt_mma(RL, Ly.rows, (int)k0, RL, Ly.rows, (int)k0, Ly.kpad, kb, Ly.n_mod, M, N,
+                 c.rdev(), 0, R, Ly.rows, 256, &p.st->status, s2, &t, &fl, kLookaheadCtas));
+      CK(cudaEventRecord(side->mma[pi % kSideEvents], s2));
+      CK(cudaStreamWaitEvent(c.s, side->mma[pi % kSideEvents], 0));
     }
-    // A(k0:n, P) -= that update, the diagonal block, the rows below, residues
+    // A(k0:n, P) -= the update, the diagonal block, the rows below, residues
     PanelExactParams pp;
     std::memset(&pp, 0, sizeof(pp));
     pp.R = R;
     pp.Mpad = Ly.rows;
     pp.Npad = 256;
     pp.has_update = k0 > 0;
+    pp.has_bulk = kb > 0;
+    pp.kb = kb;
+    pp.k_last = (int32_t)(k0 - kb);
     pp.n_upd = Ly.n_mod;
     pp.consts = consts;
     pp.A = a;
@@ -543,7 +607,11 @@ int factor_exact(const Ctx& c, double* a, int64_t lda, int spd) {
     }
     CK(diag_timer(c, k0, b, spd).run(KT_DIAG, c.s,
                                      [&] { return launch_chol_panel_exact(pp, c.s); }));
+    CK(cudaEventRecord(side->done[pi % kSideEvents], c.s));
   }
+  // join the second stream back
+  CK(cudaEventRecord(side->join, s2));
+  CK(cudaStreamWaitEvent(c.s, side->join, 0));
   if (spd)
     CK(t.run(KT_AUX, c.s, [&] {
       return launch_tri_block_inverse(a, lda, nA, c.rdev(), b, p.Tinv, c.s);
@@ -980,7 +1048,8 @@ static int check_opts(const cpinv_opts* o) {
   if (o->mode != CPINV_MODE_FP64 && o->mode != CPINV_MODE_EXACT_SLICE &&
       o->mode != CPINV_MODE_SPLIT_BF16X3)
     return CPINV_ERR_INVALID_ARG;
-  if (o->panel < 0 || o->panel > 32 || o->reserved != 0) return CPINV_ERR_INVALID_ARG;
+  if (o->panel < 0 || o->panel > 32 || (o->panel && 64 % o->panel) || o->reserved != 0)
+    return CPINV_ERR_INVALID_ARG;
   if (!(o->rel_tol >= 0.0) || !std::isfinite(o->rel_tol)) return CPINV_ERR_INVALID_ARG;
   return CPINV_OK;
 }
@@ -1280,6 +1349,27 @@ int cpinv_profile_read(cpinv_profile_entry* out, int max_entries) {
       out[n].launches = launches[k];
       out[n].ms = ms[k];
       out[n].flops = flops[k];
+    }
+    ++n;
+  }
+  return n;
+}
+
+int cpinv_profile_timeline(cpinv_timeline_entry* out, int max_entries) {
+  if (cudaDeviceSynchronize() != cudaSuccess) return -1;
+  if (g_tr.recs.empty()) return 0;
+  const cudaEvent_t origin = g_tr.recs.front().e0;
+  int n = 0;
+  for (auto& t : g_tr.recs) {
+    if (out && n < max_entries) {
+      float a = 0.f, b = 0.f;
+      if (cudaEventElapsedTime(&a, origin, t.e0) != cudaSuccess ||
+          cudaEventElapsedTime(&b, origin, t.e1) != cudaSuccess)
+        return -1;
+      std::memset(&out[n], 0, sizeof(out[n]));
+      std::strncpy(out[n].name, kKindName[t.kind], sizeof(out[n].name) - 1);
+      out[n].start_ms = a;
+      out[n].end_ms = b;
     }
     ++n;
   }

@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(256) panel_solve_split_kernel(
 // The grid is small (at most 1 + n/8 CTAs of 256 threads, four resident per
 // SM), so every CTA is resident at once; no CTA waits on one that waits.
 constexpr uint32_t kFlagSpinLimit = 1u << 22;
+constexpr int kMaxLast = 64;  // columns of the update summed in the panel kernel itself
 
 // The waiters poll with relaxed loads (an acquire load per poll would
 // invalidate the SM's L1 each time, slowing every CTA on that SM, the
@@ -117,38 +118,68 @@ __device__ __forceinline__ void st_release(int64_t* p, int64_t v) {
   asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// A(k0 + ir, k0 + jc) - X(ir, jc), X the exact update (residues in R), the
-// difference rounded once.
+// Signed magnitude of the beta-bit integer that the residue planes hold for
+// the factor entry v of a row with scale E (sign in bit 63).
+__device__ __forceinline__ uint64_t scaled_int(double v, int E, int beta) {
+  const uint64_t bits = (uint64_t)__double_as_longlong(v);
+  return crt::integerize(bits, E, beta) | (bits & 0x8000000000000000ull);
+}
+
+// acc += a b for signed-magnitude integers below 2^62 (acc two's complement
+// over 128 bits: sums of up to 64 such products fit).
+__device__ __forceinline__ void mac128(uint64_t& lo, int64_t& hi, uint64_t a, uint64_t b) {
+  const uint64_t ma = a & 0x7FFFFFFFFFFFFFFFull, mb = b & 0x7FFFFFFFFFFFFFFFull;
+  const uint64_t plo = ma * mb, phi = __umul64hi(ma, mb);
+  if ((a ^ b) >> 63) {
+    const uint64_t r = lo - plo;
+    hi -= (int64_t)(phi + (r > lo ? 1u : 0u));
+    lo = r;
+  } else {
+    const uint64_t r = lo + plo;
+    hi += (int64_t)(phi + (r < plo ? 1u : 0u));
+    lo = r;
+  }
+}
+
+// A(k0 + ir, k0 + jc) - X(ir, jc), the difference rounded once, where X is the
+// exact update: the CRT value of the residues in R (columns 0 .. kb of the
+// factor, when has_bulk) plus (hi:lo), the exact sum over columns kb .. k0
+// formed by the caller from the factor's scaled integers.
 __device__ __forceinline__ double apply_update(const PanelExactParams& p,
                                                const crt::CrtShared& sh, int shift,
                                                float inv_ptop, int64_t ir, int64_t jc,
-                                               double a_old) {
-  const size_t plane = (size_t)p.Mpad * (size_t)p.Npad;
-  const uint8_t* r = p.R + ir * p.Npad + jc;
-  // every residue load in flight at once: one memory latency per output
-  uint32_t rv[crt::kMaxMod];
+                                               double a_old, uint64_t lo, int64_t hi) {
+  uint32_t Y[crt::kLimbs] = {0, 0, 0, 0, 0};
+  if (p.has_bulk) {
+    const size_t plane = (size_t)p.Mpad * (size_t)p.Npad;
+    const uint8_t* r = p.R + ir * p.Npad + jc;
+    // every residue load in flight at once: one memory latency per output
+    uint32_t rv[crt::kMaxMod];
 #pragma unroll
-  for (int m = 0; m < crt::kMaxMod; ++m) rv[m] = m < p.n_upd ? r[(size_t)m * plane] : 0u;
-  uint64_t acc[crt::kLimbs];
+    for (int m = 0; m < crt::kMaxMod; ++m) rv[m] = m < p.n_upd ? r[(size_t)m * plane] : 0u;
+    uint64_t acc[crt::kLimbs];
 #pragma unroll
-  for (int l = 0; l < crt::kLimbs; ++l) acc[l] = 0;
+    for (int l = 0; l < crt::kLimbs; ++l) acc[l] = 0;
 #pragma unroll
-  for (int m = 0; m < crt::kMaxMod; ++m) {
-    if (m >= p.n_upd) break;
-    const uint32_t t = sh.tab[m][rv[m]];
+    for (int m = 0; m < crt::kMaxMod; ++m) {
+      if (m >= p.n_upd) break;
+      const uint32_t t = sh.tab[m][rv[m]];
 #pragma unroll
-    for (int l = 0; l < crt::kLimbs; ++l) acc[l] += (uint64_t)t * sh.Mj[m][l];
+      for (int l = 0; l < crt::kLimbs; ++l) acc[l] += (uint64_t)t * sh.Mj[m][l];
+    }
+    uint32_t S[crt::kLimbs];
+    uint64_t carry = 0;
+#pragma unroll
+    for (int l = 0; l < crt::kLimbs; ++l) {
+      const uint64_t v = acc[l] + carry;
+      S[l] = (uint32_t)v;
+      carry = v >> 32;
+    }
+    crt::crt_centre(S, sh.P, sh.halfP, shift, inv_ptop, Y);
   }
-  uint32_t S[crt::kLimbs];
-  uint64_t carry = 0;
-#pragma unroll
-  for (int l = 0; l < crt::kLimbs; ++l) {
-    const uint64_t v = acc[l] + carry;
-    S[l] = (uint32_t)v;
-    carry = v >> 32;
-  }
+  crt::limbs_add128(Y, lo, hi);
   const int scale = p.E[p.k0 + ir] - 1022 - p.beta + p.E[p.k0 + jc] - 1022 - p.beta;
-  const double x = crt::crt_finish(S, sh.P, sh.halfP, shift, inv_ptop, scale);
+  const double x = crt::limbs_to_double(Y, scale);
   return fma(1.0, a_old, -x);
 }
 
@@ -180,26 +211,42 @@ __global__ void __launch_bounds__(256, 4) chol_panel_exact_kernel(PanelExactPara
   __shared__ crt::CrtShared sh;
   __shared__ double Ts[32][33];
   __shared__ double dv[32];
+  __shared__ uint64_t Lt[kMaxLast][32];  // Lt[k][j]: scaled integer of L(k0 + j, kb + k)
   __shared__ int go;
+  double* A = p.A;
+  const int64_t lda = p.lda;
   int shift = 0;
   float inv_ptop = 0.f;
   if (p.has_update) {
-    const crt::Consts& c = p.consts[p.n_upd];
-    const uint32_t* src = reinterpret_cast<const uint32_t*>(&c.tab[0][0]);
-    uint32_t* dst = reinterpret_cast<uint32_t*>(&sh.tab[0][0]);
-    for (int e = threadIdx.x; e < p.n_upd * 32; e += blockDim.x) dst[e] = src[e];
-    for (int e = threadIdx.x; e < p.n_upd * crt::kLimbs; e += blockDim.x)
-      sh.Mj[e / crt::kLimbs][e % crt::kLimbs] = c.Mj[e / crt::kLimbs][e % crt::kLimbs];
-    if (threadIdx.x < crt::kLimbs) {
-      sh.P[threadIdx.x] = c.P[threadIdx.x];
-      sh.halfP[threadIdx.x] = c.halfP[threadIdx.x];
+    if (p.has_bulk) {
+      const crt::Consts& c = p.consts[p.n_upd];
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(&c.tab[0][0]);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&sh.tab[0][0]);
+      for (int e = threadIdx.x; e < p.n_upd * 32; e += blockDim.x) dst[e] = src[e];
+      for (int e = threadIdx.x; e < p.n_upd * crt::kLimbs; e += blockDim.x)
+        sh.Mj[e / crt::kLimbs][e % crt::kLimbs] = c.Mj[e / crt::kLimbs][e % crt::kLimbs];
+      if (threadIdx.x < crt::kLimbs) {
+        sh.P[threadIdx.x] = c.P[threadIdx.x];
+        sh.halfP[threadIdx.x] = c.halfP[threadIdx.x];
+      }
+      shift = c.shift;
+      inv_ptop = c.inv_ptop;
     }
-    shift = c.shift;
-    inv_ptop = c.inv_ptop;
+    // the block's rows over the last columns kb .. k0, as scaled integers
+    for (int e = threadIdx.x; e < p.k_last * 32; e += blockDim.x) {
+      const int k = e >> 5, j = e & 31;
+      Lt[k][j] = j < bw ? scaled_int(A[(k0 + j) * lda + p.kb + k], p.E[k0 + j], p.beta) : 0ull;
+    }
     __syncthreads();
   }
-  double* A = p.A;
-  const int64_t lda = p.lda;
+  // the exact update of block entry (i, j): CRT part + sum over the last columns
+  auto block_update = [&](int i, int j) {
+    uint64_t lo = 0;
+    int64_t hi = 0;
+    for (int k = 0; k < p.k_last; ++k) mac128(lo, hi, Lt[k][i], Lt[k][j]);
+    double* a = A + (k0 + i) * lda + (k0 + j);
+    *a = apply_update(p, sh, shift, inv_ptop, i, j, *a, lo, hi);
+  };
   const int tri = bw * (bw + 1) / 2;
   if (helper) {
     // this CTA's share of the diagonal block's update, then count it
@@ -209,8 +256,7 @@ __global__ void __launch_bounds__(256, 4) chol_panel_exact_kernel(PanelExactPara
     for (int o = beg + threadIdx.x; o < end; o += blockDim.x) {
       int i, j;
       tri_index(o, i, j);
-      double* a = A + (k0 + i) * lda + (k0 + j);
-      *a = apply_update(p, sh, shift, inv_ptop, i, j, *a);
+      block_update(i, j);
     }
     __threadfence();
     __syncthreads();
@@ -218,13 +264,12 @@ __global__ void __launch_bounds__(256, 4) chol_panel_exact_kernel(PanelExactPara
     if (row0 >= n) return;
   }
   if (blockIdx.x == 0) {
-    // the diagonal block: update (lower part), factor, residues, publish
+    // the diagonal block: update (lower part), factor, publish, residues
     if (p.has_update && p.helpers == 0) {
       for (int o = threadIdx.x; o < tri; o += blockDim.x) {
         int i, j;
         tri_index(o, i, j);
-        double* a = A + (k0 + i) * lda + (k0 + j);
-        *a = apply_update(p, sh, shift, inv_ptop, i, j, *a);
+        block_update(i, j);
       }
       __syncthreads();
     } else if (p.has_update) {
@@ -261,9 +306,28 @@ __global__ void __launch_bounds__(256, 4) chol_panel_exact_kernel(PanelExactPara
   const int64_t i = row0 + warp;
   const bool row_ok = i < n;
   double acc = 0.0;
-  if (row_ok && lane < bw) {
+  if (row_ok && p.has_update) {
+    // this row's scaled integers over the last columns, lane k holding k,
+    // k + 32, k + 64; lane c sums against column c of the block
+    uint64_t ai[kMaxLast / 32];
+#pragma unroll
+    for (int q = 0; q < kMaxLast / 32; ++q) {
+      const int k = lane + 32 * q;
+      ai[q] = k < p.k_last ? scaled_int(A[i * lda + p.kb + k], p.E[i], p.beta) : 0ull;
+    }
+    uint64_t lo = 0;
+    int64_t hi = 0;
+#pragma unroll
+    for (int q = 0; q < kMaxLast / 32; ++q) {
+      const int kend = p.k_last - 32 * q < 32 ? p.k_last - 32 * q : 32;
+      for (int kk = 0; kk < kend; ++kk) {
+        const uint64_t a = __shfl_sync(0xffffffffu, ai[q], kk);
+        mac128(lo, hi, a, Lt[32 * q + kk][lane]);
+      }
+    }
+    if (lane < bw) acc = apply_update(p, sh, shift, inv_ptop, i - k0, lane, A[i * lda + k0 + lane], lo, hi);
+  } else if (row_ok && lane < bw) {
     acc = A[i * lda + k0 + lane];
-    if (p.has_update) acc = apply_update(p, sh, shift, inv_ptop, i - k0, lane, acc);
   }
   if (threadIdx.x == 0) {
     int ok = 0;
@@ -317,7 +381,9 @@ int64_t chol_panel_exact_ctas(int64_t nmax, int64_t k0, int b) {
 }
 
 cudaError_t launch_chol_panel_exact(const PanelExactParams& p, cudaStream_t s) {
-  if (p.b > 32 || p.b < 1 || (p.has_update && !p.consts)) return cudaErrorInvalidValue;
+  if (p.b > 32 || p.b < 1 || (p.has_bulk && (!p.consts || !p.R))) return cudaErrorInvalidValue;
+  if (p.k_last < 0 || p.k_last > kMaxLast || (p.has_update && p.kb + p.k_last != p.k0))
+    return cudaErrorInvalidValue;
   const int64_t ctas = chol_panel_exact_ctas(p.nd.max, p.k0, p.b);
   if (p.helpers < 0 || p.helpers >= ctas) return cudaErrorInvalidValue;
   chol_panel_exact_kernel<<<(unsigned)ctas, 256, 0, s>>>(p);

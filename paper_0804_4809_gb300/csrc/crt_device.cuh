@@ -134,11 +134,11 @@ struct CrtShared {
   uint32_t halfP[crt::kLimbs];
 };
 
-// S (the CRT sum, < n P) -> centred X = S mod P in (-P/2, P/2] -> FP64,
-// correctly rounded, times 2^scale.
-__device__ __forceinline__ double crt_finish(const uint32_t (&S)[crt::kLimbs],
-                                             const uint32_t* P, const uint32_t* halfP, int shift,
-                                             float inv_ptop, int scale) {
+// S (the CRT sum, < n P) -> X = S mod P centred into (-P/2, P/2], as a
+// two's complement integer of kLimbs limbs.
+__device__ __forceinline__ void crt_centre(const uint32_t (&S)[crt::kLimbs], const uint32_t* P,
+                                           const uint32_t* halfP, int shift, float inv_ptop,
+                                           uint32_t (&Y)[crt::kLimbs]) {
   // q = floor(S / P) in [0, n): estimate from the top bits, then correct
   uint64_t stop = 0;
 #pragma unroll
@@ -191,7 +191,7 @@ __device__ __forceinline__ double crt_finish(const uint32_t (&S)[crt::kLimbs],
       }
     }
   }
-  // centre: X > P/2 -> X - P (negative); magnitude and sign
+  // centre: X > P/2 -> X - P (negative, two's complement)
   bool gt = false, decided = false;
 #pragma unroll
   for (int l = crt::kLimbs - 1; l >= 0; --l) {
@@ -200,15 +200,56 @@ __device__ __forceinline__ double crt_finish(const uint32_t (&S)[crt::kLimbs],
       decided = true;
     }
   }
-  uint32_t mag[crt::kLimbs];
   int64_t bb = 0;
 #pragma unroll
   for (int l = 0; l < crt::kLimbs; ++l) {
-    const int64_t v = (int64_t)P[l] - (int64_t)X[l] + bb;
-    mag[l] = gt ? (uint32_t)v : X[l];
+    const int64_t v = (int64_t)X[l] - (int64_t)P[l] + bb;
+    Y[l] = gt ? (uint32_t)v : X[l];
     bb = v >> 32;
   }
-  return compose_double(gt, mag, scale);
+}
+
+// A two's complement integer of kLimbs limbs times 2^scale, correctly
+// rounded to FP64.
+__device__ __forceinline__ double limbs_to_double(const uint32_t (&Y)[crt::kLimbs], int scale) {
+  const bool neg = (int32_t)Y[crt::kLimbs - 1] < 0;
+  uint32_t mag[crt::kLimbs];
+  uint64_t c = 1;
+#pragma unroll
+  for (int l = 0; l < crt::kLimbs; ++l) {
+    if (neg) {
+      const uint64_t v = (uint64_t)(~Y[l]) + c;
+      mag[l] = (uint32_t)v;
+      c = v >> 32;
+    } else {
+      mag[l] = Y[l];
+    }
+  }
+  return compose_double(neg, mag, scale);
+}
+
+// Y += (hi:lo), a signed 128-bit two's complement integer.
+__device__ __forceinline__ void limbs_add128(uint32_t (&Y)[crt::kLimbs], uint64_t lo, int64_t hi) {
+  const uint32_t ext = hi < 0 ? 0xFFFFFFFFu : 0u;
+  const uint32_t w[crt::kLimbs] = {(uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)(uint64_t)hi,
+                                   (uint32_t)((uint64_t)hi >> 32), ext};
+  uint64_t c = 0;
+#pragma unroll
+  for (int l = 0; l < crt::kLimbs; ++l) {
+    const uint64_t v = (uint64_t)Y[l] + w[l] + c;
+    Y[l] = (uint32_t)v;
+    c = v >> 32;
+  }
+}
+
+// S (the CRT sum, < n P) -> centred X = S mod P in (-P/2, P/2] -> FP64,
+// correctly rounded, times 2^scale.
+__device__ __forceinline__ double crt_finish(const uint32_t (&S)[crt::kLimbs],
+                                             const uint32_t* P, const uint32_t* halfP, int shift,
+                                             float inv_ptop, int scale) {
+  uint32_t Y[crt::kLimbs];
+  crt_centre(S, P, halfP, shift, inv_ptop, Y);
+  return limbs_to_double(Y, scale);
 }
 
 }  // namespace crt

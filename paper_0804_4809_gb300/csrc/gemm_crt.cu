@@ -920,7 +920,8 @@ cudaError_t crt_split(const double* X, int64_t ld, int tview, Dim rows, Dim K, c
 cudaError_t crt_mma(const void* SA, int64_t a_rows, int a_row0, const void* SB, int64_t b_rows,
                     int b_row0, int64_t kpad, int64_t kuse, int n_mod, Dim M, Dim N,
                     const int64_t* rdev, int lower, uint8_t* R, int64_t Mpad, int64_t Npad,
-                    int32_t* status, cudaStream_t s, KernelTimer* timer, const GemmParams* fl) {
+                    int32_t* status, cudaStream_t s, KernelTimer* timer, const GemmParams* fl,
+                    int max_ctas) {
   const int64_t Mmax = M.max, Nmax = N.max;
   if (Mmax <= 0 || Nmax <= 0) return cudaSuccess;
   const int BN = (Nmax >= 2048) ? 256 : (Nmax <= 32 ? 32 : 128);
@@ -942,11 +943,13 @@ cudaError_t crt_mma(const void* SA, int64_t a_rows, int a_row0, const void* SB, 
   mp.Mpad = Mpad;
   mp.Npad = Npad;
   mp.status = status;
-  // CTAs: about one wave of (tile, group of moduli); a CTA runs its moduli
-  // back to back (double-buffered accumulators), amortising its set-up
+  // CTAs: about one wave of (tile, group of moduli) -- or max_ctas, to leave
+  // SMs to concurrent work; a CTA runs its moduli back to back
+  // (double-buffered accumulators), amortising its set-up
   int64_t tiles = ((Mmax + BM - 1) / BM) * ((Nmax + BN - 1) / BN) / (lower ? 2 : 1);
   if (tiles < 1) tiles = 1;
-  int64_t groups = (152 + tiles - 1) / tiles;
+  const int64_t wave = max_ctas > 0 ? max_ctas : 152;
+  int64_t groups = (wave + tiles - 1) / tiles;
   if (groups > n_mod) groups = n_mod;
   if (groups < 1) groups = 1;
   mp.mods_per_cta = (int)((n_mod + groups - 1) / groups);
@@ -955,6 +958,9 @@ cudaError_t crt_mma(const void* SA, int64_t a_rows, int a_row0, const void* SB, 
   mt.flops_mult = (double)n_mod;
   return mt.run(KT_MMA, s, [&] {
     if (BN == 256) return launch_mma<256, 4, false>(ta, tb, mp, Mmax, Nmax, s);
+    // a capped grid shares the SMs with concurrent work: fewer stages, less
+    // shared memory per CTA
+    if (BN == 32 && max_ctas > 0) return launch_mma<32, 4, false>(ta, tb, mp, Mmax, Nmax, s);
     if (BN == 32) return launch_mma<32, 8, false>(ta, tb, mp, Mmax, Nmax, s);
     return launch_mma<128, 6, false>(ta, tb, mp, Mmax, Nmax, s);
   });

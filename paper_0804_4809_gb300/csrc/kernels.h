@@ -86,7 +86,8 @@ cudaError_t crt_split(const double* X, int64_t ld, int tview, Dim rows, Dim K, c
 cudaError_t crt_mma(const void* SA, int64_t a_rows, int a_row0, const void* SB, int64_t b_rows,
                     int b_row0, int64_t kpad, int64_t kuse, int n_mod, Dim M, Dim N,
                     const int64_t* rdev, int lower, uint8_t* R, int64_t Mpad, int64_t Npad,
-                    int32_t* status, cudaStream_t s, KernelTimer* timer, const GemmParams* fl);
+                    int32_t* status, cudaStream_t s, KernelTimer* timer, const GemmParams* fl,
+                    int max_ctas = 0);
 cudaError_t crt_reconstruct(const uint8_t* R, int64_t Mpad, int64_t Npad, Dim M, Dim N,
                             const int64_t* rdev, const int32_t* EA, const int32_t* EB, int betaA,
                             int betaB, double alpha, double beta, double* C, int64_t ldc,
@@ -103,9 +104,12 @@ cudaError_t launch_panel_solve_split(double* A, int64_t lda, Dim nd, const int64
 // One fused launch per panel of the exact-slice factorisation (update
 // reconstruction, diagonal block, rows below, residue split).
 struct PanelExactParams {
-  const uint8_t* R;   // update residues R[j][row][col] (rows from k0)
+  const uint8_t* R;   // residues of the update over columns 0 .. kb, R[j][row][col] (rows from k0)
   int64_t Mpad, Npad;
   int32_t has_update, n_upd;  // moduli count of the update
+  int32_t has_bulk;   // kb > 0: R holds the part over columns 0 .. kb
+  int32_t k_last;     // columns kb .. k0 (<= 64) summed exactly in the kernel
+  int64_t kb;
   const crt::Consts* consts;  // crt_consts_device()
   double* A;
   int64_t lda;
