@@ -719,8 +719,9 @@ int front_inverse(const Ctx& c) {
   }));
   rc = tri_inverse(c, p.bufA, p.bufW, p.bufM);
   if (rc) return rc;
-  // M = W'W (full, symmetric)
-  CK(matmul(c, S_PROD, p.bufW, nA, true, p.bufW, nA, false, p.bufM, nA, R, R, R, 1.0, 0.0, 0));
+  // M = W'W: the lower triangle, mirrored (symmetric)
+  CK(matmul(c, S_PROD, p.bufW, nA, true, p.bufW, nA, false, p.bufM, nA, R, R, R, 1.0, 0.0, 1));
+  CK(KernelTimer().run(KT_AUX, c.s, [&] { return launch_mirror(p.bufM, nA, R, c.rdev(), c.s); }));
   return CPINV_OK;
 }
 
@@ -1104,11 +1105,13 @@ int cpinv_pinv(const double* G, int64_t m, int64_t n, int64_t ldg, double* Gp, i
     if (int r = front_inverse(c)) return r;
     const int64_t nA = p.nA;
     const Dim R = rdim(0, nA);
-    // X = L M  (bufW),  K = X X'  (bufA)
+    // X = L M  (bufW),  K = X X'  (bufA: the lower triangle, mirrored)
     CK(matmul(c, S_CHAIN, p.bufL, nA, false, p.bufM, nA, false, p.bufW, nA, hdim(nA), R, R, 1.0,
               0.0, 0));
     CK(matmul(c, S_CHAIN, p.bufW, nA, false, p.bufW, nA, true, p.bufA, nA, hdim(nA), hdim(nA), R,
-              1.0, 0.0, 0));
+              1.0, 0.0, 1));
+    CK(KernelTimer().run(KT_AUX, c.s,
+                         [&] { return launch_mirror(p.bufA, nA, hdim(nA), c.rdev(), c.s); }));
     if (!p.trans)  // G+ = K G'   (n x n)(n x m)
       CK(matmul(c, S_CHAIN, p.bufA, nA, false, G, ldg, true, Gp, ldgp, hdim(n), hdim(m), hdim(n),
                 1.0, 0.0, 0));

@@ -1009,7 +1009,7 @@ cudaError_t crt_reconstruct(const uint8_t* R, int64_t Mpad, int64_t Npad, Dim M,
   rp.lower = lower;
   rp.pad = 0;
   // small outputs (factorisation panels): latency-bound, four lanes per output
-  const bool small = M.max * N.max <= ((int64_t)1 << 19);
+  const bool small = M.max * N.max <= ((int64_t)1 << 16);
   return timer->run(KT_RECON, s, [&] {
     if (small)
       reconstruct_split_kernel<<<grid1d(M.max * N.max * kRecLanes, 256), 256, 0, s>>>(rp, n_mod);
