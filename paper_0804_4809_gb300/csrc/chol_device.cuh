@@ -82,19 +82,16 @@ __device__ __forceinline__ void diag_chol_block(double* A, int64_t lda, Dim nd, 
     // L2 loads: other CTAs of a fused launch may have just written the block
     a[q] = (lane < bw && j < bw && j <= lane) ? __ldcg(A + (k0 + lane) * lda + (k0 + j)) : 0.0;
   }
-  // Finishes column c held in `acol` (owner warp only); returns L(lane, c).
-  // The pivot test and 1/sqrt run on lane c alone (the FP64 pipe is narrow:
-  // a full-warp FP64 instruction costs many issue cycles), then y is
-  // broadcast and the column is scaled in one multiply.
+  // Finishes column c held in `acol` (owner warp only); returns L(lane, c):
+  // pivot test and 1/sqrt of lane c's entry, broadcast, the column scaled in
+  // one multiply.
   auto pivot = [&](int c, double acol) -> double {
-    double y = 0.0;
-    int ok = 0;
-    if (lane == c) {
-      ok = acol > tol;  // false for NaN
-      if (ok) y = rsqrt_newton(acol);
-    }
-    y = __shfl_sync(0xffffffffu, y, c);
-    ok = __shfl_sync(0xffffffffu, ok, c);
+    // every lane runs the chain on its own entry (no divergence; the FP64
+    // pipe's cost per warp instruction does not depend on the active lanes)
+    // and lane c's result is broadcast; a rejected pivot gives y = 0
+    const double yl = acol > tol ? rsqrt_newton(acol) : 0.0;  // false for NaN
+    const double y = __shfl_sync(0xffffffffu, yl, c);
+    const int ok = y != 0.0;
     const double l = (ok && lane >= c) ? acol * y : 0.0;  // lane c: d y = sqrt(d)
     colbuf[c % 3][lane] = l;
     if (lane == c) {
