@@ -106,6 +106,35 @@ int cpinv_lstsq(const double* G, int64_t m, int64_t n, int64_t ldg,
                 const cpinv_opts* o, int64_t* rank_out, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Least squares from accumulated normal equations (incremental learning,
+ * Sec. 4: the network is trained as data arrive).  The method (Appendix,
+ * Theorem 1) needs G only through A = G'G and B = G'F:
+ *   W = L (L'L)^-1 (L'L)^-1 L' B,   L the full-rank Cholesky factor of A,
+ * so blocks of rows G_i, F_i can be folded in one at a time.
+ *
+ * cpinv_gram_update: A += G'G (lower triangle written; the upper one is not
+ *   read by the solver) and, if F != NULL, B += G'F, in the arithmetic of
+ *   `mode` (exact-slice: each increment correctly rounded, then added in
+ *   FP64).  G: m x n, F: m x k, A: n x n (lda >= n), B: n x k (ldb >= k);
+ *   device pointers; workspace cpinv_gram_update_workspace_size(m, n, k,
+ *   mode) bytes, 256-byte aligned.  Enqueues only.
+ * cpinv_lstsq_gram: W (n x k) from A (lower triangle) and B, with the
+ *   Appendix tolerance taken over A's diagonal; rank_out as for cpinv_lstsq.
+ *   Equals cpinv_lstsq(G, F) when A and B were accumulated from all rows of
+ *   G and F (up to the roundings of the accumulation).
+ * ------------------------------------------------------------------------- */
+size_t cpinv_gram_update_workspace_size(int64_t m, int64_t n, int64_t k, int32_t mode);
+int cpinv_gram_update(const double* G, int64_t m, int64_t n, int64_t ldg,
+                      const double* F, int64_t k, int64_t ldf,
+                      double* A, int64_t lda, double* B, int64_t ldb,
+                      int32_t mode, void* workspace, size_t workspace_bytes, void* stream);
+size_t cpinv_lstsq_gram_workspace_size(int64_t n, int64_t k, const cpinv_opts* o);
+int cpinv_lstsq_gram(const double* A, int64_t n, int64_t lda, const double* B, int64_t k,
+                     int64_t ldb, double* W, int64_t ldw,
+                     void* workspace, size_t workspace_bytes,
+                     const cpinv_opts* o, int64_t* rank_out, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Adjoint of the least-squares weights (reverse mode): given the cotangent
  * Wbar = dL/dW (n x k) of a scalar L of W = G+ F, returns
  *   dG = dL/dG (m x n)  and, if dF != NULL, dF = dL/dF (m x k),

@@ -231,6 +231,24 @@ def lstsq(G: np.ndarray, F: np.ndarray, rel_tol: float = REL_TOL,
     return geninv(G, rel_tol=rel_tol, exact_gram=exact_gram, keep=keep) @ F
 
 
+def lstsq_from_gram(A: np.ndarray, B: np.ndarray, rel_tol: float = REL_TOL) -> tuple:
+    """W = L M M L' B from given normal equations A = G'G, B = G'F (Appendix
+    steps from the Gram matrix on; Theorem 1 with L' G' F = L' B).  The
+    method needs G only through A and B, which is what makes accumulating
+    them block by block possible (Sec. 4: on-line and incremental learning).
+    Only the lower triangle of A is read.  Returns (W, rank)."""
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    A = np.tril(A) + np.tril(A, -1).T
+    tol = pivot_tolerance(A, rel_tol)
+    L, accepted, _ = full_rank_cholesky(A, tol)
+    r = L.shape[1]
+    if r == 0:
+        return np.zeros((A.shape[0], B.shape[1])), 0
+    M = np.linalg.inv(L.T @ L)
+    return L @ M @ M @ L.T @ B, r
+
+
 def penrose_residuals(G: np.ndarray, Y: np.ndarray) -> dict:
     """The four Penrose error matrices of Sec. 1 / Sec. 3, as max-abs and
     Frobenius norms: GYG - G, YGY - Y, (GY)' - GY, (YG)' - YG."""

@@ -79,6 +79,14 @@ SIGNATURES = {
                                             _c_vp, _c_i64, _c_vp, _c_i64, _c_vp, _c_i64, _c_vp,
                                             _c_i64, _c_vp, _c_sz, ctypes.POINTER(Opts),
                                             ctypes.POINTER(_c_i64), _c_vp]),
+    "cpinv_gram_update_workspace_size": (_c_sz, [_c_i64, _c_i64, _c_i64, ctypes.c_int32]),
+    "cpinv_gram_update": (ctypes.c_int, [_c_vp, _c_i64, _c_i64, _c_i64, _c_vp, _c_i64, _c_i64,
+                                         _c_vp, _c_i64, _c_vp, _c_i64, ctypes.c_int32, _c_vp,
+                                         _c_sz, _c_vp]),
+    "cpinv_lstsq_gram_workspace_size": (_c_sz, [_c_i64, _c_i64, ctypes.POINTER(Opts)]),
+    "cpinv_lstsq_gram": (ctypes.c_int, [_c_vp, _c_i64, _c_i64, _c_vp, _c_i64, _c_i64, _c_vp,
+                                        _c_i64, _c_vp, _c_sz, ctypes.POINTER(Opts),
+                                        ctypes.POINTER(_c_i64), _c_vp]),
     "cpinv_lstsq_batched_workspace_size": (_c_sz, [ctypes.c_int32, ctypes.POINTER(Problem),
                                                    ctypes.POINTER(Opts)]),
     "cpinv_lstsq_batched": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(Problem),
@@ -215,6 +223,57 @@ def rank(G: torch.Tensor, mode="fp64", rel_tol: float = 1e-9, panel: int = 0, sl
                           _stream(G.device))
     _check(st)
     return int(r.value), mask
+
+
+def gram_update(A: torch.Tensor, G: torch.Tensor, B: torch.Tensor | None = None,
+                F: torch.Tensor | None = None, mode="fp64") -> None:
+    """A += G'G (lower triangle) and, with F, B += G'F, in place."""
+    G = _mat(G, "G")
+    m, n = G.shape
+    if A.shape != (n, n) or not A.is_contiguous() or A.dtype != torch.float64:
+        raise ValueError("A must be a contiguous float64 n x n tensor")
+    k = 0
+    if F is not None:
+        F = _mat(F, "F")
+        k = F.shape[1]
+        if B is None or B.shape != (n, k) or not B.is_contiguous():
+            raise ValueError("B must be a contiguous n x k tensor")
+    md = _MODES[mode] if isinstance(mode, str) else int(mode)
+    nbytes = lib().cpinv_gram_update_workspace_size(m, n, max(k, 1), md)
+    if nbytes == 0:
+        raise CpinvError(1, "invalid sizes or mode")
+    ws = _workspace(nbytes, G.device)
+    st = lib().cpinv_gram_update(G.data_ptr(), m, n, _ld(G),
+                                 F.data_ptr() if F is not None else None, k,
+                                 _ld(F) if F is not None else 1, A.data_ptr(), n,
+                                 B.data_ptr() if B is not None else None, max(k, 1), md,
+                                 ws.data_ptr(), ws.numel(), _stream(G.device))
+    _check(st)
+
+
+def lstsq_gram(A: torch.Tensor, B: torch.Tensor, mode="fp64", rel_tol: float = 1e-9,
+               panel: int = 0):
+    """W = G+ F from normal equations A = G'G (lower triangle read), B = G'F.
+    Returns (W, rank)."""
+    A = _mat(A, "A")
+    B = _mat(B, "B")
+    n, k = A.shape[0], B.shape[1]
+    o = make_opts(mode, rel_tol, panel)
+    if A.shape != (n, n) or B.shape[0] != n:
+        raise ValueError("A must be n x n and B n x k")
+    W = torch.zeros((n, k), dtype=torch.float64, device=A.device)
+    if n == 0:
+        return W, 0
+    nbytes = lib().cpinv_lstsq_gram_workspace_size(n, k, ctypes.byref(o))
+    if nbytes == 0:
+        raise CpinvError(1, "invalid options or sizes")
+    ws = _workspace(nbytes, A.device)
+    r = _c_i64(-1)
+    st = lib().cpinv_lstsq_gram(A.data_ptr(), n, _ld(A), B.data_ptr(), k, _ld(B), W.data_ptr(),
+                                _ld(W), ws.data_ptr(), ws.numel(), ctypes.byref(o),
+                                ctypes.byref(r), _stream(A.device))
+    _check(st)
+    return W, int(r.value)
 
 
 def lstsq_backward(G: torch.Tensor, F: torch.Tensor, dW: torch.Tensor, mode="fp64",

@@ -124,7 +124,7 @@ void trace_end(int rec, cudaStream_t s, int kind, const GemmParams* g, double mu
 
 namespace {
 
-enum Job { JOB_RANK = 0, JOB_PINV = 1, JOB_LSTSQ = 2, JOB_BACKWARD = 3 };
+enum Job { JOB_RANK = 0, JOB_PINV = 1, JOB_LSTSQ = 2, JOB_BACKWARD = 3, JOB_GRAM_LSTSQ = 4 };
 
 struct Plan {
   int64_t m, n, nA, k;
@@ -619,17 +619,11 @@ int factor_exact(const Ctx& c, double* a, int64_t lda, int spd) {
   return CPINV_OK;
 }
 
-// Gram, tolerance, full-rank Cholesky, compaction.  Leaves L in bufL (JOB_PINV
-// / JOB_LSTSQ) and r in st->rank.
-int front_rank(const Ctx& c, const double* G, int64_t ldg, bool compact) {
+// Tolerance, full-rank Cholesky and compaction of the Gram matrix already in
+// bufA (lower triangle).  Leaves L in bufL (compact) and r in st->rank.
+int rank_from_gram(const Ctx& c, bool compact) {
   const Plan& p = *c.p;
   const int64_t nA = p.nA;
-  if (!p.trans)  // A = G'G
-    CK(matmul(c, S_GRAM, G, ldg, true, G, ldg, false, p.bufA, nA, hdim(nA), hdim(nA), hdim(p.m),
-              1.0, 0.0, 1));
-  else  // A = G G'
-    CK(matmul(c, S_GRAM, G, ldg, false, G, ldg, true, p.bufA, nA, hdim(nA), hdim(nA), hdim(p.n),
-              1.0, 0.0, 1));
   CK(KernelTimer().run(KT_AUX, c.s,
                        [&] { return launch_tol(p.bufA, nA, nA, p.rel_tol, p.st, c.s); }));
   int rc = chol_exact_ok(p) ? factor_exact(c, p.bufA, nA, 0) : factor(c, p.bufA, nA, 0);
@@ -641,6 +635,20 @@ int front_rank(const Ctx& c, const double* G, int64_t ldg, bool compact) {
       return launch_gather(p.bufA, nA, nA, p.colidx, p.bufL, nA, c.s);
     }));
   return CPINV_OK;
+}
+
+// Gram, tolerance, full-rank Cholesky, compaction.  Leaves L in bufL (JOB_PINV
+// / JOB_LSTSQ) and r in st->rank.
+int front_rank(const Ctx& c, const double* G, int64_t ldg, bool compact) {
+  const Plan& p = *c.p;
+  const int64_t nA = p.nA;
+  if (!p.trans)  // A = G'G
+    CK(matmul(c, S_GRAM, G, ldg, true, G, ldg, false, p.bufA, nA, hdim(nA), hdim(nA), hdim(p.m),
+              1.0, 0.0, 1));
+  else  // A = G G'
+    CK(matmul(c, S_GRAM, G, ldg, false, G, ldg, true, p.bufA, nA, hdim(nA), hdim(nA), hdim(p.n),
+              1.0, 0.0, 1));
+  return rank_from_gram(c, compact);
 }
 
 // W = U^-1 for the lower-triangular U (order r <= nA, ld nA), given the
@@ -999,6 +1007,90 @@ int begin(Plan& p, Job job, void* ws, size_t ws_bytes) {
 
 using namespace cpinv;
 
+namespace {
+
+// C = alpha op(A) op(B) + beta C in the given arithmetic (lower: only the
+// lower triangle of a square C); the body of cpinv_matmul.
+int product_raw(int32_t transA, int32_t transB, int64_t M, int64_t N, int64_t K, double alpha,
+                const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                int64_t ldc, int32_t mode, int32_t bits, int lower, void* workspace,
+                size_t workspace_bytes, int32_t check, void* stream) {
+  if (M < 0 || N < 0 || K < 0) return CPINV_ERR_INVALID_ARG;
+  if (mode != CPINV_MODE_FP64 && mode != CPINV_MODE_EXACT_SLICE &&
+      mode != CPINV_MODE_SPLIT_BF16X3)
+    return CPINV_ERR_INVALID_ARG;
+  const int64_t arows = transA ? K : M, acols = transA ? M : K;
+  const int64_t brows = transB ? N : K, bcols = transB ? K : N;
+  if ((arows > 0 && lda < acols) || (brows > 0 && ldb < bcols) || ldc < N)
+    return CPINV_ERR_INVALID_ARG;
+  if (M == 0 || N == 0) return CPINV_OK;
+  if (!C || (K > 0 && (!A || !B))) return CPINV_ERR_INVALID_ARG;
+  if (!std::isfinite(alpha) || !std::isfinite(beta)) return CPINV_ERR_INVALID_ARG;
+  if (C == A || C == B) return CPINV_ERR_INVALID_ARG;  // C must not alias an operand
+  const int beta_bits = bits ? bits : 53;
+  if (mode == CPINV_MODE_EXACT_SLICE && (beta_bits < 1 || beta_bits > 62)) return CPINV_ERR_INVALID_ARG;
+  const bool same = A == B && lda == ldb && (transA != 0) != (transB != 0) && M == N;
+  size_t need = 0;
+  if (mode == CPINV_MODE_FP64) need = 256;
+  else if (mode == CPINV_MODE_SPLIT_BF16X3) need = 1024 + split_workspace_bytes(M, N, K, same);
+  else {
+    const int64_t Kc = K < kCrtMaxK ? (K > 0 ? K : 1) : kCrtMaxK;
+    const int nm = crt_moduli_for(Kc, beta_bits, beta_bits);
+    if (nm < 0) return CPINV_ERR_INVALID_ARG;
+    need = 1024 + crt_workspace_bytes(M, N, Kc, nm, same);
+  }
+  if (!workspace || ((uintptr_t)workspace & 255u) || workspace_bytes < need)
+    return CPINV_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevState* st = (DevState*)workspace;
+  CK(cudaMemsetAsync(st, 0, sizeof(DevState), s));
+  GemmParams g;
+  std::memset(&g, 0, sizeof(g));
+  g.A = A;
+  g.B = B;
+  g.C = C;
+  g.lda = lda;
+  g.ldb = ldb;
+  g.ldc = ldc;
+  g.M = hdim(M);
+  g.N = hdim(N);
+  g.K = hdim(K);
+  g.alpha = alpha;
+  g.beta = beta;
+  g.rdev = &st->rank;
+  g.lower = lower && M == N;
+  if (mode == CPINV_MODE_FP64 || K == 0) {
+    KernelTimer t;
+    t.gemm = &g;
+    CK(t.run(KT_GEMM_FP64, s, [&] { return launch_dgemm(g, transA != 0, transB != 0, s); }));
+  } else if (mode == CPINV_MODE_SPLIT_BF16X3) {
+    CrtGemm sg;
+    sg.p = g;
+    sg.transA = transA != 0;
+    sg.transB = transB != 0;
+    sg.same_operand = same;
+    sg.betaA = sg.betaB = 0;
+    sg.ws = (char*)workspace + 1024;
+    sg.ws_bytes = workspace_bytes - 1024;
+    sg.st = st;
+    KernelTimer t;
+    CK(launch_split_gemm(sg, s, &t));
+  } else {
+    CK(crt_product(g, transA != 0, transB != 0, beta_bits, same, (char*)workspace + 1024,
+                   workspace_bytes - 1024, st, s));
+  }
+  CK(trace_resolve(s, &st->rank));
+  if (!check) return CPINV_OK;
+  DevState h;
+  CK(cudaMemcpyAsync(&h, st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h.status & ST_NONFINITE) return CPINV_ERR_NONFINITE_INPUT;
+  if (h.status & ST_TIMEOUT) return CPINV_ERR_TIMEOUT;
+  return CPINV_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 void cpinv_default_opts(cpinv_opts* o) {
@@ -1185,6 +1277,52 @@ int cpinv_lstsq(const double* G, int64_t m, int64_t n, int64_t ldg, const double
   return finish(Ctx{us, &p}, rank_out);
 }
 
+size_t cpinv_lstsq_gram_workspace_size(int64_t n, int64_t k, const cpinv_opts* o) {
+  Plan p{};
+  if (n < 0 || k < 0 || !make_plan(p, n, n, k > 0 ? k : 1, o)) return 0;
+  return plan_bytes(p, JOB_LSTSQ);
+}
+
+int cpinv_lstsq_gram(const double* A, int64_t n, int64_t lda, const double* B, int64_t k,
+                     int64_t ldb, double* W, int64_t ldw, void* workspace, size_t workspace_bytes,
+                     const cpinv_opts* o, int64_t* rank_out, void* stream) {
+  if (rank_out) *rank_out = -1;
+  if (int rc = check_opts(o)) return rc;
+  if (n < 0 || k < 0 || lda < n || ldb < k || ldw < k) return CPINV_ERR_INVALID_ARG;
+  if (n == 0) {
+    if (rank_out) *rank_out = 0;
+    return CPINV_OK;
+  }
+  // k == 0 still factors A: the rank is reported, no W is written
+  if (!A || (k > 0 && (!B || !W))) return CPINV_ERR_INVALID_ARG;
+  Plan p{};
+  if (!make_plan(p, n, n, k > 0 ? k : 1, o)) return CPINV_ERR_INVALID_ARG;
+  if (int rc = begin(p, JOB_LSTSQ, workspace, workspace_bytes)) return rc;
+  cudaStream_t us = (cudaStream_t)stream;
+  const GraphKey key = make_key(JOB_GRAM_LSTSQ, p, lda, ldb, ldw, A, B, W, workspace,
+                                workspace_bytes);
+  int rc = run_pipeline(p, us, key, [&](const Ctx& c) -> int {
+    // the caller's Gram matrix (lower triangle read) into the factor buffer
+    CK(cudaMemcpy2DAsync(p.bufA, (size_t)n * sizeof(double), A, (size_t)lda * sizeof(double),
+                         (size_t)n * sizeof(double), (size_t)n, cudaMemcpyDeviceToDevice, c.s));
+    if (int r = rank_from_gram(c, true)) return r;
+    if (k == 0) return CPINV_OK;
+    if (int r = front_inverse(c)) return r;
+    const int64_t nA = p.nA;
+    const Dim R = rdim(0, nA);
+    // W = L (M (M (L' B)))
+    CK(matmul(c, S_CHAIN, p.bufL, nA, true, B, ldb, false, p.c2, k, R, hdim(k), hdim(nA), 1.0,
+              0.0, 0));
+    CK(matmul(c, S_CHAIN, p.bufM, nA, false, p.c2, k, false, p.c3, k, R, hdim(k), R, 1.0, 0.0, 0));
+    CK(matmul(c, S_CHAIN, p.bufM, nA, false, p.c3, k, false, p.c2, k, R, hdim(k), R, 1.0, 0.0, 0));
+    CK(matmul(c, S_CHAIN, p.bufL, nA, false, p.c2, k, false, W, ldw, hdim(nA), hdim(k), R, 1.0,
+              0.0, 0));
+    return CPINV_OK;
+  });
+  if (rc) return rc;
+  return finish(Ctx{us, &p}, rank_out);
+}
+
 size_t cpinv_lstsq_backward_workspace_size(int64_t m, int64_t n, int64_t k, const cpinv_opts* o) {
   Plan p{};
   if (m < 0 || n < 0 || k < 0 || !make_plan(p, m, n, k, o)) return 0;
@@ -1253,69 +1391,31 @@ int cpinv_matmul(int32_t transA, int32_t transB, int64_t M, int64_t N, int64_t K
                  const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
                  int64_t ldc, int32_t mode, int32_t bits, void* workspace, size_t workspace_bytes,
                  int32_t check, void* stream) {
-  if (M < 0 || N < 0 || K < 0) return CPINV_ERR_INVALID_ARG;
-  if (mode != CPINV_MODE_FP64 && mode != CPINV_MODE_EXACT_SLICE &&
-      mode != CPINV_MODE_SPLIT_BF16X3)
-    return CPINV_ERR_INVALID_ARG;
-  const int64_t arows = transA ? K : M, acols = transA ? M : K;
-  const int64_t brows = transB ? N : K, bcols = transB ? K : N;
-  if ((arows > 0 && lda < acols) || (brows > 0 && ldb < bcols) || ldc < N)
-    return CPINV_ERR_INVALID_ARG;
-  if (M == 0 || N == 0) return CPINV_OK;
-  if (!C || (K > 0 && (!A || !B))) return CPINV_ERR_INVALID_ARG;
-  if (!std::isfinite(alpha) || !std::isfinite(beta)) return CPINV_ERR_INVALID_ARG;
-  if (C == A || C == B) return CPINV_ERR_INVALID_ARG;  // C must not alias an operand
-  const int beta_bits = bits ? bits : 53;
-  if (mode == CPINV_MODE_EXACT_SLICE && (beta_bits < 1 || beta_bits > 62)) return CPINV_ERR_INVALID_ARG;
-  const bool same = A == B && lda == ldb && (transA != 0) != (transB != 0) && M == N;
-  const size_t need = cpinv_matmul_workspace_size(M, N, K, mode, bits, same ? 1 : 0);
-  if (!workspace || ((uintptr_t)workspace & 255u) || workspace_bytes < need)
-    return CPINV_ERR_WORKSPACE;
-  cudaStream_t s = (cudaStream_t)stream;
-  DevState* st = (DevState*)workspace;
-  CK(cudaMemsetAsync(st, 0, sizeof(DevState), s));
-  GemmParams g;
-  std::memset(&g, 0, sizeof(g));
-  g.A = A;
-  g.B = B;
-  g.C = C;
-  g.lda = lda;
-  g.ldb = ldb;
-  g.ldc = ldc;
-  g.M = hdim(M);
-  g.N = hdim(N);
-  g.K = hdim(K);
-  g.alpha = alpha;
-  g.beta = beta;
-  g.rdev = &st->rank;
-  if (mode == CPINV_MODE_FP64 || K == 0) {
-    KernelTimer t;
-    t.gemm = &g;
-    CK(t.run(KT_GEMM_FP64, s, [&] { return launch_dgemm(g, transA != 0, transB != 0, s); }));
-  } else if (mode == CPINV_MODE_SPLIT_BF16X3) {
-    CrtGemm sg;
-    sg.p = g;
-    sg.transA = transA != 0;
-    sg.transB = transB != 0;
-    sg.same_operand = same;
-    sg.betaA = sg.betaB = 0;
-    sg.ws = (char*)workspace + 1024;
-    sg.ws_bytes = workspace_bytes - 1024;
-    sg.st = st;
-    KernelTimer t;
-    CK(launch_split_gemm(sg, s, &t));
-  } else {
-    CK(crt_product(g, transA != 0, transB != 0, beta_bits, same, (char*)workspace + 1024,
-                   workspace_bytes - 1024, st, s));
-  }
-  CK(trace_resolve(s, &st->rank));
-  if (!check) return CPINV_OK;
-  DevState h;
-  CK(cudaMemcpyAsync(&h, st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  if (h.status & ST_NONFINITE) return CPINV_ERR_NONFINITE_INPUT;
-  if (h.status & ST_TIMEOUT) return CPINV_ERR_TIMEOUT;
-  return CPINV_OK;
+  return product_raw(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, mode, bits, 0,
+                     workspace, workspace_bytes, check, stream);
+}
+
+size_t cpinv_gram_update_workspace_size(int64_t m, int64_t n, int64_t k, int32_t mode) {
+  if (m < 0 || n < 0 || k < 0) return 0;
+  const size_t a = cpinv_matmul_workspace_size(n, n, m, mode, 62, 1);
+  const size_t b = cpinv_matmul_workspace_size(n, k, m, mode, 53, 0);
+  if (!a || !b) return 0;
+  return a > b ? a : b;
+}
+
+int cpinv_gram_update(const double* G, int64_t m, int64_t n, int64_t ldg, const double* F,
+                      int64_t k, int64_t ldf, double* A, int64_t lda, double* B, int64_t ldb,
+                      int32_t mode, void* workspace, size_t workspace_bytes, void* stream) {
+  if (m < 0 || n < 0 || k < 0 || lda < n || (F && (ldf < k || !B || ldb < k))) return CPINV_ERR_INVALID_ARG;
+  if (m == 0 || n == 0) return CPINV_OK;
+  if (!G || !A || ldg < n) return CPINV_ERR_INVALID_ARG;
+  // A (lower) += G'G: the Gram increment in the arithmetic of the Gram (62-bit
+  // integers in the exact-slice mode: each increment correctly rounded)
+  int rc = product_raw(1, 0, n, n, m, 1.0, G, ldg, G, ldg, 1.0, A, lda, mode, 62, 1, workspace,
+                       workspace_bytes, 0, stream);
+  if (rc || !F || k == 0) return rc;
+  return product_raw(1, 0, n, k, m, 1.0, G, ldg, F, ldf, 1.0, B, ldb, mode, 53, 0, workspace,
+                     workspace_bytes, 0, stream);
 }
 
 int cpinv_profile_enable(int on) {

@@ -442,3 +442,23 @@ def test_correct_formula_passes_compact_pins():
 def test_planted_mistakes_are_caught(kind):
     with np.errstate(all="ignore"):
         assert not _pins_pass(_mutant(kind)), kind
+
+
+def test_lstsq_from_gram_matches_lstsq():
+    """Theorem 1 applied to F needs G only through A = G'G and B = G'F:
+    from the correctly rounded A and B the result equals lstsq(G, F) (the
+    two differ only in where G'F is rounded), and the normal equations
+    hold."""
+    G = inputs.rank_deficient(120, 40, 25, 61)
+    F = inputs.normal((120, 3), 62)
+    W, r = oracle.lstsq_from_gram(oracle.gram(G), oracle.exact_cross(G, F))
+    assert r == 25
+    W0 = oracle.lstsq(G, F)
+    assert np.linalg.norm(W - W0) <= 1e-11 * np.linalg.norm(W0)
+    res = G.T @ (G @ W - F)
+    assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(G) ** 2 * np.linalg.norm(W)
+    # only the lower triangle of A is read
+    A = oracle.gram(G)
+    A_up = A + np.triu(np.full_like(A, 7.0), 1)
+    W2, _ = oracle.lstsq_from_gram(A_up, oracle.exact_cross(G, F))
+    assert np.array_equal(W2, W)
