@@ -10,31 +10,36 @@
 namespace cpinv {
 namespace chol {
 
-// 1/sqrt(d) for d > 0 from a single-precision seed y0 (about 22 correct
-// bits) and one third-order correction: with e = 1 - d y0^2,
-//   1/sqrt(d) = y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3e^2/8 + O(e^3)),
-// so y = y0 + (y0 e)(1/2 + 3e/8) is accurate to O(e^3) ~ 2^-66: four
-// dependent FP64 operations (y0^2 is exact: y0 has 24 significant bits).
-// The seed is formed with integer operations on the bit patterns (FP64 <->
-// FP32 conversions are slow on this part): d = 2^(2k) f with f in [1, 4)
-// taken to float by truncating its significand, y0 = 2^-k rsqrtf(f).  A
-// subnormal d is scaled by 2^108 first and the result by 2^54 at the end.
-__device__ __forceinline__ double rsqrt_newton(double d) {
-  const bool sub = (((uint64_t)__double_as_longlong(d) >> 52) & 0x7FF) == 0;
-  const double dd = sub ? d * 0x1p108 : d;  // subnormal: work on d 2^108
-  const uint64_t bits = (uint64_t)__double_as_longlong(dd);
-  const int E = (int)((bits >> 52) & 0x7FF) - 1023;
+// Seed y0 ~ 1/sqrt(d) (about 22 correct bits) for a finite d > 0 given by
+// its bit pattern, with integer operations only (FP64 <-> FP32 conversions
+// and FP64 instructions are slow on this part): d = 2^(2k) f with f in
+// [1, 4) taken to float by truncating its significand, y0 = 2^-k rsqrtf(f).
+// A subnormal d is normalised by a leading-zero count first.
+__device__ __forceinline__ double rsqrt_seed(uint64_t bits) {
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  const uint64_t mant = bits & 0xFFFFFFFFFFFFFull;
+  const bool sub = ex == 0;
+  const int sh = sub ? __clzll((long long)mant) - 11 : 0;
+  const int E = sub ? -1022 - sh : ex - 1023;  // d = 1.frac 2^E
+  const uint64_t frac = (mant << sh) & 0xFFFFFFFFFFFFFull;
   const int k = E >> 1;  // floor(E / 2)
-  const uint32_t fbits =
-      ((uint32_t)(127 + (E - 2 * k)) << 23) | (uint32_t)((bits >> 29) & 0x7FFFFF);
+  const uint32_t fbits = ((uint32_t)(127 + (E - 2 * k)) << 23) | (uint32_t)(frac >> 29);
   const uint32_t sb = __float_as_uint(rsqrtf(__uint_as_float(fbits)));
   const int es = (int)((sb >> 23) & 0xFF) - 127 - k;  // exponent of the seed
-  const double y0 = __longlong_as_double(
+  return __longlong_as_double(
       (long long)(((uint64_t)(es + 1023) << 52) | ((uint64_t)(sb & 0x7FFFFF) << 29)));
-  const double e = fma(-dd, y0 * y0, 1.0);
-  const double y = fma(y0 * e, fma(e, 0.375, 0.5), y0);
-  // subnormal d: y * 2^54 by the exponent field (y is a normal number)
-  return sub ? __longlong_as_double(__double_as_longlong(y) + (54ll << 52)) : y;
+}
+
+// One third-order correction of the seed: with e = 1 - d y0^2,
+//   1/sqrt(d) = y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3e^2/8 + O(e^3)),
+// accurate to O(e^3) ~ 2^-66.  e is formed as 1 - (d y0) y0, which stays in
+// range for subnormal and huge d.  The pivot's column is scaled by the same
+// series, x / sqrt(d) = s + (s e)(1/2 + 3e/8) with s = x y0, so the product
+// x y0 runs beside the correction instead of after it.
+__device__ __forceinline__ double rsqrt_e(double d, double y0) { return fma(-(d * y0), y0, 1.0); }
+__device__ __forceinline__ double rsqrt_apply(double x, double y0, double e) {
+  const double s = x * y0;
+  return fma(s * e, fma(e, 0.375, 0.5), s);
 }
 
 // Named barriers 1 and 2 (0 is __syncthreads): producer / consumer hand-off
@@ -70,10 +75,12 @@ __device__ __forceinline__ void diag_chol_block(double* A, int64_t lda, Dim nd, 
   if (k0 >= n) return;
   const int bw = (int)((n - k0) < b ? (n - k0) : b);
   __shared__ double colbuf[3][32];
-  __shared__ double dinv_s[32];
+  __shared__ double y0_s[32], e_s[32];
   __shared__ int acc_s[32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const double tol = spd ? 0.0 : st->tol;
+  // the pivot test d > tol on the bit patterns (tol >= 0: a negative d, -0
+  // and NaN compare below or are excluded; +inf passes as it does in FP64)
+  const long long tolbits = __double_as_longlong(spd ? 0.0 : st->tol);
   // a[q]: this lane's entry of column 4 (t + q) + w during group t
   double a[8];
 #pragma unroll
@@ -82,21 +89,23 @@ __device__ __forceinline__ void diag_chol_block(double* A, int64_t lda, Dim nd, 
     // L2 loads: other CTAs of a fused launch may have just written the block
     a[q] = (lane < bw && j < bw && j <= lane) ? __ldcg(A + (k0 + lane) * lda + (k0 + j)) : 0.0;
   }
-  // Finishes column c held in `acol` (owner warp only); returns L(lane, c):
-  // pivot test and 1/sqrt of lane c's entry, broadcast, the column scaled in
-  // one multiply.
+  // Finishes column c held in `acol` (owner warp only); returns L(lane, c).
+  // Lane c's entry d is broadcast first and every lane runs the pivot test
+  // and the 1/sqrt chain on it (uniform: no divergence, no broadcast after
+  // the chain); a rejected pivot gives a zero column.
   auto pivot = [&](int c, double acol) -> double {
-    // every lane runs the chain on its own entry (no divergence; the FP64
-    // pipe's cost per warp instruction does not depend on the active lanes)
-    // and lane c's result is broadcast; a rejected pivot gives y = 0
-    const double yl = acol > tol ? rsqrt_newton(acol) : 0.0;  // false for NaN
-    const double y = __shfl_sync(0xffffffffu, yl, c);
-    const int ok = y != 0.0;
-    const double l = (ok && lane >= c) ? acol * y : 0.0;  // lane c: d y = sqrt(d)
+    const double d = __shfl_sync(0xffffffffu, acol, c);
+    const long long db = __double_as_longlong(d);
+    const bool ok = db > tolbits && db <= 0x7FF0000000000000ll;
+    const double y0 = rsqrt_seed((uint64_t)db);
+    const double e = rsqrt_e(d, y0);
+    const double lv = rsqrt_apply(acol, y0, e);  // lane c: d / sqrt(d)
+    const double l = (ok && lane >= c) ? lv : 0.0;
     colbuf[c % 3][lane] = l;
     if (lane == c) {
       acc_s[c] = ok;
-      dinv_s[c] = y;
+      y0_s[c] = y0;
+      e_s[c] = e;
     }
     return l;
   };
@@ -145,7 +154,10 @@ __device__ __forceinline__ void diag_chol_block(double* A, int64_t lda, Dim nd, 
   }
   bar_sync(3, kDiagThreads);  // the four warps only (the caller's CTA may be larger)
   if (threadIdx.x < bw) {
-    dinv[threadIdx.x] = dinv_s[threadIdx.x];
+    // 1/T(c, c) from the stored seed and correction, all columns at once
+    const int c = threadIdx.x;
+    const double y0 = y0_s[c], e = e_s[c];
+    dinv[c] = acc_s[c] ? fma(y0 * e, fma(e, 0.375, 0.5), y0) : 0.0;
     if (!spd && accepted) accepted[k0 + threadIdx.x] = (uint8_t)acc_s[threadIdx.x];
   }
   if (threadIdx.x == 0) {

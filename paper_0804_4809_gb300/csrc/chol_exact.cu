@@ -39,52 +39,8 @@ __global__ void rowscale_kernel(const double* A, int64_t lda, Dim nd, const int6
   }
 }
 
-// Rows [k0, n) of panel k0: below the diagonal block, L(i, P) solves
-// L(i, P) T' = A(i, P) by forward substitution against the factored block T
-// (1/T_cc = dinv[c], 0 for a rejected pivot; in place); every row of the
-// panel (diagonal block included) is then cut into residues with the row
-// scale E[i] and written to RL[j][i][k0 + c].  One warp per row, lane c for
-// column c; many CTAs (the FP64 pipe of each SM is narrow).
 constexpr int kPanelRows = 8;
-
-__global__ void __launch_bounds__(256) panel_solve_split_kernel(
-    double* A, int64_t lda, Dim nd, const int64_t* rdev, int64_t k0, int b, const double* dinv,
-    const int32_t* E, int n_mod, int beta, __nv_bfloat16* RL, int64_t rl_rows, int64_t rl_kpad) {
-  const int64_t n = eval_dim(nd, rdev);
-  if (k0 >= n) return;
-  const int bw = (int)((n - k0) < b ? (n - k0) : b);
-  // Ts[r][c] = T(r, c) / T(c, c) below the diagonal (see panel_solve_rows)
-  __shared__ double Ts[32][33];
-  __shared__ double dv[32];
-  if (threadIdx.x < 32) dv[threadIdx.x] = threadIdx.x < bw ? dinv[threadIdx.x] : 0.0;
-  __syncthreads();
-  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
-    const int r = e >> 5, c = e & 31;
-    Ts[r][c] = (r < bw && c < r) ? A[(k0 + r) * lda + (k0 + c)] * dv[c] : 0.0;
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int64_t i = k0 + (int64_t)blockIdx.x * kPanelRows + (threadIdx.x >> 5);
-  if (i >= n) return;
-  double l = 0.0;
-  if (i >= k0 + bw) {
-    double acc = lane < bw ? A[i * lda + k0 + lane] : 0.0;
-    for (int c = 0; c < bw; ++c) {
-      const double ac = __shfl_sync(0xffffffffu, acc, c);
-      if (lane > c) acc = fma(-ac, Ts[lane][c], acc);
-    }
-    l = acc * dv[lane];
-    if (lane < bw) A[i * lda + k0 + lane] = l;
-  } else if (lane < bw && lane <= i - k0) {
-    l = A[i * lda + k0 + lane];  // diagonal block: already the factor
-  }
-  if (lane < bw) {
-    const uint64_t bits = (uint64_t)__double_as_longlong(l);
-    const uint64_t a = crt::integerize(bits, E[i], beta);
-    crt::store_residues(a, (bits >> 63) != 0, n_mod, RL + (size_t)i * rl_kpad + (k0 + lane),
-                        (size_t)rl_rows * (size_t)rl_kpad);
-  }
-}
+constexpr int kPanelThreads = 256;
 
 // One launch per panel of the exact-slice factorisation: the panel's update
 // (the CRT reconstruction of the exact residue product of the factor's
@@ -118,52 +74,61 @@ __device__ __forceinline__ void st_release(int64_t* p, int64_t v) {
   asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Signed magnitude of the beta-bit integer that the residue planes hold for
-// the factor entry v of a row with scale E (sign in bit 63).
-__device__ __forceinline__ uint64_t scaled_int(double v, int E, int beta) {
+// The beta-bit integer that the residue planes hold for the factor entry v
+// of a row with scale E, in two's complement.
+__device__ __forceinline__ int64_t scaled_int(double v, int E, int beta) {
   const uint64_t bits = (uint64_t)__double_as_longlong(v);
-  return crt::integerize(bits, E, beta) | (bits & 0x8000000000000000ull);
+  const int64_t m = (int64_t)crt::integerize(bits, E, beta);
+  return (bits >> 63) ? -m : m;
 }
 
-// acc += a b for signed-magnitude integers below 2^62 (acc two's complement
-// over 128 bits: sums of up to 64 such products fit).
-__device__ __forceinline__ void mac128(uint64_t& lo, int64_t& hi, uint64_t a, uint64_t b) {
-  const uint64_t ma = a & 0x7FFFFFFFFFFFFFFFull, mb = b & 0x7FFFFFFFFFFFFFFFull;
-  const uint64_t plo = ma * mb, phi = __umul64hi(ma, mb);
-  if ((a ^ b) >> 63) {
-    const uint64_t r = lo - plo;
-    hi -= (int64_t)(phi + (r > lo ? 1u : 0u));
-    lo = r;
-  } else {
-    const uint64_t r = lo + plo;
-    hi += (int64_t)(phi + (r < plo ? 1u : 0u));
-    lo = r;
-  }
+// (hi:lo) += a b over 128 bits, two's complement.  |a|, |b| < 2^kMaxBeta, so
+// a sum of up to kMaxLast products stays below 2^126.  The product is
+// independent of the accumulator; only the carry chain is serial.
+constexpr int kMaxBeta = 60;
+__device__ __forceinline__ void mac128(uint64_t& lo, int64_t& hi, int64_t a, int64_t b) {
+  const uint64_t plo = (uint64_t)a * (uint64_t)b;
+  const int64_t phi = __mul64hi(a, b);
+  asm("add.cc.u64 %0, %0, %2;\n\taddc.s64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(plo), "l"(phi));
+}
+
+// Four residues (bytes) per register.
+constexpr int kRvWords = crt::kMaxMod / 4;
+static_assert(crt::kMaxMod % 4 == 0, "residue packing");
+
+// The residues of the bulk update (columns 0 .. kb) at block entry (ir, jc),
+// every load in flight at once; issued before the exact sum over the last
+// columns so that their latency hides behind it.
+__device__ __forceinline__ void load_residues(const PanelExactParams& p, int64_t ir, int64_t jc,
+                                              uint32_t (&rv)[kRvWords]) {
+  const size_t plane = (size_t)p.Mpad * (size_t)p.Npad;
+  const uint8_t* r = p.R + ir * p.Npad + jc;
+  uint32_t b[crt::kMaxMod];
+#pragma unroll
+  for (int m = 0; m < crt::kMaxMod; ++m) b[m] = (p.has_bulk && m < p.n_upd) ? r[(size_t)m * plane] : 0u;
+#pragma unroll
+  for (int w = 0; w < kRvWords; ++w)
+    rv[w] = b[4 * w] | (b[4 * w + 1] << 8) | (b[4 * w + 2] << 16) | (b[4 * w + 3] << 24);
 }
 
 // A(k0 + ir, k0 + jc) - X(ir, jc), the difference rounded once, where X is the
-// exact update: the CRT value of the residues in R (columns 0 .. kb of the
+// exact update: the CRT value of the residues rv (columns 0 .. kb of the
 // factor, when has_bulk) plus (hi:lo), the exact sum over columns kb .. k0
 // formed by the caller from the factor's scaled integers.
 __device__ __forceinline__ double apply_update(const PanelExactParams& p,
                                                const crt::CrtShared& sh, int shift,
                                                float inv_ptop, int64_t ir, int64_t jc,
-                                               double a_old, uint64_t lo, int64_t hi) {
+                                               double a_old, const uint32_t (&rv)[kRvWords],
+                                               uint64_t lo, int64_t hi) {
   uint32_t Y[crt::kLimbs] = {0, 0, 0, 0, 0};
   if (p.has_bulk) {
-    const size_t plane = (size_t)p.Mpad * (size_t)p.Npad;
-    const uint8_t* r = p.R + ir * p.Npad + jc;
-    // every residue load in flight at once: one memory latency per output
-    uint32_t rv[crt::kMaxMod];
-#pragma unroll
-    for (int m = 0; m < crt::kMaxMod; ++m) rv[m] = m < p.n_upd ? r[(size_t)m * plane] : 0u;
     uint64_t acc[crt::kLimbs];
 #pragma unroll
     for (int l = 0; l < crt::kLimbs; ++l) acc[l] = 0;
 #pragma unroll
     for (int m = 0; m < crt::kMaxMod; ++m) {
       if (m >= p.n_upd) break;
-      const uint32_t t = sh.tab[m][rv[m]];
+      const uint32_t t = sh.tab[m][(rv[m >> 2] >> (8 * (m & 3))) & 0xFFu];
 #pragma unroll
       for (int l = 0; l < crt::kLimbs; ++l) acc[l] += (uint64_t)t * sh.Mj[m][l];
     }
@@ -199,7 +164,7 @@ __device__ __forceinline__ void tri_index(int o, int& i, int& j) {
   j = o - i * (i + 1) / 2;
 }
 
-__global__ void __launch_bounds__(256, 4) chol_panel_exact_kernel(PanelExactParams p) {
+__global__ void __launch_bounds__(kPanelThreads, 4) chol_panel_exact_kernel(PanelExactParams p) {
   const int64_t n = eval_dim(p.nd, p.rdev);
   const int64_t k0 = p.k0;
   if (k0 >= n) return;
@@ -211,41 +176,75 @@ __global__ void __launch_bounds__(256, 4) chol_panel_exact_kernel(PanelExactPara
   __shared__ crt::CrtShared sh;
   __shared__ double Ts[32][33];
   __shared__ double dv[32];
-  __shared__ uint64_t Lt[kMaxLast][32];  // Lt[k][j]: scaled integer of L(k0 + j, kb + k)
+  __shared__ int64_t Lt[kMaxLast][32];  // Lt[k][j]: scaled integer of L(k0 + j, kb + k)
   __shared__ int go;
   double* A = p.A;
   const int64_t lda = p.lda;
   int shift = 0;
   float inv_ptop = 0.f;
   if (p.has_update) {
+    // the block's rows over the last columns kb .. k0 as scaled integers
+    // (Lt[k][j] for L(k0 + j, kb + k)) and the CRT tables; every global load
+    // is issued before the first is used
+    constexpr int kLtPer = kMaxLast * 32 / kPanelThreads;
+    double lv[kLtPer];
+    int le[kLtPer];
+#pragma unroll
+    for (int q = 0; q < kLtPer; ++q) {
+      const int e = threadIdx.x + kPanelThreads * q, k = e >> 5, j = e & 31;
+      const bool in = k < p.k_last && j < bw;
+      lv[q] = in ? A[(k0 + j) * lda + p.kb + k] : 0.0;
+      le[q] = in ? p.E[k0 + j] : 0;
+    }
     if (p.has_bulk) {
       const crt::Consts& c = p.consts[p.n_upd];
+      constexpr int kTabPer = (crt::kMaxMod * 32 + kPanelThreads - 1) / kPanelThreads;
       const uint32_t* src = reinterpret_cast<const uint32_t*>(&c.tab[0][0]);
       uint32_t* dst = reinterpret_cast<uint32_t*>(&sh.tab[0][0]);
-      for (int e = threadIdx.x; e < p.n_upd * 32; e += blockDim.x) dst[e] = src[e];
-      for (int e = threadIdx.x; e < p.n_upd * crt::kLimbs; e += blockDim.x)
-        sh.Mj[e / crt::kLimbs][e % crt::kLimbs] = c.Mj[e / crt::kLimbs][e % crt::kLimbs];
+      uint32_t tv[kTabPer];
+#pragma unroll
+      for (int q = 0; q < kTabPer; ++q) {
+        const int e = threadIdx.x + kPanelThreads * q;
+        tv[q] = e < p.n_upd * 32 ? src[e] : 0u;
+      }
+      const int em = threadIdx.x;
+      const uint32_t mv = em < p.n_upd * crt::kLimbs ? c.Mj[em / crt::kLimbs][em % crt::kLimbs] : 0u;
+      uint32_t pv = 0, hv = 0;
       if (threadIdx.x < crt::kLimbs) {
-        sh.P[threadIdx.x] = c.P[threadIdx.x];
-        sh.halfP[threadIdx.x] = c.halfP[threadIdx.x];
+        pv = c.P[threadIdx.x];
+        hv = c.halfP[threadIdx.x];
       }
       shift = c.shift;
       inv_ptop = c.inv_ptop;
+#pragma unroll
+      for (int q = 0; q < kTabPer; ++q) {
+        const int e = threadIdx.x + kPanelThreads * q;
+        if (e < p.n_upd * 32) dst[e] = tv[q];
+      }
+      if (em < p.n_upd * crt::kLimbs) sh.Mj[em / crt::kLimbs][em % crt::kLimbs] = mv;
+      if (threadIdx.x < crt::kLimbs) {
+        sh.P[threadIdx.x] = pv;
+        sh.halfP[threadIdx.x] = hv;
+      }
     }
-    // the block's rows over the last columns kb .. k0, as scaled integers
-    for (int e = threadIdx.x; e < p.k_last * 32; e += blockDim.x) {
-      const int k = e >> 5, j = e & 31;
-      Lt[k][j] = j < bw ? scaled_int(A[(k0 + j) * lda + p.kb + k], p.E[k0 + j], p.beta) : 0ull;
+#pragma unroll
+    for (int q = 0; q < kLtPer; ++q) {
+      const int e = threadIdx.x + kPanelThreads * q, k = e >> 5, j = e & 31;
+      if (k < kMaxLast) Lt[k][j] = scaled_int(lv[q], le[q], p.beta);
     }
     __syncthreads();
   }
   // the exact update of block entry (i, j): CRT part + sum over the last columns
   auto block_update = [&](int i, int j) {
+    double* a = A + (k0 + i) * lda + (k0 + j);
+    const double a_old = *a;
+    uint32_t rv[kRvWords];
+    load_residues(p, i, j, rv);
     uint64_t lo = 0;
     int64_t hi = 0;
+#pragma unroll 4
     for (int k = 0; k < p.k_last; ++k) mac128(lo, hi, Lt[k][i], Lt[k][j]);
-    double* a = A + (k0 + i) * lda + (k0 + j);
-    *a = apply_update(p, sh, shift, inv_ptop, i, j, *a, lo, hi);
+    *a = apply_update(p, sh, shift, inv_ptop, i, j, a_old, rv, lo, hi);
   };
   const int tri = bw * (bw + 1) / 2;
   if (helper) {
@@ -307,25 +306,29 @@ __global__ void __launch_bounds__(256, 4) chol_panel_exact_kernel(PanelExactPara
   const bool row_ok = i < n;
   double acc = 0.0;
   if (row_ok && p.has_update) {
-    // this row's scaled integers over the last columns, lane k holding k,
-    // k + 32, k + 64; lane c sums against column c of the block
-    uint64_t ai[kMaxLast / 32];
+    // this row's scaled integers over the last columns, lane k holding k and
+    // k + 32; lane c sums against column c of the block
+    const double a_old = lane < bw ? A[i * lda + k0 + lane] : 0.0;
+    uint32_t rv[kRvWords];
+    load_residues(p, i - k0, lane < bw ? lane : 0, rv);
+    int64_t ai[kMaxLast / 32];
 #pragma unroll
     for (int q = 0; q < kMaxLast / 32; ++q) {
       const int k = lane + 32 * q;
-      ai[q] = k < p.k_last ? scaled_int(A[i * lda + p.kb + k], p.E[i], p.beta) : 0ull;
+      ai[q] = k < p.k_last ? scaled_int(A[i * lda + p.kb + k], p.E[i], p.beta) : 0;
     }
     uint64_t lo = 0;
     int64_t hi = 0;
 #pragma unroll
     for (int q = 0; q < kMaxLast / 32; ++q) {
       const int kend = p.k_last - 32 * q < 32 ? p.k_last - 32 * q : 32;
+#pragma unroll 4
       for (int kk = 0; kk < kend; ++kk) {
-        const uint64_t a = __shfl_sync(0xffffffffu, ai[q], kk);
+        const int64_t a = __shfl_sync(0xffffffffu, ai[q], kk);
         mac128(lo, hi, a, Lt[32 * q + kk][lane]);
       }
     }
-    if (lane < bw) acc = apply_update(p, sh, shift, inv_ptop, i - k0, lane, A[i * lda + k0 + lane], lo, hi);
+    if (lane < bw) acc = apply_update(p, sh, shift, inv_ptop, i - k0, lane, a_old, rv, lo, hi);
   } else if (row_ok && lane < bw) {
     acc = A[i * lda + k0 + lane];
   }
@@ -348,12 +351,12 @@ __global__ void __launch_bounds__(256, 4) chol_panel_exact_kernel(PanelExactPara
   // L2 loads (the block was written by another CTA in this launch), all in
   // one round trip, scaled in shared memory afterwards
   if (threadIdx.x < 32) dv[threadIdx.x] = threadIdx.x < bw ? __ldcg(p.dinv + threadIdx.x) : 0.0;
-  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+  for (int e = threadIdx.x; e < 32 * 32; e += kPanelThreads) {
     const int r = e >> 5, c = e & 31;
     Ts[r][c] = (r < bw && c < r) ? __ldcg(A + (k0 + r) * lda + (k0 + c)) : 0.0;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) Ts[e >> 5][e & 31] *= dv[e & 31];
+  for (int e = threadIdx.x; e < 32 * 32; e += kPanelThreads) Ts[e >> 5][e & 31] *= dv[e & 31];
   __syncthreads();
   if (!row_ok) return;
   for (int c = 0; c < bw; ++c) {
@@ -382,11 +385,24 @@ int64_t chol_panel_exact_ctas(int64_t nmax, int64_t k0, int b) {
 
 cudaError_t launch_chol_panel_exact(const PanelExactParams& p, cudaStream_t s) {
   if (p.b > 32 || p.b < 1 || (p.has_bulk && (!p.consts || !p.R))) return cudaErrorInvalidValue;
-  if (p.k_last < 0 || p.k_last > kMaxLast || (p.has_update && p.kb + p.k_last != p.k0))
+  if (p.k_last < 0 || p.k_last > kMaxLast || (p.has_update && p.kb + p.k_last != p.k0) ||
+      p.beta < 1 || p.beta > kMaxBeta)
     return cudaErrorInvalidValue;
   const int64_t ctas = chol_panel_exact_ctas(p.nd.max, p.k0, p.b);
   if (p.helpers < 0 || p.helpers >= ctas) return cudaErrorInvalidValue;
-  chol_panel_exact_kernel<<<(unsigned)ctas, 256, 0, s>>>(p);
+  // The panel kernel shares its SMs with the look-ahead residue product on
+  // another stream; with the largest shared-memory carveout an SM running
+  // panel CTAs still takes a product CTA (the carveout of a busy SM cannot
+  // change, so a small one would keep the product off those SMs).
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(chol_panel_exact_kernel,
+                                         cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  chol_panel_exact_kernel<<<(unsigned)ctas, kPanelThreads, 0, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -396,16 +412,5 @@ cudaError_t launch_rowscale(const double* A, int64_t lda, Dim nd, const int64_t*
   return cudaGetLastError();
 }
 
-cudaError_t launch_panel_solve_split(double* A, int64_t lda, Dim nd, const int64_t* rdev,
-                                     int64_t k0, int b, const double* dinv, const int32_t* E,
-                                     int n_mod, int beta, void* RL, int64_t rl_rows,
-                                     int64_t rl_kpad, cudaStream_t s) {
-  if (b > 32) return cudaErrorInvalidValue;
-  const int64_t rows = nd.max - k0;
-  if (rows <= 0) return cudaSuccess;
-  panel_solve_split_kernel<<<(unsigned)((rows + kPanelRows - 1) / kPanelRows), 256, 0, s>>>(
-      A, lda, nd, rdev, k0, b, dinv, E, n_mod, beta, (__nv_bfloat16*)RL, rl_rows, rl_kpad);
-  return cudaGetLastError();
-}
 
 }  // namespace cpinv

@@ -851,6 +851,11 @@ cudaError_t launch_mma(const CUtensorMap& ta, const CUtensorMap& tb, const MmaPa
     cudaError_t e = cudaFuncSetAttribute(crt_mma_kernel<BN, STAGES, S3>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    // largest carveout: room beside this CTA for kernels on other streams
+    e = cudaFuncSetAttribute(crt_mma_kernel<BN, STAGES, S3>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
     attr = true;
   }
   const int groups = (mp.n_mod + mp.mods_per_cta - 1) / mp.mods_per_cta;

@@ -96,11 +96,6 @@ cudaError_t crt_reconstruct(const uint8_t* R, int64_t Mpad, int64_t Npad, Dim M,
 // chol_exact.cu
 cudaError_t launch_rowscale(const double* A, int64_t lda, Dim nd, const int64_t* rdev,
                             int64_t rows_max, int32_t* E, cudaStream_t s);
-cudaError_t launch_panel_solve_split(double* A, int64_t lda, Dim nd, const int64_t* rdev,
-                                     int64_t k0, int b, const double* dinv, const int32_t* E,
-                                     int n_mod, int beta, void* RL, int64_t rl_rows,
-                                     int64_t rl_kpad, cudaStream_t s);
-
 // One fused launch per panel of the exact-slice factorisation (update
 // reconstruction, diagonal block, rows below, residue split).
 struct PanelExactParams {
