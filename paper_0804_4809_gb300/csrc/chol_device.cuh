@@ -42,13 +42,42 @@ __device__ __forceinline__ double rsqrt_apply(double x, double y0, double e) {
   return fma(s * e, fma(e, 0.375, 0.5), s);
 }
 
-// Named barriers 1 and 2 (0 is __syncthreads): producer / consumer hand-off
-// of one column between the four warps of the diagonal-block kernel.
+// Named barrier 3 (0 is __syncthreads) joins the four warps of the
+// diagonal-block factorisation inside a larger CTA.
 __device__ __forceinline__ void bar_sync(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
-__device__ __forceinline__ void bar_arrive(int id, int count) {
-  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+
+// Column hand-off: one shared-memory barrier per column, completed by the 32
+// arrivals of the owner warp's lanes (each after writing its entry; arrive
+// has release semantics) and waited on by every other warp on its own
+// (acquire), so a warp still issuing its updates never holds back the next
+// pivot.  The wait is bounded: false after kColSpinLimit polls.
+constexpr uint32_t kColSpinLimit = 1u << 22;
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void col_init(uint64_t* mb, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mb)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void col_inval(uint64_t* mb) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(mb)) : "memory");
+}
+__device__ __forceinline__ void col_publish(uint64_t* mb) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mb)) : "memory");
+}
+__device__ __forceinline__ bool col_wait(uint64_t* mb) {
+  for (uint32_t it = 0; it < kColSpinLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(mb))
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
 }
 
 constexpr int kDiagWarps = 4;
@@ -57,31 +86,37 @@ constexpr int kDiagThreads = 32 * kDiagWarps;
 // Factorisation of the diagonal block of panel k0 (b <= 32) by one CTA of
 // four warps.  Lane i holds row i; warp w holds the columns j = w (mod 4).
 // Column c is finished by its owner warp (pivot test, square root, scaling)
-// and handed to the others through a triple-buffered shared column and a
-// named barrier: the owner arrives, the others wait.  Look-ahead: the owner
-// of column c+1 applies the update of column c to that column first and
-// finishes it before its other updates, so the hand-off of every column
-// waits for one update and one pivot only.  The columns are processed in
-// groups of four (one per warp); after each group every warp's registers
-// shift by one column, so register indices stay compile-time constants in a
-// loop that is not unrolled (a fully unrolled factorisation is long enough
-// to stall on instruction fetch).  The sequence of operations on every entry
-// (updates in column order, the pivot, the scaling) is that of the plain
-// column-by-column algorithm.
+// and handed to the others through its own shared column and barrier.
+// Look-ahead: the owner of column c+1 applies the update of column c to that
+// column first and finishes it before its other updates, so the hand-off of
+// every column waits for one update and one pivot only.  (FP64 instructions
+// take about 65 cycles of an SM sub-partition's FP64 pipe each, whatever the
+// active lanes, so the chain's cost is its count of FP64 instructions.)  A
+// warp's registers shift by one column each time it finishes one, so its
+// next column is always a[0] and register indices stay compile-time
+// constants in a loop over columns that is not unrolled: a long unrolled
+// body misses the instruction cache each time the loop jumps back.  The
+// sequence of operations on every entry (updates in column order, the
+// pivot, the scaling) is that of the plain column-by-column algorithm.
 __device__ __forceinline__ void diag_chol_block(double* A, int64_t lda, Dim nd, int64_t k0, int b,
                                                 DevState* st, const int64_t* rdev,
                                                 uint8_t* accepted, double* dinv, int spd) {
   const int64_t n = eval_dim(nd, rdev);
   if (k0 >= n) return;
   const int bw = (int)((n - k0) < b ? (n - k0) : b);
-  __shared__ double colbuf[3][32];
+  __shared__ double colbuf[32][32];
+  __shared__ __align__(8) uint64_t colbar[32];
   __shared__ double y0_s[32], e_s[32];
   __shared__ int acc_s[32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x < 32) col_init(&colbar[threadIdx.x], 32);
+  bar_sync(3, kDiagThreads);  // the barriers are initialised for all four warps
   // the pivot test d > tol on the bit patterns (tol >= 0: a negative d, -0
   // and NaN compare below or are excluded; +inf passes as it does in FP64)
   const long long tolbits = __double_as_longlong(spd ? 0.0 : st->tol);
-  // a[q]: this lane's entry of column 4 (t + q) + w during group t
+  // a[q]: this lane's entry of column jn + 4q, jn = this warp's next column
+  // to finish (jn = w + 4 * columns finished)
+  int jn = w;
   double a[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
@@ -101,7 +136,7 @@ __device__ __forceinline__ void diag_chol_block(double* A, int64_t lda, Dim nd, 
     const double e = rsqrt_e(d, y0);
     const double lv = rsqrt_apply(acol, y0, e);  // lane c: d / sqrt(d)
     const double l = (ok && lane >= c) ? lv : 0.0;
-    colbuf[c % 3][lane] = l;
+    colbuf[c][lane] = l;
     if (lane == c) {
       acc_s[c] = ok;
       y0_s[c] = y0;
@@ -109,50 +144,45 @@ __device__ __forceinline__ void diag_chol_block(double* A, int64_t lda, Dim nd, 
     }
     return l;
   };
-  if (w == 0) {
-    a[0] = pivot(0, a[0]);
-    __syncwarp();
-    __threadfence_block();
-    bar_arrive(1, kDiagThreads);
-  }
-#pragma unroll 1
-  for (int t = 0; kDiagWarps * t < bw; ++t) {
-#pragma unroll
-    for (int u = 0; u < kDiagWarps; ++u) {
-      const int c = kDiagWarps * t + u;
-      if (c >= bw) break;
-      const int buf = c % 3;
-      if (w != u) bar_sync(1 + (c & 1), kDiagThreads);
-      else __syncwarp();
-      const double li = colbuf[buf][lane];
-      const int nxt = c + 1;
-      // the owner of column c+1 is warp (u+1) mod 4; the column is its a[0]
-      // within this group, its a[1] when it opens the next group
-      const int qn = (u + 1 < kDiagWarps) ? 0 : 1;
-      const bool ahead = nxt < bw && w == ((u + 1) & (kDiagWarps - 1));
-      if (ahead) {
-        if (lane >= nxt) a[qn] = fma(-li, colbuf[buf][nxt], a[qn]);
-        a[qn] = pivot(nxt, a[qn]);
-        __syncwarp();
-        __threadfence_block();
-        bar_arrive(1 + (nxt & 1), kDiagThreads);
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        if (q == 0 && w <= u) continue;  // column 4t + w is not after c
-        if (ahead && q == qn) continue;
-        const int j = kDiagWarps * (t + q) + w;
-        if (j < bw && lane >= j) a[q] = fma(-li, colbuf[buf][j], a[q]);
-      }
-    }
-    // column 4t + w is final: store it, then shift the registers by one column
-    const int j0 = kDiagWarps * t + w;
-    if (j0 < bw && lane < bw && lane >= j0) A[(k0 + lane) * lda + (k0 + j0)] = a[0];
+  // column jn is final in a[0]: store it and shift the registers by one column
+  auto retire = [&]() {
+    if (jn < bw && lane < bw && lane >= jn) A[(k0 + lane) * lda + (k0 + jn)] = a[0];
 #pragma unroll
     for (int q = 0; q < 7; ++q) a[q] = a[q + 1];
     a[7] = 0.0;
+    jn += kDiagWarps;
+  };
+  bool timed_out = false;
+  if (w == 0) {
+    a[0] = pivot(0, a[0]);
+    col_publish(&colbar[0]);
+    retire();
   }
+  // One iteration per column, the same code for every column (a loop body
+  // small enough to stay in the instruction cache across iterations).
+#pragma unroll 1
+  for (int c = 0; c < bw; ++c) {
+    if (w != (c & (kDiagWarps - 1))) timed_out |= !col_wait(&colbar[c]);
+    else __syncwarp();
+    const double li = colbuf[c][lane];
+    const int nxt = c + 1;
+    if (nxt < bw && w == (nxt & (kDiagWarps - 1))) {
+      // this warp owns column c+1 (its a[0]): last update, pivot, hand-off
+      if (lane >= nxt) a[0] = fma(-li, colbuf[c][nxt], a[0]);
+      a[0] = pivot(nxt, a[0]);
+      col_publish(&colbar[nxt]);
+      retire();
+    }
+    // the update of column c on this warp's remaining columns
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int j = jn + kDiagWarps * q;
+      if (j < bw && lane >= j) a[q] = fma(-li, colbuf[c][j], a[q]);
+    }
+  }
+  if (timed_out && lane == 0) atomicOr(&st->status, ST_TIMEOUT);
   bar_sync(3, kDiagThreads);  // the four warps only (the caller's CTA may be larger)
+  if (threadIdx.x < 32) col_inval(&colbar[threadIdx.x]);
   if (threadIdx.x < bw) {
     // 1/T(c, c) from the stored seed and correction, all columns at once
     const int c = threadIdx.x;

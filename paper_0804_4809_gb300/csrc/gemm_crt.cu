@@ -737,6 +737,167 @@ __global__ void __launch_bounds__(256, 2) reconstruct_kernel(ReconParams p, int 
   }
 }
 
+// Reconstruction when the modulus product P fits in 128 bits (n_mod <= 19:
+// the FP64-accurate products of the chain).  Each term t_j (P / p_j) then
+// has four 32-bit limbs, and the reduction mod P, the centring and the
+// rounding work on 64-bit words.  Four adjacent columns per thread (one
+// 32-bit load per modulus), eight rows x 128 columns per block.
+constexpr int kRec128MaxMod = 19;
+constexpr int kRec128Rows = 8, kRec128Cols = 128;
+struct __align__(16) Rec128Shared {
+  uint32_t Mj[crt::kMaxMod][4];  // P / p_j (< 2^128)
+  uint8_t tab[crt::kMaxMod][128];
+};
+
+// Correctly rounded (hi:lo) * 2^scale with sign, by integer operations.
+__device__ __forceinline__ double u128_to_double(bool neg, uint64_t hi, uint64_t lo, int scale) {
+  if ((hi | lo) == 0) return neg ? -0.0 : 0.0;
+  int top;
+  uint64_t t;  // the 64 bits from the leading one down
+  bool sticky;
+  if (hi) {
+    const int lz = __clzll((long long)hi);
+    top = 127 - lz;
+    t = lz ? (hi << lz) | (lo >> (64 - lz)) : hi;
+    sticky = lz ? (lo << lz) != 0 : lo != 0;
+  } else {
+    const int lz = __clzll((long long)lo);
+    top = 63 - lz;
+    t = lo << lz;
+    sticky = false;
+  }
+  uint64_t mant = t >> 11;
+  const uint64_t rem = t & 0x7FFull;
+  if (rem > 0x400ull || (rem == 0x400ull && (sticky || (mant & 1ull)))) ++mant;
+  int e = top;  // value = mant * 2^(top - 52)
+  if (mant >> 53) {
+    mant >>= 1;
+    ++e;
+  }
+  const int biased = e + scale + 1023;
+  if (biased <= 0 || biased >= 2047) {
+    const double d = ldexp((double)mant, e - 52 + scale);
+    return neg ? -d : d;
+  }
+  return __longlong_as_double(
+      (long long)(((uint64_t)neg << 63) | ((uint64_t)biased << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
+
+// The low 64 bits of (s2:s1:s0) >> sh, 0 <= sh < 192.
+__device__ __forceinline__ uint64_t shr192(uint64_t s2, uint64_t s1, uint64_t s0, int sh) {
+  if (sh >= 128) return s2 >> (sh - 128);
+  if (sh >= 64) return sh == 64 ? s1 : (s1 >> (sh - 64)) | (s2 << (128 - sh));
+  return sh == 0 ? s0 : (s0 >> sh) | (s1 << (64 - sh));
+}
+
+__global__ void __launch_bounds__(256) reconstruct128_kernel(ReconParams p, int n_mod) {
+  const crt::Consts& c = g_crt_consts[n_mod];
+  __shared__ Rec128Shared sh;
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&c.tab[0][0]);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&sh.tab[0][0]);
+    for (int e = threadIdx.x; e < n_mod * 32; e += blockDim.x) dst[e] = src[e];
+    for (int e = threadIdx.x; e < n_mod * 4; e += blockDim.x) sh.Mj[e >> 2][e & 3] = c.Mj[e >> 2][e & 3];
+  }
+  __syncthreads();
+  const uint64_t P0 = c.P[0] | ((uint64_t)c.P[1] << 32), P1 = c.P[2] | ((uint64_t)c.P[3] << 32);
+  const uint64_t H0 = c.halfP[0] | ((uint64_t)c.halfP[1] << 32),
+                 H1 = c.halfP[2] | ((uint64_t)c.halfP[3] << 32);
+  // quotient estimate floor(S / P) from the 24 leading bits of P: S >> qs
+  // is below n 2^24 < 2^29, so FP32 holds it with a relative error of 2^-24
+  const int pbits = P1 ? 128 - __clzll((long long)P1) : 64 - __clzll((long long)P0);
+  const int qs = pbits > 24 ? pbits - 24 : 0;
+  const float inv_ptop = 1.0f / (float)(uint32_t)shr192(0, P1, P0, qs);
+
+  const int64_t M = eval_dim(p.M, p.rdev), N = eval_dim(p.N, p.rdev);
+  const int64_t i = (int64_t)blockIdx.y * kRec128Rows + (threadIdx.x >> 5);
+  const int64_t j0 = (int64_t)blockIdx.x * kRec128Cols + 4 * (threadIdx.x & 31);
+  if (i >= M || j0 >= N || (p.lower && j0 > i)) return;
+  const size_t plane = (size_t)p.Mpad * (size_t)p.Npad;
+  const uint32_t* r = reinterpret_cast<const uint32_t*>(p.R + i * p.Npad + j0);
+  uint64_t acc[4][4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+#pragma unroll
+    for (int l = 0; l < 4; ++l) acc[e][l] = 0;
+  // residues in groups of seven loads in flight, then their sums
+#pragma unroll
+  for (int m0 = 0; m0 < 21; m0 += 7) {
+    uint32_t rv[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) rv[q] = (m0 + q) < n_mod ? r[(size_t)(m0 + q) * (plane / 4)] : 0u;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      const int m = m0 + q;
+      if (m < n_mod) {
+        const uint4 mj = *reinterpret_cast<const uint4*>(&sh.Mj[m][0]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const uint64_t t = sh.tab[m][(rv[q] >> (8 * e)) & 0xFFu];
+          acc[e][0] += t * mj.x;
+          acc[e][1] += t * mj.y;
+          acc[e][2] += t * mj.z;
+          acc[e][3] += t * mj.w;
+        }
+      }
+    }
+  }
+  const int sa = p.EA[i] - 1022 - p.betaA;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int64_t j = j0 + e;
+    if (j >= N || (p.lower && j > i)) continue;
+    // S = sum_j t_j P/p_j (< n P < 2^131) as (s2:s1:s0)
+    uint32_t Sl[5];
+    uint64_t carry = 0;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      const uint64_t v = acc[e][l] + carry;
+      Sl[l] = (uint32_t)v;
+      carry = v >> 32;
+    }
+    Sl[4] = (uint32_t)carry;
+    const uint64_t s0 = Sl[0] | ((uint64_t)Sl[1] << 32), s1 = Sl[2] | ((uint64_t)Sl[3] << 32);
+    const uint64_t s2 = Sl[4];
+    // X = S - q P, then into [0, P) (the estimate is off by at most one)
+    const uint64_t q = (uint64_t)floorf((float)(uint32_t)shr192(s2, s1, s0, qs) * inv_ptop);
+    const uint64_t qp0 = q * P0;
+    const uint64_t c0 = __umul64hi(q, P0);
+    const uint64_t qp1 = q * P1 + c0;
+    const uint64_t qp2 = __umul64hi(q, P1) + (qp1 < c0 ? 1u : 0u);
+    uint64_t x0 = s0 - qp0;
+    uint64_t b = s0 < qp0;
+    uint64_t x1 = s1 - qp1 - b;
+    b = (s1 < qp1) || (s1 == qp1 && b);
+    int64_t x2 = (int64_t)(s2 - qp2 - b);
+    if (x2 < 0) {  // X += P
+      x0 += P0;
+      const uint64_t cc = x0 < P0;
+      const uint64_t t1 = x1 + P1;
+      const uint64_t cc1 = t1 < x1;
+      x1 = t1 + cc;
+      x2 += (int64_t)(cc1 + (x1 < cc ? 1u : 0u));
+    } else if (x2 > 0 || x1 > P1 || (x1 == P1 && x0 >= P0)) {  // X -= P
+      const uint64_t bb = x0 < P0;
+      x0 -= P0;
+      const uint64_t t1 = x1 - P1;
+      x1 = t1 - bb;
+    }
+    // centre into (-P/2, P/2]
+    const bool neg = x1 > H1 || (x1 == H1 && x0 > H0);
+    uint64_t m0 = x0, m1 = x1;
+    if (neg) {
+      m0 = P0 - x0;
+      m1 = P1 - x1 - (P0 < x0 ? 1u : 0u);
+    }
+    double v = u128_to_double(neg, m1, m0, sa + p.EB[j] - 1022 - p.betaB);
+    double* cp = p.C + i * p.ldc + j;
+    if (p.alpha != 1.0) v *= p.alpha;
+    if (p.beta != 0.0) v = fma(p.beta, *cp, v);
+    *cp = v;
+  }
+}
+
 // The same reconstruction for small outputs (the panel updates of the
 // factorisation): four lanes share one output, each summing every fourth
 // modulus, and the partial sums meet by shuffles, so an output's latency
@@ -1018,6 +1179,10 @@ cudaError_t crt_reconstruct(const uint8_t* R, int64_t Mpad, int64_t Npad, Dim M,
   return timer->run(KT_RECON, s, [&] {
     if (small)
       reconstruct_split_kernel<<<grid1d(M.max * N.max * kRecLanes, 256), 256, 0, s>>>(rp, n_mod);
+    else if (n_mod <= kRec128MaxMod)
+      reconstruct128_kernel<<<dim3((unsigned)((N.max + kRec128Cols - 1) / kRec128Cols),
+                                   (unsigned)((M.max + kRec128Rows - 1) / kRec128Rows)),
+                              256, 0, s>>>(rp, n_mod);
     else
       reconstruct_kernel<<<grid1d(M.max * ((N.max + kRecW - 1) / kRecW), 256), 256, 0, s>>>(
           rp, n_mod);

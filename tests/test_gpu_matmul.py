@@ -125,3 +125,38 @@ def test_split_bf16x3_error_bound(cp, ta, tb, M, N, K):
     assert np.all(np.abs(C - X) <= 2.0 ** -13 * bound)
     # and it is not secretly an FP64 product: the error is far above FP64's
     assert np.max(np.abs(C - X) / bound) > 1e-10
+
+
+@pytest.mark.parametrize("ta,tb", [(False, False), (True, True)])
+@pytest.mark.parametrize("M,N,K", [(300, 260, 1000), (257, 513, 2048), (1030, 70, 333)])
+def test_exact_slice_53bit_outputs_correctly_rounded(cp, ta, tb, M, N, K):
+    """53-bit operands (the chain's products: fewer moduli, the 128-bit
+    reconstruction).  Integer entries below 2^40 times a power of two per
+    row are exact in 53-bit fixed point, so the product is exact before its
+    one rounding."""
+    g = np.random.default_rng(M + 3 * N + 7 * K)
+    opA = g.integers(-2 ** 40, 2 ** 40, (M, K)).astype(np.float64) * np.exp2(g.integers(-30, 30, (M, 1)))
+    opB = g.integers(-2 ** 40, 2 ** 40, (K, N)).astype(np.float64) * np.exp2(g.integers(-30, 30, (1, N)))
+    A = opA.T.copy() if ta else opA
+    B = opB.T.copy() if tb else opB
+    C = _run(cp, A, B, ta, tb, "exact", bits=53)
+    X = _exact(opA, opB)
+    assert np.array_equal(C, X), float(np.max(np.abs(C - X) / np.maximum(np.abs(X), 1e-300)))
+
+
+def test_exact_slice_53bit_symmetric_and_alpha_beta(cp):
+    import torch
+    g = np.random.default_rng(77)
+    G = g.integers(-2 ** 30, 2 ** 30, (700, 400)).astype(np.float64) * np.exp2(g.integers(-8, 8, (1, 400)))
+    Gd = to_dev(G)
+    C = cp.matmul(Gd, Gd, True, False, mode="exact", bits=53)
+    torch.cuda.synchronize()
+    X = _exact(G.T, G)
+    assert np.array_equal(C.cpu().numpy(), X)
+    A = g.standard_normal((500, 300))
+    B = g.standard_normal((300, 280))
+    C0 = g.standard_normal((500, 280))
+    C = _run(cp, A, B, False, False, "exact", bits=53, alpha=-0.5, beta=2.0, C=C0)
+    Xc = -0.5 * _exact(A, B) + 2.0 * C0
+    bound = 0.5 * (np.abs(A) @ np.abs(B)) + 2.0 * np.abs(C0)
+    assert np.all(np.abs(C - Xc) <= 8 * U * bound)
