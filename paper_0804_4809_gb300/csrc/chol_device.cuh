@@ -35,7 +35,9 @@ __device__ __forceinline__ double rsqrt_seed(uint64_t bits) {
 // accurate to O(e^3) ~ 2^-66.  e is formed as 1 - (d y0) y0, which stays in
 // range for subnormal and huge d.  The pivot's column is scaled by the same
 // series, x / sqrt(d) = s + (s e)(1/2 + 3e/8) with s = x y0, so the product
-// x y0 runs beside the correction instead of after it.
+// x y0 runs beside the correction instead of after it.  (Squaring the seed
+// exactly in the integer unit saves one FP64 instruction but measured
+// slower: the range test and the integer chain cost more than it saves.)
 __device__ __forceinline__ double rsqrt_e(double d, double y0) { return fma(-(d * y0), y0, 1.0); }
 __device__ __forceinline__ double rsqrt_apply(double x, double y0, double e) {
   const double s = x * y0;

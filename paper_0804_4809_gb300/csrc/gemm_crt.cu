@@ -737,34 +737,45 @@ __global__ void __launch_bounds__(256, 2) reconstruct_kernel(ReconParams p, int 
   }
 }
 
-// Reconstruction when the modulus product P fits in 128 bits (n_mod <= 19:
-// the FP64-accurate products of the chain).  Each term t_j (P / p_j) then
-// has four 32-bit limbs, and the reduction mod P, the centring and the
-// rounding work on 64-bit words.  Four adjacent columns per thread (one
-// 32-bit load per modulus), eight rows x 128 columns per block.
-constexpr int kRec128MaxMod = 19;
-constexpr int kRec128Rows = 8, kRec128Cols = 128;
-struct __align__(16) Rec128Shared {
-  uint32_t Mj[crt::kMaxMod][4];  // P / p_j (< 2^128)
+// Reconstruction on 64-bit words, for n_mod <= 22 (P < 2^143).  NL = 4
+// limbs of 32 bits hold every multiplier P / p_j when P < 2^128 (n_mod <=
+// 19: the FP64-accurate products of the chain), NL = 5 otherwise (the
+// Gram's and the factorisation's wider products).  The CRT sum S (< n P)
+// lives in three 64-bit words; the reduction mod P uses a quotient estimate
+// from FP32, the centring and the rounding work word-wise.  Four adjacent
+// columns per thread (one 32-bit load per modulus), eight rows x 128
+// columns per block.
+constexpr int kRecWordsMaxMod = 22;
+constexpr int kRecWords4MaxMod = 19;
+constexpr int kRecWRows = 8, kRecWCols = 128;
+struct __align__(16) RecWShared {
+  uint32_t Mj[crt::kMaxMod][8];  // P / p_j, limbs 0..4, padded
   uint8_t tab[crt::kMaxMod][128];
 };
 
-// Correctly rounded (hi:lo) * 2^scale with sign, by integer operations.
-__device__ __forceinline__ double u128_to_double(bool neg, uint64_t hi, uint64_t lo, int scale) {
-  if ((hi | lo) == 0) return neg ? -0.0 : 0.0;
+// Correctly rounded (m2:m1:m0) * 2^scale with sign, by integer operations.
+__device__ __forceinline__ double u192_to_double(bool neg, uint64_t m2, uint64_t m1, uint64_t m0,
+                                                 int scale) {
   int top;
   uint64_t t;  // the 64 bits from the leading one down
   bool sticky;
-  if (hi) {
-    const int lz = __clzll((long long)hi);
+  if (m2) {
+    const int lz = __clzll((long long)m2);
+    top = 191 - lz;
+    t = lz ? (m2 << lz) | (m1 >> (64 - lz)) : m2;
+    sticky = (lz ? (m1 << lz) != 0 : m1 != 0) || m0 != 0;
+  } else if (m1) {
+    const int lz = __clzll((long long)m1);
     top = 127 - lz;
-    t = lz ? (hi << lz) | (lo >> (64 - lz)) : hi;
-    sticky = lz ? (lo << lz) != 0 : lo != 0;
-  } else {
-    const int lz = __clzll((long long)lo);
+    t = lz ? (m1 << lz) | (m0 >> (64 - lz)) : m1;
+    sticky = lz ? (m0 << lz) != 0 : m0 != 0;
+  } else if (m0) {
+    const int lz = __clzll((long long)m0);
     top = 63 - lz;
-    t = lo << lz;
+    t = m0 << lz;
     sticky = false;
+  } else {
+    return neg ? -0.0 : 0.0;
   }
   uint64_t mant = t >> 11;
   const uint64_t rem = t & 0x7FFull;
@@ -790,39 +801,68 @@ __device__ __forceinline__ uint64_t shr192(uint64_t s2, uint64_t s1, uint64_t s0
   return sh == 0 ? s0 : (s0 >> sh) | (s1 << (64 - sh));
 }
 
-__global__ void __launch_bounds__(256) reconstruct128_kernel(ReconParams p, int n_mod) {
+// (x2:x1:x0) += (y2:y1:y0) or -= , modulo 2^192
+__device__ __forceinline__ void add192(uint64_t& x2, uint64_t& x1, uint64_t& x0, uint64_t y2,
+                                       uint64_t y1, uint64_t y0) {
+  x0 += y0;
+  const uint64_t c0 = x0 < y0;
+  const uint64_t t1 = x1 + y1;
+  const uint64_t c1 = t1 < x1;
+  x1 = t1 + c0;
+  x2 += y2 + c1 + (x1 < c0 ? 1u : 0u);
+}
+__device__ __forceinline__ void sub192(uint64_t& x2, uint64_t& x1, uint64_t& x0, uint64_t y2,
+                                       uint64_t y1, uint64_t y0) {
+  const uint64_t b0 = x0 < y0;
+  x0 -= y0;
+  const uint64_t b1 = (x1 < y1) || (x1 == y1 && b0);
+  x1 = x1 - y1 - b0;
+  x2 = x2 - y2 - b1;
+}
+__device__ __forceinline__ bool gt192(uint64_t x2, uint64_t x1, uint64_t x0, uint64_t y2,
+                                      uint64_t y1, uint64_t y0) {
+  return x2 != y2 ? x2 > y2 : (x1 != y1 ? x1 > y1 : x0 > y0);
+}
+
+template <int NL>
+__global__ void __launch_bounds__(256) reconstruct_words_kernel(ReconParams p, int n_mod) {
   const crt::Consts& c = g_crt_consts[n_mod];
-  __shared__ Rec128Shared sh;
+  __shared__ RecWShared sh;
   {
     const uint32_t* src = reinterpret_cast<const uint32_t*>(&c.tab[0][0]);
     uint32_t* dst = reinterpret_cast<uint32_t*>(&sh.tab[0][0]);
     for (int e = threadIdx.x; e < n_mod * 32; e += blockDim.x) dst[e] = src[e];
-    for (int e = threadIdx.x; e < n_mod * 4; e += blockDim.x) sh.Mj[e >> 2][e & 3] = c.Mj[e >> 2][e & 3];
+    for (int e = threadIdx.x; e < n_mod * 8; e += blockDim.x)
+      sh.Mj[e >> 3][e & 7] = (e & 7) < crt::kLimbs ? c.Mj[e >> 3][e & 7] : 0u;
   }
   __syncthreads();
   const uint64_t P0 = c.P[0] | ((uint64_t)c.P[1] << 32), P1 = c.P[2] | ((uint64_t)c.P[3] << 32);
+  const uint64_t P2 = c.P[4];
   const uint64_t H0 = c.halfP[0] | ((uint64_t)c.halfP[1] << 32),
                  H1 = c.halfP[2] | ((uint64_t)c.halfP[3] << 32);
+  const uint64_t H2 = c.halfP[4];
   // quotient estimate floor(S / P) from the 24 leading bits of P: S >> qs
   // is below n 2^24 < 2^29, so FP32 holds it with a relative error of 2^-24
-  const int pbits = P1 ? 128 - __clzll((long long)P1) : 64 - __clzll((long long)P0);
+  const int pbits = P2   ? 192 - __clzll((long long)P2)
+                    : P1 ? 128 - __clzll((long long)P1)
+                         : 64 - __clzll((long long)P0);
   const int qs = pbits > 24 ? pbits - 24 : 0;
-  const float inv_ptop = 1.0f / (float)(uint32_t)shr192(0, P1, P0, qs);
+  const float inv_ptop = 1.0f / (float)(uint32_t)shr192(P2, P1, P0, qs);
 
   const int64_t M = eval_dim(p.M, p.rdev), N = eval_dim(p.N, p.rdev);
-  const int64_t i = (int64_t)blockIdx.y * kRec128Rows + (threadIdx.x >> 5);
-  const int64_t j0 = (int64_t)blockIdx.x * kRec128Cols + 4 * (threadIdx.x & 31);
+  const int64_t i = (int64_t)blockIdx.y * kRecWRows + (threadIdx.x >> 5);
+  const int64_t j0 = (int64_t)blockIdx.x * kRecWCols + 4 * (threadIdx.x & 31);
   if (i >= M || j0 >= N || (p.lower && j0 > i)) return;
   const size_t plane = (size_t)p.Mpad * (size_t)p.Npad;
   const uint32_t* r = reinterpret_cast<const uint32_t*>(p.R + i * p.Npad + j0);
-  uint64_t acc[4][4];
+  uint64_t acc[4][NL];
 #pragma unroll
   for (int e = 0; e < 4; ++e)
 #pragma unroll
-    for (int l = 0; l < 4; ++l) acc[e][l] = 0;
+    for (int l = 0; l < NL; ++l) acc[e][l] = 0;
   // residues in groups of seven loads in flight, then their sums
 #pragma unroll
-  for (int m0 = 0; m0 < 21; m0 += 7) {
+  for (int m0 = 0; m0 < kRecWordsMaxMod; m0 += 7) {
     uint32_t rv[7];
 #pragma unroll
     for (int q = 0; q < 7; ++q) rv[q] = (m0 + q) < n_mod ? r[(size_t)(m0 + q) * (plane / 4)] : 0u;
@@ -831,6 +871,7 @@ __global__ void __launch_bounds__(256) reconstruct128_kernel(ReconParams p, int 
       const int m = m0 + q;
       if (m < n_mod) {
         const uint4 mj = *reinterpret_cast<const uint4*>(&sh.Mj[m][0]);
+        const uint32_t mj4 = NL > 4 ? sh.Mj[m][4] : 0u;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const uint64_t t = sh.tab[m][(rv[q] >> (8 * e)) & 0xFFu];
@@ -838,6 +879,7 @@ __global__ void __launch_bounds__(256) reconstruct128_kernel(ReconParams p, int 
           acc[e][1] += t * mj.y;
           acc[e][2] += t * mj.z;
           acc[e][3] += t * mj.w;
+          if (NL > 4) acc[e][NL - 1] += t * mj4;
         }
       }
     }
@@ -847,50 +889,39 @@ __global__ void __launch_bounds__(256) reconstruct128_kernel(ReconParams p, int 
   for (int e = 0; e < 4; ++e) {
     const int64_t j = j0 + e;
     if (j >= N || (p.lower && j > i)) continue;
-    // S = sum_j t_j P/p_j (< n P < 2^131) as (s2:s1:s0)
-    uint32_t Sl[5];
+    // S = sum_j t_j P/p_j (< n P) as (s2:s1:s0)
+    uint32_t Sl[6];
     uint64_t carry = 0;
 #pragma unroll
-    for (int l = 0; l < 4; ++l) {
+    for (int l = 0; l < NL; ++l) {
       const uint64_t v = acc[e][l] + carry;
       Sl[l] = (uint32_t)v;
       carry = v >> 32;
     }
-    Sl[4] = (uint32_t)carry;
+    Sl[NL] = (uint32_t)carry;
+    if (NL == 4) Sl[5] = 0;
     const uint64_t s0 = Sl[0] | ((uint64_t)Sl[1] << 32), s1 = Sl[2] | ((uint64_t)Sl[3] << 32);
-    const uint64_t s2 = Sl[4];
+    const uint64_t s2 = Sl[4] | ((uint64_t)Sl[5] << 32);
     // X = S - q P, then into [0, P) (the estimate is off by at most one)
     const uint64_t q = (uint64_t)floorf((float)(uint32_t)shr192(s2, s1, s0, qs) * inv_ptop);
     const uint64_t qp0 = q * P0;
     const uint64_t c0 = __umul64hi(q, P0);
     const uint64_t qp1 = q * P1 + c0;
-    const uint64_t qp2 = __umul64hi(q, P1) + (qp1 < c0 ? 1u : 0u);
-    uint64_t x0 = s0 - qp0;
-    uint64_t b = s0 < qp0;
-    uint64_t x1 = s1 - qp1 - b;
-    b = (s1 < qp1) || (s1 == qp1 && b);
-    int64_t x2 = (int64_t)(s2 - qp2 - b);
-    if (x2 < 0) {  // X += P
-      x0 += P0;
-      const uint64_t cc = x0 < P0;
-      const uint64_t t1 = x1 + P1;
-      const uint64_t cc1 = t1 < x1;
-      x1 = t1 + cc;
-      x2 += (int64_t)(cc1 + (x1 < cc ? 1u : 0u));
-    } else if (x2 > 0 || x1 > P1 || (x1 == P1 && x0 >= P0)) {  // X -= P
-      const uint64_t bb = x0 < P0;
-      x0 -= P0;
-      const uint64_t t1 = x1 - P1;
-      x1 = t1 - bb;
-    }
+    const uint64_t qp2 = __umul64hi(q, P1) + (qp1 < c0 ? 1u : 0u) + q * P2;
+    uint64_t x0 = s0, x1 = s1, x2 = s2;
+    sub192(x2, x1, x0, qp2, qp1, qp0);
+    if ((int64_t)x2 < 0) add192(x2, x1, x0, P2, P1, P0);
+    else if (!gt192(P2, P1, P0, x2, x1, x0)) sub192(x2, x1, x0, P2, P1, P0);  // X >= P
     // centre into (-P/2, P/2]
-    const bool neg = x1 > H1 || (x1 == H1 && x0 > H0);
-    uint64_t m0 = x0, m1 = x1;
+    const bool neg = gt192(x2, x1, x0, H2, H1, H0);
     if (neg) {
-      m0 = P0 - x0;
-      m1 = P1 - x1 - (P0 < x0 ? 1u : 0u);
+      uint64_t m2 = P2, m1 = P1, m0 = P0;
+      sub192(m2, m1, m0, x2, x1, x0);
+      x2 = m2;
+      x1 = m1;
+      x0 = m0;
     }
-    double v = u128_to_double(neg, m1, m0, sa + p.EB[j] - 1022 - p.betaB);
+    double v = u192_to_double(neg, NL > 4 ? x2 : 0, x1, x0, sa + p.EB[j] - 1022 - p.betaB);
     double* cp = p.C + i * p.ldc + j;
     if (p.alpha != 1.0) v *= p.alpha;
     if (p.beta != 0.0) v = fma(p.beta, *cp, v);
@@ -1179,10 +1210,14 @@ cudaError_t crt_reconstruct(const uint8_t* R, int64_t Mpad, int64_t Npad, Dim M,
   return timer->run(KT_RECON, s, [&] {
     if (small)
       reconstruct_split_kernel<<<grid1d(M.max * N.max * kRecLanes, 256), 256, 0, s>>>(rp, n_mod);
-    else if (n_mod <= kRec128MaxMod)
-      reconstruct128_kernel<<<dim3((unsigned)((N.max + kRec128Cols - 1) / kRec128Cols),
-                                   (unsigned)((M.max + kRec128Rows - 1) / kRec128Rows)),
-                              256, 0, s>>>(rp, n_mod);
+    else if (n_mod <= kRecWords4MaxMod)
+      reconstruct_words_kernel<4><<<dim3((unsigned)((N.max + kRecWCols - 1) / kRecWCols),
+                                         (unsigned)((M.max + kRecWRows - 1) / kRecWRows)),
+                                    256, 0, s>>>(rp, n_mod);
+    else if (n_mod <= kRecWordsMaxMod)
+      reconstruct_words_kernel<5><<<dim3((unsigned)((N.max + kRecWCols - 1) / kRecWCols),
+                                         (unsigned)((M.max + kRecWRows - 1) / kRecWRows)),
+                                    256, 0, s>>>(rp, n_mod);
     else
       reconstruct_kernel<<<grid1d(M.max * ((N.max + kRecW - 1) / kRecW), 256), 256, 0, s>>>(
           rp, n_mod);
