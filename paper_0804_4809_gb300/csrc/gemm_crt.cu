@@ -183,23 +183,29 @@ __global__ void row_expo_kernel(const double* X, int64_t ld, int trans, Dim rows
 }
 
 // Residue planes of the 32-row x 64-column tile (rows i0.., k0..) of op(X):
-// 256 threads, each four rows x two adjacent columns, so that every modulus is
-// written as one 32-bit word (two BF16) per thread and row.
+// 256 threads, each one row x eight adjacent columns, so that every modulus
+// is written as one 16-byte store (eight BF16) per thread.
 template <int J>
-__device__ __forceinline__ void split_store(const uint32_t (&c0)[3], bool n0, const uint32_t (&c1)[3],
-                                            bool n1, int n_mod, uint32_t* dst, size_t plane_words) {
+__device__ __forceinline__ void split_store8(const uint32_t (&c)[8][3], const bool (&ng)[8],
+                                             int n_mod, uint4* dst, size_t plane_vec) {
   if (J >= n_mod) return;
-  const uint32_t lo = crt::small_int_bf16_bits(crt::residue21<J>(c0[0], c0[1], c0[2], n0));
-  const uint32_t hi = crt::small_int_bf16_bits(crt::residue21<J>(c1[0], c1[1], c1[2], n1));
-  dst[J * plane_words] = lo | (hi << 16);
+  uint32_t w[4];
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    const uint32_t lo =
+        crt::small_int_bf16_bits(crt::residue21<J>(c[2 * h][0], c[2 * h][1], c[2 * h][2], ng[2 * h]));
+    const uint32_t hi = crt::small_int_bf16_bits(
+        crt::residue21<J>(c[2 * h + 1][0], c[2 * h + 1][1], c[2 * h + 1][2], ng[2 * h + 1]));
+    w[h] = lo | (hi << 16);
+  }
+  dst[J * plane_vec] = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 template <int... Js>
-__device__ __forceinline__ void split_store_all(std::integer_sequence<int, Js...>,
-                                                const uint32_t (&c0)[3], bool n0,
-                                                const uint32_t (&c1)[3], bool n1, int n_mod,
-                                                uint32_t* dst, size_t plane_words) {
-  (split_store<Js>(c0, n0, c1, n1, n_mod, dst, plane_words), ...);
+__device__ __forceinline__ void split_store8_all(std::integer_sequence<int, Js...>,
+                                                 const uint32_t (&c)[8][3], const bool (&ng)[8],
+                                                 int n_mod, uint4* dst, size_t plane_vec) {
+  (split_store8<Js>(c, ng, n_mod, dst, plane_vec), ...);
 }
 
 __global__ void __launch_bounds__(256) split_kernel(const double* X, int64_t ld, int trans,
@@ -207,7 +213,8 @@ __global__ void __launch_bounds__(256) split_kernel(const double* X, int64_t ld,
                                                     int64_t kpad, const int64_t* rdev,
                                                     const int32_t* E, int n_mod, int beta,
                                                     bf16* out) {
-  __shared__ uint64_t tile[32][65];
+  // rows padded to 66 words: 16-byte aligned, four banks apart
+  __shared__ __align__(16) uint64_t tile[32][66];
   const int64_t rows = eval_dim(rowsd, rdev), cols = eval_dim(colsd, rdev);
   const int64_t i0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 64;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
@@ -226,29 +233,30 @@ __global__ void __launch_bounds__(256) split_kernel(const double* X, int64_t ld,
     }
   }
   __syncthreads();
-  const size_t plane_words = (size_t)rows_max * (size_t)kpad / 2;
+  const int q = threadIdx.x >> 3, g = threadIdx.x & 7;  // row, group of eight columns
+  const int64_t i = i0 + q;
+  if (i >= rows_max) return;
+  const int Ei = i < rows ? E[i] : 0;
+  uint32_t c[8][3];
+  bool ng[8];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int q = ty + 8 * u;
-    const int64_t i = i0 + q;
-    if (i >= rows_max) continue;
-    const int Ei = i < rows ? E[i] : 0;
-    uint32_t c[2][3];
-    bool neg[2];
+  for (int h = 0; h < 4; ++h) {
+    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(&tile[q][8 * g + 2 * h]);
+    const uint64_t bb[2] = {v.x, v.y};
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const uint64_t b = tile[q][2 * tx + h];
+    for (int u = 0; u < 2; ++u) {
+      const uint64_t b = bb[u];
       uint64_t a = 0;
       if (!nonfinite_bits(b)) a = crt::integerize(b, Ei, beta);
-      neg[h] = (b >> 63) != 0;
-      c[h][0] = (uint32_t)(a & 0x1FFFFF);
-      c[h][1] = (uint32_t)((a >> 21) & 0x1FFFFF);
-      c[h][2] = (uint32_t)(a >> 42);
+      ng[2 * h + u] = (b >> 63) != 0;
+      c[2 * h + u][0] = (uint32_t)(a & 0x1FFFFF);
+      c[2 * h + u][1] = (uint32_t)((a >> 21) & 0x1FFFFF);
+      c[2 * h + u][2] = (uint32_t)(a >> 42);
     }
-    uint32_t* dst = reinterpret_cast<uint32_t*>(out + (size_t)i * kpad + k0) + tx;
-    split_store_all(std::make_integer_sequence<int, crt::kMaxMod>{}, c[0], neg[0], c[1], neg[1],
-                    n_mod, dst, plane_words);
   }
+  uint4* dst = reinterpret_cast<uint4*>(out + (size_t)i * kpad + k0 + 8 * g);
+  split_store8_all(std::make_integer_sequence<int, crt::kMaxMod>{}, c, ng, n_mod, dst,
+                   (size_t)rows_max * (size_t)kpad / 8);
 }
 
 // Split precision: the row of op(X) scaled by 2^(1022 - E[i]) (|x| < 1), then
