@@ -469,7 +469,7 @@ int factor(const Ctx& c, double* a, int64_t lda, int spd) {
 }
 
 // CTAs of a fused panel launch that share the update of its diagonal block
-constexpr int64_t kPanelHelpers = 3;
+constexpr int64_t kPanelHelpers = 9;
 
 // A second library stream per device, with the events of the look-ahead
 // (reused cyclically: each wait is enqueued right after the record it

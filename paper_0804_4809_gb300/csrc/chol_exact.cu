@@ -234,17 +234,74 @@ __global__ void __launch_bounds__(kPanelThreads, 4) chol_panel_exact_kernel(Pane
     }
     __syncthreads();
   }
-  // the exact update of block entry (i, j): CRT part + sum over the last columns
-  auto block_update = [&](int i, int j) {
-    double* a = A + (k0 + i) * lda + (k0 + j);
-    const double a_old = *a;
-    uint32_t rv[kRvWords];
-    load_residues(p, i, j, rv);
-    uint64_t lo = 0;
-    int64_t hi = 0;
+  // The exact update of the block's entries [beg, end) of its lower
+  // triangle, four lanes per entry: lane g of a quad loads the residues of
+  // the moduli g, g + 4, ..., sums the columns kb + g, kb + g + 4, ... and the
+  // CRT terms of its moduli; the partial sums meet by shuffles and lane 0
+  // centres, rounds and stores.  The loop is warp-uniform (idle quads work on
+  // a repeated entry and store nothing) so the shuffles see the whole warp.
+  auto block_update_quads = [&](int beg, int end) {
+    const int g = threadIdx.x & 3;
+    constexpr int kQuads = kPanelThreads / 4;
+    constexpr int kModPerLane = crt::kMaxMod / 4;
+    for (int base = beg; base < end; base += kQuads) {
+      const int o0 = base + (int)(threadIdx.x >> 2);
+      const bool valid = o0 < end;
+      int i, j;
+      tri_index(valid ? o0 : beg, i, j);
+      double* a = A + (k0 + i) * lda + (k0 + j);
+      const double a_old = g == 0 ? *a : 0.0;
+      uint32_t rv[kModPerLane];
+      const size_t plane = (size_t)p.Mpad * (size_t)p.Npad;
+      const uint8_t* rp = p.R + (int64_t)i * p.Npad + j;
+#pragma unroll
+      for (int t = 0; t < kModPerLane; ++t) {
+        const int m = g + 4 * t;
+        rv[t] = (p.has_bulk && m < p.n_upd) ? rp[(size_t)m * plane] : 0u;
+      }
+      uint64_t lo = 0;
+      int64_t hi = 0;
 #pragma unroll 4
-    for (int k = 0; k < p.k_last; ++k) mac128(lo, hi, Lt[k][i], Lt[k][j]);
-    *a = apply_update(p, sh, shift, inv_ptop, i, j, a_old, rv, lo, hi);
+      for (int k = g; k < p.k_last; k += 4) mac128(lo, hi, Lt[k][i], Lt[k][j]);
+      uint64_t acc[crt::kLimbs] = {0, 0, 0, 0, 0};
+      if (p.has_bulk) {
+#pragma unroll
+        for (int t = 0; t < kModPerLane; ++t) {
+          const int m = g + 4 * t;
+          if (m < p.n_upd) {
+            const uint32_t tv = sh.tab[m][rv[t]];
+#pragma unroll
+            for (int l = 0; l < crt::kLimbs; ++l) acc[l] += (uint64_t)tv * sh.Mj[m][l];
+          }
+        }
+      }
+#pragma unroll
+      for (int off = 1; off < 4; off <<= 1) {
+        const uint64_t plo = __shfl_xor_sync(0xffffffffu, lo, off);
+        const int64_t phi = __shfl_xor_sync(0xffffffffu, hi, off);
+        lo += plo;
+        hi += phi + (lo < plo ? 1 : 0);
+#pragma unroll
+        for (int l = 0; l < crt::kLimbs; ++l) acc[l] += __shfl_xor_sync(0xffffffffu, acc[l], off);
+      }
+      if (g == 0 && valid) {
+        uint32_t Y[crt::kLimbs] = {0, 0, 0, 0, 0};
+        if (p.has_bulk) {
+          uint32_t S[crt::kLimbs];
+          uint64_t carry = 0;
+#pragma unroll
+          for (int l = 0; l < crt::kLimbs; ++l) {
+            const uint64_t v = acc[l] + carry;
+            S[l] = (uint32_t)v;
+            carry = v >> 32;
+          }
+          crt::crt_centre(S, sh.P, sh.halfP, shift, inv_ptop, Y);
+        }
+        crt::limbs_add128(Y, lo, hi);
+        const int scale = p.E[k0 + i] - 1022 - p.beta + p.E[k0 + j] - 1022 - p.beta;
+        *a = fma(1.0, a_old, -crt::limbs_to_double(Y, scale));
+      }
+    }
   };
   const int tri = bw * (bw + 1) / 2;
   if (helper) {
@@ -252,11 +309,7 @@ __global__ void __launch_bounds__(kPanelThreads, 4) chol_panel_exact_kernel(Pane
     const int chunk = (tri + p.helpers - 1) / p.helpers;
     const int beg = ((int)blockIdx.x - 1) * chunk;
     const int end = beg + chunk < tri ? beg + chunk : tri;
-    for (int o = beg + threadIdx.x; o < end; o += blockDim.x) {
-      int i, j;
-      tri_index(o, i, j);
-      block_update(i, j);
-    }
+    block_update_quads(beg, end);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) atomicAdd((unsigned long long*)&p.st->diag_count, 1ull);
@@ -265,11 +318,7 @@ __global__ void __launch_bounds__(kPanelThreads, 4) chol_panel_exact_kernel(Pane
   if (blockIdx.x == 0) {
     // the diagonal block: update (lower part), factor, publish, residues
     if (p.has_update && p.helpers == 0) {
-      for (int o = threadIdx.x; o < tri; o += blockDim.x) {
-        int i, j;
-        tri_index(o, i, j);
-        block_update(i, j);
-      }
+      block_update_quads(0, tri);
       __syncthreads();
     } else if (p.has_update) {
       // wait for the helpers' shares (bounded; ST_TIMEOUT on expiry)
