@@ -413,7 +413,9 @@ struct MmaParams {
   const int64_t* rdev;
   int32_t nk;               // K / BK (K padded)
   int32_t n_mod;
-  int32_t mods_per_cta;
+  int32_t tiles_m, tiles_n;  // output tiles (BM x BN) covering M.max x N.max
+  int32_t tiles;             // tiles in the enumeration (the lower ones only when lower)
+  int32_t pad_t;
   int32_t lower;            // skip tiles strictly above the diagonal
   uint8_t* R;               // residues [n_mod][Mpad][Npad]
   int64_t Mpad, Npad;
@@ -467,12 +469,41 @@ __global__ void __launch_bounds__(192, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   const int64_t M = eval_dim(p.M, p.rdev), N = eval_dim(p.N, p.rdev);
-  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
-  const int jbeg = blockIdx.z * p.mods_per_cta;
-  const int jend = min(p.n_mod, jbeg + p.mods_per_cta);
-  if (m0 >= M || n0 >= N || jbeg >= jend) return;
-  if (p.lower && n0 > m0 + BM - 1) return;
-  const int nmods = jend - jbeg;
+  // Jobs are the (modulus, tile) pairs, modulus-major; CTA c runs jobs c,
+  // c + G, c + 2G, ... (G CTAs), so every CTA gets the same number of jobs
+  // to within one and the CTAs running at the same time work on
+  // neighbouring tiles of the same modulus (their operand tiles are shared
+  // in L2).  Jobs on tiles outside the output (a device-side size below its
+  // maximum) are skipped by every role alike.
+  const int64_t J = (int64_t)p.tiles * p.n_mod;
+  const int64_t G = gridDim.x;
+  const int njobs = (int)((J - (int64_t)blockIdx.x + G - 1) / G);
+  if (njobs <= 0) return;
+  // job -> (m0, n0, modulus); false when the job has no output
+  auto job = [&](int jj, int64_t& m0, int64_t& n0, int& j) -> bool {
+    const int64_t q = (int64_t)blockIdx.x + (int64_t)jj * G;
+    j = (int)(q / p.tiles);
+    const int t = (int)(q - (int64_t)j * p.tiles);
+    int ty, tx;
+    if (!p.lower) {
+      ty = t / p.tiles_n;
+      tx = t - ty * p.tiles_n;
+    } else {  // row ty holds the tiles tx with tx BN <= ty BM + BM - 1
+      int rem = t;
+      ty = 0;
+      for (;;) {
+        int cnt = (ty * BM + BM - 1) / BN + 1;
+        cnt = cnt < p.tiles_n ? cnt : p.tiles_n;
+        if (rem < cnt || ty + 1 >= p.tiles_m) break;
+        rem -= cnt;
+        ++ty;
+      }
+      tx = rem;
+    }
+    m0 = (int64_t)ty * BM;
+    n0 = (int64_t)tx * BN;
+    return m0 < M && n0 < N && !(p.lower && n0 > m0 + BM - 1);
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -506,8 +537,10 @@ __global__ void __launch_bounds__(192, 1)
     // ---------------- TMA producer ----------------
     if (lane == 0) {
       uint32_t it = 0;
-      for (int jj = 0; jj < nmods && !*abort; ++jj) {
-        const int j = jbeg + jj;
+      for (int jj = 0; jj < njobs && !*abort; ++jj) {
+        int64_t m0, n0;
+        int j;
+        if (!job(jj, m0, n0, j)) continue;
         for (int kb = 0; kb < nk; ++kb, ++it) {
           const int s = (int)(it % STAGES);
           const uint32_t ph = (it / STAGES) & 1u;
@@ -534,9 +567,14 @@ __global__ void __launch_bounds__(192, 1)
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16<BN>();
       uint32_t it = 0;
-      for (int jj = 0; jj < nmods && !*abort; ++jj) {
-        const int acc = jj & 1;
-        if (!mbar_wait(&sm.accempty[acc], ((jj >> 1) & 1u) ^ 1u, abort)) break;
+      int na = 0;  // active jobs so far (the accumulator sequence)
+      for (int jj = 0; jj < njobs && !*abort; ++jj) {
+        int64_t m0, n0;
+        int j;
+        if (!job(jj, m0, n0, j)) continue;
+        const int acc = na & 1;
+        if (!mbar_wait(&sm.accempty[acc], ((na >> 1) & 1u) ^ 1u, abort)) break;
+        ++na;
         tc_fence_after();
         const uint32_t dtm = tmem + (uint32_t)(acc * BN);
         bool ok = true;
@@ -571,11 +609,15 @@ __global__ void __launch_bounds__(192, 1)
   } else {
     // ---------------- epilogue: 4 warps, warp w reads TMEM lanes 32*(w%4).. ----------------
     const int q = warp & 3;
-    const int64_t row = m0 + q * 32 + lane;
-    for (int jj = 0; jj < nmods; ++jj) {
-      const int acc = jj & 1;
-      const int j = jbeg + jj;
-      if (!mbar_wait(&sm.accfull[acc], (jj >> 1) & 1u, abort)) break;
+    int na = 0;
+    for (int jj = 0; jj < njobs; ++jj) {
+      int64_t m0, n0;
+      int j;
+      if (!job(jj, m0, n0, j)) continue;
+      const int acc = na & 1;
+      if (!mbar_wait(&sm.accfull[acc], (na >> 1) & 1u, abort)) break;
+      ++na;
+      const int64_t row = m0 + q * 32 + lane;
       tc_fence_after();
       if constexpr (S3) {
         const int64_t Mv = M, Nv = N;
@@ -1042,9 +1084,27 @@ bool make_map(CUtensorMap* map, const bf16* base, int64_t kpad, int64_t rows, in
   return r == CUDA_SUCCESS;
 }
 
+// The grid: `wave` CTAs (one per SM, or fewer to leave SMs to concurrent
+// work) taking the (modulus, tile) jobs in turn; fewer when there are fewer
+// jobs.
 template <int BN, int STAGES, bool S3>
-cudaError_t launch_mma(const CUtensorMap& ta, const CUtensorMap& tb, const MmaParams& mp,
-                       int64_t Mmax, int64_t Nmax, cudaStream_t s) {
+cudaError_t launch_mma(const CUtensorMap& ta, CUtensorMap const& tb, MmaParams& mp,
+                       int64_t Mmax, int64_t Nmax, int64_t wave, cudaStream_t s) {
+  mp.tiles_m = (int32_t)((Mmax + BM - 1) / BM);
+  mp.tiles_n = (int32_t)((Nmax + BN - 1) / BN);
+  int64_t tiles = 0;
+  if (!mp.lower) {
+    tiles = (int64_t)mp.tiles_m * mp.tiles_n;
+  } else {
+    for (int ty = 0; ty < mp.tiles_m; ++ty) {
+      const int64_t cnt = ((int64_t)ty * BM + BM - 1) / BN + 1;
+      tiles += cnt < mp.tiles_n ? cnt : mp.tiles_n;
+    }
+  }
+  mp.tiles = (int32_t)tiles;
+  const int64_t jobs = tiles * mp.n_mod;
+  const int64_t ctas = jobs < wave ? jobs : wave;
+  if (ctas <= 0) return cudaSuccess;
   const size_t smem = sizeof(MmaSmem<BN, STAGES, S3 ? 2 : 1>) + 1024;
   static bool attr = false;
   if (!attr) {
@@ -1058,9 +1118,7 @@ cudaError_t launch_mma(const CUtensorMap& ta, const CUtensorMap& tb, const MmaPa
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const int groups = (mp.n_mod + mp.mods_per_cta - 1) / mp.mods_per_cta;
-  dim3 grid((unsigned)((Nmax + BN - 1) / BN), (unsigned)((Mmax + BM - 1) / BM), (unsigned)groups);
-  crt_mma_kernel<BN, STAGES, S3><<<grid, 192, smem, s>>>(ta, tb, mp);
+  crt_mma_kernel<BN, STAGES, S3><<<dim3((unsigned)ctas), 192, smem, s>>>(ta, tb, mp);
   return cudaGetLastError();
 }
 
@@ -1148,26 +1206,17 @@ cudaError_t crt_mma(const void* SA, int64_t a_rows, int a_row0, const void* SB, 
   mp.Mpad = Mpad;
   mp.Npad = Npad;
   mp.status = status;
-  // CTAs: about one wave of (tile, group of moduli) -- or max_ctas, to leave
-  // SMs to concurrent work; a CTA runs its moduli back to back
-  // (double-buffered accumulators), amortising its set-up
-  int64_t tiles = ((Mmax + BM - 1) / BM) * ((Nmax + BN - 1) / BN) / (lower ? 2 : 1);
-  if (tiles < 1) tiles = 1;
   const int64_t wave = max_ctas > 0 ? max_ctas : 152;
-  int64_t groups = (wave + tiles - 1) / tiles;
-  if (groups > n_mod) groups = n_mod;
-  if (groups < 1) groups = 1;
-  mp.mods_per_cta = (int)((n_mod + groups - 1) / groups);
   KernelTimer mt = *timer;
   mt.gemm = fl;
   mt.flops_mult = (double)n_mod;
   return mt.run(KT_MMA, s, [&] {
-    if (BN == 256) return launch_mma<256, 4, false>(ta, tb, mp, Mmax, Nmax, s);
+    if (BN == 256) return launch_mma<256, 4, false>(ta, tb, mp, Mmax, Nmax, wave, s);
     // a capped grid shares the SMs with concurrent work: fewer stages, less
     // shared memory per CTA
-    if (BN == 32 && max_ctas > 0) return launch_mma<32, 4, false>(ta, tb, mp, Mmax, Nmax, s);
-    if (BN == 32) return launch_mma<32, 8, false>(ta, tb, mp, Mmax, Nmax, s);
-    return launch_mma<128, 6, false>(ta, tb, mp, Mmax, Nmax, s);
+    if (BN == 32 && max_ctas > 0) return launch_mma<32, 4, false>(ta, tb, mp, Mmax, Nmax, wave, s);
+    if (BN == 32) return launch_mma<32, 8, false>(ta, tb, mp, Mmax, Nmax, wave, s);
+    return launch_mma<128, 6, false>(ta, tb, mp, Mmax, Nmax, wave, s);
   });
 }
 
@@ -1293,7 +1342,7 @@ cudaError_t launch_split_gemm(const CrtGemm& g, cudaStream_t s, KernelTimer* tim
   mp.rdev = p.rdev;
   mp.nk = (int)(kpad / BK);
   mp.n_mod = 1;
-  mp.mods_per_cta = 1;
+
   mp.lower = p.lower;
   mp.status = &g.st->status;
   mp.C = p.C;
@@ -1305,7 +1354,8 @@ cudaError_t launch_split_gemm(const CrtGemm& g, cudaStream_t s, KernelTimer* tim
   KernelTimer mt = *timer;
   mt.gemm = &g.p;
   mt.flops_mult = 3.0;
-  return mt.run(KT_MMA, s, [&] { return launch_mma<128, 3, true>(ta, tb, mp, Mmax, Nmax, s); });
+  return mt.run(KT_MMA, s,
+                [&] { return launch_mma<128, 3, true>(ta, tb, mp, Mmax, Nmax, 152, s); });
 }
 
 cudaError_t launch_crt_gemm(const CrtGemm& g, cudaStream_t s, KernelTimer* timer) {
