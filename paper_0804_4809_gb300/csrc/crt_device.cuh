@@ -149,7 +149,9 @@ __device__ __forceinline__ void crt_centre(const uint32_t (&S)[crt::kLimbs], con
     if (off) w |= limb_at(S, li + 1) << (32 - off);
     stop |= (uint64_t)w << (32 * b);
   }
-  int qe = (int)floorf((float)stop * inv_ptop);
+  // from the top 32 bits of the window (stop < 2^63): a 64-bit integer to
+  // float conversion would run on the FP64 pipe
+  int qe = (int)floorf((float)(uint32_t)(stop >> 32) * (inv_ptop * 4294967296.0f));
   qe = qe < 0 ? 0 : qe;
   // X = S - qe * P  (signed, two's complement over the limbs)
   int64_t borrow = 0;

@@ -960,7 +960,9 @@ __global__ void __launch_bounds__(256) reconstruct_words_kernel(ReconParams p, i
     const uint64_t s0 = Sl[0] | ((uint64_t)Sl[1] << 32), s1 = Sl[2] | ((uint64_t)Sl[3] << 32);
     const uint64_t s2 = Sl[4] | ((uint64_t)Sl[5] << 32);
     // X = S - q P, then into [0, P) (the estimate is off by at most one)
-    const uint64_t q = (uint64_t)floorf((float)(uint32_t)shr192(s2, s1, s0, qs) * inv_ptop);
+    // (through a 32-bit integer: a float to 64-bit integer conversion would
+    // run on the FP64 pipe)
+    const uint64_t q = (uint32_t)floorf((float)(uint32_t)shr192(s2, s1, s0, qs) * inv_ptop);
     const uint64_t qp0 = q * P0;
     const uint64_t c0 = __umul64hi(q, P0);
     const uint64_t qp1 = q * P1 + c0;
