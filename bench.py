@@ -235,7 +235,7 @@ def run_e2e(mode, G_host, steps, device):
         plan(Gd, Yd, stream=s.cuda_stream)
         Yh.copy_(Yd, non_blocking=True)
 
-    for _ in range(3):  # the first calls run directly, then capture the call's graph
+    for _ in range(5):  # the first calls run directly, then capture the call's graph
         step()
     torch.cuda.synchronize()
     ts = []
@@ -396,6 +396,8 @@ def ours(args):
         line["roofline_tensor"] = tensor_roofline(device, burst, burst_src)
     line["e2e"] = {"value": round(flops * K * ws / t_e2e / 1e12, 4), "unit": "TFLOP/s",
                    "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+                   "ms_per_step_median": round(1e3 * statistics.median(e2e["s"]), 4),
+                   "ms_per_step_max": round(1e3 * max(e2e["s"]), 4),
                    "mode": modes[0]}
     if cpu is not None:
         t_cpu = statistics.median(cpu["times"])
@@ -576,8 +578,9 @@ def batched_bench(args, device, flush, loop_steps: int = 2) -> dict:
 
 def rbf_and_adjoint_bench(args, device, flush, steps: int = 3) -> dict:
     """Device time per call of the RBF least-squares workload (16384 x 2048,
-    d = 8, k = 16) and of the adjoint workload (8192 x 1024 RBF, d = 4,
-    k = 8: forward W = G+ F plus the reverse pass) in each arithmetic mode."""
+    d = 8, k = 16), of the same solve from normal equations accumulated over
+    row blocks, and of the adjoint workload (8192 x 1024 RBF, d = 4, k = 8:
+    forward W = G+ F plus the reverse pass) in each arithmetic mode."""
     import torch
 
     from paper_0804_4809_gb300 import cpinv, inputs
@@ -594,6 +597,27 @@ def rbf_and_adjoint_bench(args, device, flush, steps: int = 3) -> dict:
         t = sum(ms) / 1e3 / steps
         out["rbf_lstsq"][md] = {"ms": round(t * 1e3, 3), "rank": r,
                                 "tflops": round(lstsq_flops(16384, 2048, r, 16) / t / 1e12, 3)}
+    # incremental learning (Sec. 4): the same rows arriving in 8 blocks of
+    # 2048, folded into A = G'G, B = G'F (cpinv_gram_update), then W from A
+    # and B alone (cpinv_lstsq_gram); against the one-shot solve above
+    out["incremental_lstsq"] = {"workload": "RBF 16384 x 2048, k = 16, rows in 8 blocks of 2048"}
+    blocks = [(Gd[i:i + 2048].contiguous(), Fd[i:i + 2048].contiguous()) for i in range(0, 16384, 2048)]
+    A = torch.zeros((2048, 2048), dtype=torch.float64, device=device)
+    B = torch.zeros((2048, 16), dtype=torch.float64, device=device)
+    for md in ("exact", "fp64"):
+        W1, r1 = cpinv.lstsq(Gd, Fd, mode=md)
+
+        def run():
+            A.zero_()
+            B.zero_()
+            for Gb, Fb in blocks:
+                cpinv.gram_update(A, Gb, B, Fb, mode=md)
+            return cpinv.lstsq_gram(A, B, mode=md)
+        W2, r2 = run()
+        ms = time_steps(run, steps, flush, s)
+        d = float(torch.linalg.norm(W2 - W1) / torch.linalg.norm(W1))
+        out["incremental_lstsq"][md] = {"ms": round(sum(ms) / steps, 3), "rank": r2,
+                                        "rank_one_shot": r1, "rel_diff_vs_one_shot": d}
     G2, X2, _ = inputs.rbf_design(8192, 1024, 4, 0.3, 5)
     F2 = inputs.smooth_targets(X2, 8, 5)
     G2d, F2d = torch.from_numpy(G2).to(device), torch.from_numpy(F2).to(device)

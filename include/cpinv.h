@@ -135,6 +135,17 @@ int cpinv_lstsq_gram(const double* A, int64_t n, int64_t lda, const double* B, i
                      const cpinv_opts* o, int64_t* rank_out, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Failure path of the device-side waits, exercised without a fault: one
+ * thread runs the bounded wait of the factorisation kernels on a counter that
+ * nothing advances (workspace: >= 128 bytes of device memory, overwritten),
+ * so the wait gives up after about a second and records the timeout.
+ * Returns CPINV_ERR_TIMEOUT when the wait expired as designed (the expected
+ * result; the context stays usable), CPINV_OK if it did not, CPINV_ERR_CUDA
+ * or CPINV_ERR_INVALID_ARG otherwise.  Synchronises the stream.
+ * ------------------------------------------------------------------------- */
+int cpinv_selftest_wait_timeout(void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Adjoint of the least-squares weights (reverse mode): given the cotangent
  * Wbar = dL/dW (n x k) of a scalar L of W = G+ F, returns
  *   dG = dL/dG (m x n)  and, if dF != NULL, dF = dL/dF (m x k),

@@ -79,6 +79,7 @@ SIGNATURES = {
                                             _c_vp, _c_i64, _c_vp, _c_i64, _c_vp, _c_i64, _c_vp,
                                             _c_i64, _c_vp, _c_sz, ctypes.POINTER(Opts),
                                             ctypes.POINTER(_c_i64), _c_vp]),
+    "cpinv_selftest_wait_timeout": (ctypes.c_int, [_c_vp, _c_sz, _c_vp]),
     "cpinv_gram_update_workspace_size": (_c_sz, [_c_i64, _c_i64, _c_i64, ctypes.c_int32]),
     "cpinv_gram_update": (ctypes.c_int, [_c_vp, _c_i64, _c_i64, _c_i64, _c_vp, _c_i64, _c_i64,
                                          _c_vp, _c_i64, _c_vp, _c_i64, ctypes.c_int32, _c_vp,
@@ -274,6 +275,15 @@ def lstsq_gram(A: torch.Tensor, B: torch.Tensor, mode="fp64", rel_tol: float = 1
                                 ctypes.byref(r), _stream(A.device))
     _check(st)
     return W, int(r.value)
+
+
+def selftest_wait_timeout(device=None) -> int:
+    """Runs the kernels' bounded wait on a counter nothing advances; returns
+    the library status (CPINV_ERR_TIMEOUT expected)."""
+    import torch
+    dev = torch.device("cuda", 0) if device is None else torch.device(device)
+    ws = _workspace(256, dev)
+    return int(lib().cpinv_selftest_wait_timeout(ws.data_ptr(), ws.numel(), _stream(dev)))
 
 
 def lstsq_backward(G: torch.Tensor, F: torch.Tensor, dW: torch.Tensor, mode="fp64",

@@ -1418,6 +1418,19 @@ int cpinv_gram_update(const double* G, int64_t m, int64_t n, int64_t ldg, const 
                      workspace_bytes, 0, stream);
 }
 
+int cpinv_selftest_wait_timeout(void* workspace, size_t workspace_bytes, void* stream) {
+  if (!workspace || workspace_bytes < sizeof(DevState)) return CPINV_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevState* st = (DevState*)workspace;
+  if (cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess) return CPINV_ERR_CUDA;
+  if (launch_wait_selftest(st, s) != cudaSuccess) return CPINV_ERR_CUDA;
+  DevState h;
+  if (cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return CPINV_ERR_CUDA;
+  return (h.status & ST_TIMEOUT) ? CPINV_ERR_TIMEOUT : CPINV_OK;
+}
+
 int cpinv_profile_enable(int on) {
   const int prev = g_tr.on ? 1 : 0;
   for (auto& t : g_tr.recs) {

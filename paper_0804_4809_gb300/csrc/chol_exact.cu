@@ -73,6 +73,22 @@ __device__ __forceinline__ int64_t ld_relaxed(const int64_t* p) {
 __device__ __forceinline__ void st_release(int64_t* p, int64_t v) {
   asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+// Bounded wait for *ctr >= target (one thread): false after kFlagSpinLimit
+// polls (about a second), with ST_TIMEOUT recorded in *status; the caller
+// goes on either way.  Later reads are ordered after the poll by a fence.
+__device__ __forceinline__ bool wait_at_least(const int64_t* ctr, int64_t target, int32_t* status) {
+  bool ok = false;
+  for (uint32_t it = 0; it < kFlagSpinLimit; ++it) {
+    if (ld_relaxed(ctr) >= target) {
+      ok = true;
+      break;
+    }
+    __nanosleep(it < 64 ? 32 : 256);
+  }
+  if (!ok) atomicOr(status, ST_TIMEOUT);
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+  return ok;
+}
 
 // The beta-bit integer that the residue planes hold for the factor entry v
 // of a row with scale E, in two's complement.
@@ -322,18 +338,7 @@ __global__ void __launch_bounds__(kPanelThreads, 4) chol_panel_exact_kernel(Pane
       __syncthreads();
     } else if (p.has_update) {
       // wait for the helpers' shares (bounded; ST_TIMEOUT on expiry)
-      if (threadIdx.x == 0) {
-        int ok = 0;
-        for (uint32_t it = 0; it < kFlagSpinLimit; ++it) {
-          if (ld_relaxed(&p.st->diag_count) >= p.diag_target) {
-            ok = 1;
-            break;
-          }
-          __nanosleep(it < 64 ? 32 : 256);
-        }
-        if (!ok) atomicOr(&p.st->status, ST_TIMEOUT);
-        asm volatile("fence.acq_rel.gpu;" ::: "memory");
-      }
+      if (threadIdx.x == 0) wait_at_least(&p.st->diag_count, p.diag_target, &p.st->status);
       __syncthreads();
     }
     if (warp < chol::kDiagWarps)
@@ -381,19 +386,7 @@ __global__ void __launch_bounds__(kPanelThreads, 4) chol_panel_exact_kernel(Pane
   } else if (row_ok && lane < bw) {
     acc = A[i * lda + k0 + lane];
   }
-  if (threadIdx.x == 0) {
-    int ok = 0;
-    for (uint32_t it = 0; it < kFlagSpinLimit; ++it) {
-      if (ld_relaxed(&p.st->panel_flag) >= p.epoch) {
-        ok = 1;
-        break;
-      }
-      __nanosleep(it < 64 ? 32 : 256);
-    }
-    if (!ok) atomicOr(&p.st->status, ST_TIMEOUT);
-    asm volatile("fence.acq_rel.gpu;" ::: "memory");
-    go = ok;
-  }
+  if (threadIdx.x == 0) go = wait_at_least(&p.st->panel_flag, p.epoch, &p.st->status);
   __syncthreads();
   if (!go) return;
   // Ts[r][c] = T(r, c) / T(c, c) below the diagonal (see panel_solve_rows);
@@ -417,6 +410,13 @@ __global__ void __launch_bounds__(kPanelThreads, 4) chol_panel_exact_kernel(Pane
     A[i * lda + k0 + lane] = l;
     split_store(p, i, k0 + lane, l);
   }
+}
+
+// The panel kernel's bounded wait on a counter that nothing advances: it
+// must give up, record ST_TIMEOUT and return (the failure path of every
+// flag wait, exercised without a fault).
+__global__ void wait_selftest_kernel(DevState* st) {
+  if (threadIdx.x == 0) wait_at_least(&st->spare[0], 1, &st->status);
 }
 
 inline unsigned grid1d(int64_t total, int threads) {
@@ -452,6 +452,11 @@ cudaError_t launch_chol_panel_exact(const PanelExactParams& p, cudaStream_t s) {
     attr = true;
   }
   chol_panel_exact_kernel<<<(unsigned)ctas, kPanelThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(DevState* st, cudaStream_t s) {
+  wait_selftest_kernel<<<1, 32, 0, s>>>(st);
   return cudaGetLastError();
 }
 

@@ -74,6 +74,13 @@ __device__ __forceinline__ int residue21(uint32_t a0, uint32_t a1, uint32_t a2, 
 // CRT reconstruction: exact integer (5 x 32-bit limbs) -> FP64
 // ---------------------------------------------------------------------------
 
+// +-mant * 2^e outside the normal exponent range: the FP64 unit handles the
+// under/overflow; out of line, so that the common path never executes it.
+__device__ __noinline__ inline double compose_out_of_range(bool neg, uint64_t mant, int e) {
+  const double d = ldexp((double)mant, e);
+  return neg ? -d : d;
+}
+
 __device__ __forceinline__ double compose_double(bool neg, const uint32_t (&mag)[crt::kLimbs],
                                                  int scale) {
   // correctly rounded mag * 2^scale (mag < 2^160), via integer operations
@@ -110,11 +117,7 @@ __device__ __forceinline__ double compose_double(bool neg, const uint32_t (&mag)
     ++e;
   }
   const int biased = e + scale + 1023;
-  if (biased <= 0 || biased >= 2047) {
-    // out of the normal range: let the FP64 unit handle under/overflow
-    const double d = ldexp((double)mant, e - 52 + scale);
-    return neg ? -d : d;
-  }
+  if (biased <= 0 || biased >= 2047) return compose_out_of_range(neg, mant, e - 52 + scale);
   const uint64_t bits = ((uint64_t)neg << 63) | ((uint64_t)biased << 52) | (mant & 0xFFFFFFFFFFFFFull);
   return __longlong_as_double((long long)bits);
 }

@@ -430,8 +430,13 @@ struct MmaParams {
 
 // alpha x + beta c, with the alpha == 1 and beta == 0 tests on the bit
 // patterns (integer compares: an FP64 compare takes a slot of the narrow
-// FP64 pipe, and these run once per output).
-__device__ __forceinline__ double scale_add(double x, double alpha, double beta, const double* c) {
+// FP64 pipe, and these run once per output); out of line, called only when
+// plain_store() is false, so the common path executes no FP64 instruction.
+__device__ __forceinline__ bool plain_store(double alpha, double beta) {
+  return __double_as_longlong(alpha) == 0x3FF0000000000000ll &&
+         ((uint64_t)__double_as_longlong(beta) << 1) == 0;
+}
+__device__ __noinline__ double scale_add(double x, double alpha, double beta, const double* c) {
   if (__double_as_longlong(alpha) != 0x3FF0000000000000ll) x *= alpha;
   if (((uint64_t)__double_as_longlong(beta) << 1) != 0) x = fma(beta, *c, x);
   return x;
@@ -643,7 +648,7 @@ __global__ void __launch_bounds__(192, 1)
             if (col >= Nv || (p.lower && col > row)) continue;
             double d = f32_scaled_to_f64(v[e], sr + p.EB[col] - 1022);
             double* cp = p.C + row * p.ldc + col;
-            d = scale_add(d, p.alpha, p.beta, cp);
+            if (!plain_store(p.alpha, p.beta)) d = scale_add(d, p.alpha, p.beta, cp);
             *cp = d;
           }
         }
@@ -788,7 +793,7 @@ __global__ void __launch_bounds__(256, 2) reconstruct_kernel(ReconParams p, int 
       }
       double v = crt::crt_finish(S, sh.P, sh.halfP, shift, inv_ptop, sa + p.EB[j] - 1022 - p.betaB);
       double* cp = p.C + i * p.ldc + j;
-      v = scale_add(v, p.alpha, p.beta, cp);
+      if (!plain_store(p.alpha, p.beta)) v = scale_add(v, p.alpha, p.beta, cp);
       *cp = v;
     }
   }
@@ -809,6 +814,13 @@ struct __align__(16) RecWShared {
   uint32_t Mj[crt::kMaxMod][8];  // P / p_j, limbs 0..4, padded
   uint8_t tab[crt::kMaxMod][128];
 };
+
+// +-mant * 2^e outside the normal exponent range (the FP64 unit rounds the
+// underflow); out of line, so that the common path never executes it.
+__device__ __noinline__ double scaled_out_of_range(bool neg, uint64_t mant, int e) {
+  const double d = ldexp((double)mant, e);
+  return neg ? -d : d;
+}
 
 // Correctly rounded (m2:m1:m0) * 2^scale with sign, by integer operations.
 __device__ __forceinline__ double u192_to_double(bool neg, uint64_t m2, uint64_t m1, uint64_t m0,
@@ -843,10 +855,7 @@ __device__ __forceinline__ double u192_to_double(bool neg, uint64_t m2, uint64_t
     ++e;
   }
   const int biased = e + scale + 1023;
-  if (biased <= 0 || biased >= 2047) {
-    const double d = ldexp((double)mant, e - 52 + scale);
-    return neg ? -d : d;
-  }
+  if (biased <= 0 || biased >= 2047) return scaled_out_of_range(neg, mant, e - 52 + scale);
   return __longlong_as_double(
       (long long)(((uint64_t)neg << 63) | ((uint64_t)biased << 52) | (mant & 0xFFFFFFFFFFFFFull)));
 }
@@ -982,7 +991,7 @@ __global__ void __launch_bounds__(256) reconstruct_words_kernel(ReconParams p, i
     }
     double v = u192_to_double(neg, NL > 4 ? x2 : 0, x1, x0, sa + p.EB[j] - 1022 - p.betaB);
     double* cp = p.C + i * p.ldc + j;
-    v = scale_add(v, p.alpha, p.beta, cp);
+    if (!plain_store(p.alpha, p.beta)) v = scale_add(v, p.alpha, p.beta, cp);
     *cp = v;
   }
 }
@@ -1053,7 +1062,7 @@ __global__ void __launch_bounds__(256) reconstruct_split_kernel(ReconParams p, i
     double v = crt::crt_finish(S, sh.P, sh.halfP, c.shift, c.inv_ptop,
                           p.EA[i] - 1022 - p.betaA + p.EB[j] - 1022 - p.betaB);
     double* cp = p.C + i * p.ldc + j;
-    v = scale_add(v, p.alpha, p.beta, cp);
+    if (!plain_store(p.alpha, p.beta)) v = scale_add(v, p.alpha, p.beta, cp);
     *cp = v;
   }
 }

@@ -124,6 +124,9 @@ struct PanelExactParams {
   int32_t pad;
   int64_t diag_target;  // st->diag_count once this panel's helpers are done
 };
+// One CTA waits, bounded, on st->spare[0] >= 1 (nothing sets it): records
+// ST_TIMEOUT in st->status after about a second and returns.
+cudaError_t launch_wait_selftest(DevState* st, cudaStream_t s);
 cudaError_t launch_chol_panel_exact(const PanelExactParams& p, cudaStream_t s);
 int64_t chol_panel_exact_ctas(int64_t nmax, int64_t k0, int b);  // grid size of that launch
 
