@@ -191,10 +191,6 @@ int prod_kind(const Plan& p, Site site, int64_t Mmax, int64_t Nmax, int64_t Kmax
   return PK_EXACT;
 }
 
-bool use_exact(const Plan& p, Site site, int64_t Mmax, int64_t Nmax, int64_t Kmax) {
-  return prod_kind(p, site, Mmax, Nmax, Kmax) == PK_EXACT;
-}
-
 size_t crt_need(const Plan& p, Site site, int64_t M, int64_t N, int64_t K, bool same) {
   const int pk = prod_kind(p, site, M, N, K);
   if (pk == PK_SPLIT) return split_workspace_bytes(M, N, K, same);
