@@ -177,6 +177,24 @@ def dist_setup():
     return ws, rank, local
 
 
+def max_over_ranks(vals, device):
+    """Element-wise maximum of the ranks' timings (the slowest rank sets the
+    job's time); the values themselves with a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in vals]
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def whole_job_tflops(flops_per_step, steps, world_size, t_max_s):
+    """Whole-job throughput: every rank solves `steps` problems of
+    `flops_per_step` algorithmic flops; the job takes the slowest rank's time."""
+    return flops_per_step * steps * world_size / t_max_s / 1e12
+
+
 def time_steps(fn, steps, flush, stream):
     import torch
     evs = []
@@ -298,17 +316,13 @@ def ours(args):
     t_sum = sum(results[head]["ms"]) / 1e3
     t_fp64 = sum(results["fp64"]["ms"]) / 1e3 if "fp64" in results else t_sum
     t_e2e = sum(e2e["s"])
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_sum, t_fp64, t_e2e], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_sum, t_fp64, t_e2e = (float(x) for x in t.tolist())
+    t_sum, t_fp64, t_e2e = max_over_ranks([t_sum, t_fp64, t_e2e], device)
     if rank != 0:
         return
 
     flops = pinv_flops(M, N, R)
     K = args.steps
-    value = flops * K * ws / t_sum / 1e12
+    value = whole_job_tflops(flops, K, ws, t_sum)
     line = {
         "metric": "pinv TFLOP/s (algorithmic flops / device time), 4096x2048 rank 1536",
         "value": round(value, 4),
