@@ -93,7 +93,8 @@ constexpr int kDiagThreads = 32 * kDiagWarps;
 // column first and finishes it before its other updates, so the hand-off of
 // every column waits for one update and one pivot only.  (FP64 instructions
 // take about 65 cycles of an SM sub-partition's FP64 pipe each, whatever the
-// active lanes, so the chain's cost is its count of FP64 instructions.)  A
+// active lanes, so the chain's cost is its count of FP64 instructions, and
+// the trailing updates of two high columns share one instruction.)  A
 // warp's registers shift by one column each time it finishes one, so its
 // next column is always a[0] and register indices stay compile-time
 // constants in a loop over columns that is not unrolled: a long unrolled
@@ -119,13 +120,26 @@ __device__ __forceinline__ void diag_chol_block(double* A, int64_t lda, Dim nd, 
   // a[q]: this lane's entry of column jn + 4q, jn = this warp's next column
   // to finish (jn = w + 4 * columns finished)
   int jn = w;
-  double a[8];
+  double a[4];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
+  for (int q = 0; q < 4; ++q) {
     const int j = w + kDiagWarps * q;
     // L2 loads: other CTAs of a fused launch may have just written the block
     a[q] = (lane < bw && j < bw && j <= lane) ? __ldcg(A + (k0 + lane) * lda + (k0 + j)) : 0.0;
   }
+  // The warp's four high columns (>= 16) have entries in rows 16..31 only,
+  // so two of them share a register until the low ones are done: pk[h]
+  // holds column w + 16 + 8h in lanes 0-15 and column w + 20 + 8h in lanes
+  // 16-31, row 16 + (lane & 15); an update instruction then does the work
+  // of two (an FP64 instruction costs the same whatever its active lanes).
+  const int prow = 16 + (lane & 15);
+  double pk[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int jp = w + 16 + 8 * h + (lane < 16 ? 0 : 4);
+    pk[h] = (prow < bw && jp < bw && jp <= prow) ? __ldcg(A + (k0 + prow) * lda + (k0 + jp)) : 0.0;
+  }
+  bool packed = true;
   // Finishes column c held in `acol` (owner warp only); returns L(lane, c).
   // Lane c's entry d is broadcast first and every lane runs the pivot test
   // and the 1/sqrt chain on it (uniform: no divergence, no broadcast after
@@ -146,13 +160,23 @@ __device__ __forceinline__ void diag_chol_block(double* A, int64_t lda, Dim nd, 
     }
     return l;
   };
-  // column jn is final in a[0]: store it and shift the registers by one column
+  // column jn is final in a[0]: store it and shift the registers by one
+  // column; after the fourth, the high columns go back to lane = row
   auto retire = [&]() {
     if (jn < bw && lane < bw && lane >= jn) A[(k0 + lane) * lda + (k0 + jn)] = a[0];
 #pragma unroll
-    for (int q = 0; q < 7; ++q) a[q] = a[q + 1];
-    a[7] = 0.0;
+    for (int q = 0; q < 3; ++q) a[q] = a[q + 1];
+    a[3] = 0.0;
     jn += kDiagWarps;
+    if (packed && jn == w + 16) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const double lo = __shfl_sync(0xffffffffu, pk[h], (lane - 16) & 31);
+        a[2 * h] = lane >= 16 ? lo : 0.0;
+        a[2 * h + 1] = lane >= 16 ? pk[h] : 0.0;
+      }
+      packed = false;
+    }
   };
   bool timed_out = false;
   if (w == 0) {
@@ -175,11 +199,20 @@ __device__ __forceinline__ void diag_chol_block(double* A, int64_t lda, Dim nd, 
       col_publish(&colbar[nxt]);
       retire();
     }
-    // the update of column c on this warp's remaining columns
+    // the update of column c on this warp's remaining columns (the same
+    // operation on every entry, in the same order, packed or not)
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < 4; ++q) {
       const int j = jn + kDiagWarps * q;
-      if (j < bw && lane >= j) a[q] = fma(-li, colbuf[c][j], a[q]);
+      if (j < bw && lane >= j && (!packed || j < 16)) a[q] = fma(-li, colbuf[c][j], a[q]);
+    }
+    if (packed) {
+      const double lr = colbuf[c][prow];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int jp = w + 16 + 8 * h + (lane < 16 ? 0 : 4);
+        if (jp < bw && prow < bw && prow >= jp) pk[h] = fma(-lr, colbuf[c][jp], pk[h]);
+      }
     }
   }
   if (timed_out && lane == 0) atomicOr(&st->status, ST_TIMEOUT);
