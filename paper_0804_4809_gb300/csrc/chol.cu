@@ -148,7 +148,12 @@ __global__ void __launch_bounds__(1024) tri_block_inverse_kernel(const double* T
   }
   const int bw = (int)((r - k0) < b ? (r - k0) : b);
   __shared__ double Ts[32][33];
+  __shared__ double rinv[32];
   Ts[i][j] = (i < bw && j < bw && j <= i) ? T[(k0 + i) * ld + (k0 + j)] : 0.0;
+  __syncthreads();
+  // 1/T_kk for every k by one warp (an FP64 division is a long run of FP64
+  // instructions, each costing the same with one active lane as with 32)
+  if (j == 0) rinv[i] = i < bw ? 1.0 / Ts[i][i] : 0.0;
   __syncthreads();
   double w = 0.0;
   if (j < bw) {
@@ -156,7 +161,7 @@ __global__ void __launch_bounds__(1024) tri_block_inverse_kernel(const double* T
     double x = 0.0;
     for (int k = j; k < bw; ++k) {
       double v = 0.0;
-      if (i == k) v = ((k == j ? 1.0 : 0.0) - x) / Ts[k][k];
+      if (i == k) v = ((k == j ? 1.0 : 0.0) - x) * rinv[k];
       const double wk = __shfl_sync(0xffffffffu, v, k);
       if (i == k) w = wk;
       if (i > k) x = fma(Ts[i][k], wk, x);
