@@ -41,8 +41,8 @@ import math
 
 import numpy as np
 
-#: Appendix: ``tol = min(dA(dA>0))*1e-9`` -- absolute threshold relative to the
-#: smallest positive diagonal entry of A = G'G.
+#: Appendix: the pivot threshold is this factor times the smallest positive
+#: diagonal entry of A = G'G (an absolute threshold, not scaled by n or eps).
 REL_TOL = 1e-9
 
 
@@ -107,7 +107,7 @@ def gram(G: np.ndarray, exact: bool = True) -> np.ndarray:
 
     ``exact=True`` (default): each entry is the exact inner product of two
     columns rounded once (``exact_cross``).  ``exact=False``: the FP64 matrix
-    product with the library's own rounding order (Matlab's ``G'*G``).  The
+    product with the BLAS library's own rounding order.  The
     paper does not fix the rounding of G'G; the method's G+ moves by about
     1e-10 (relative) between two FP64 summation orders on rank-deficient
     Gaussian products, so the oracle takes the one rounding that does not
@@ -159,7 +159,8 @@ def full_rank_cholesky(A: np.ndarray, tol, literal: bool = False, keep=None):
     pivots = np.zeros(n, dtype=np.float64)
     r = 0
     for k in range(n):
-        # Matlab: L(k:n,r) = A(k:n,k) - L(k:n,1:(r-1))*L(k,1:(r-1))'
+        # candidate column k: column k of A minus the contribution of the r
+        # columns kept so far (left-looking update, Sec. 2 Eq. (1))
         v = A[k:, k] - L[k:, :r] @ L[k, :r]
         pivots[k] = v[0]
         if (keep[k] and v[0] > 0) if keep is not None else (tol is not None and v[0] > tol):
@@ -190,7 +191,7 @@ def geninv(G: np.ndarray, rel_tol: float = REL_TOL, literal: bool = False,
         raise ValueError("G must be 2-D")
     m, n = G.shape
     transpose = m < n
-    # Appendix: if m < n, A = G G' (and n := m); else A = G'G.
+    # Appendix: the wide case (m < n) factors G G' of order m instead.
     A = gram(G.T if transpose else G, exact=exact_gram)
     nA = A.shape[0]
     if nA == 0:

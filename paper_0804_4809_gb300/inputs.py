@@ -55,17 +55,35 @@ def paper_family(n: int, seed: int) -> np.ndarray:
     return rank_deficient(2 * n, n, (7 * n) // 8, seed, dist="uniform")
 
 
+def rbf_from_centres(X: np.ndarray, C: np.ndarray, width: float) -> np.ndarray:
+    """G_ij = exp(-|x_i - c_j|^2 / (2 w^2)), squared distances expanded as
+    |x|^2 + |c|^2 - 2 x.c and clamped at 0."""
+    d2 = (np.sum(X * X, axis=1)[:, None] + np.sum(C * C, axis=1)[None, :]
+          - 2.0 * (X @ C.T))
+    np.maximum(d2, 0.0, out=d2)
+    return np.ascontiguousarray(np.exp(-d2 / (2.0 * width * width)))
+
+
 def rbf_design(m: int, n: int, d: int, width: float, seed: int):
     """Gaussian RBF design matrix.  Returns (G, X, centre_index)."""
     g = _rng(seed)
     X = g.uniform(0.0, 1.0, (m, d))
     idx = np.sort(g.choice(m, size=n, replace=False))
-    C = X[idx]
-    d2 = (np.sum(X * X, axis=1)[:, None] + np.sum(C * C, axis=1)[None, :]
-          - 2.0 * (X @ C.T))
-    np.maximum(d2, 0.0, out=d2)
-    G = np.exp(-d2 / (2.0 * width * width))
-    return np.ascontiguousarray(G), X, idx
+    return rbf_from_centres(X, X[idx], width), X, idx
+
+
+def rbf_repeated_centres(m: int, n_distinct: int, n: int, d: int, width: float, seed: int):
+    """RBF design whose n centres repeat n_distinct distinct inputs (the
+    extra n - n_distinct columns are copies of earlier or later ones, in a
+    shuffled order).  A repeated centre gives an exactly repeated column, so
+    the rank is n_distinct with a wide pivot gap: every pivot is either of
+    the order of the data or at rounding level.  Returns (G, X, centre_index)."""
+    g = _rng(seed)
+    X = g.uniform(0.0, 1.0, (m, d))
+    base = np.sort(g.choice(m, size=n_distinct, replace=False))
+    idx = np.concatenate([base, g.choice(base, size=n - n_distinct, replace=True)])
+    g.shuffle(idx)
+    return rbf_from_centres(X, X[idx], width), X, idx
 
 
 def smooth_targets(X: np.ndarray, k: int, seed: int, noise: float = 1e-3) -> np.ndarray:
