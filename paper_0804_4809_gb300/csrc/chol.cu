@@ -70,7 +70,8 @@ __global__ void __launch_bounds__(chol::kDiagThreads) diag_chol_kernel(double* A
                                                                  const int64_t* rdev,
                                                                  uint8_t* accepted, double* dinv,
                                                                  int spd) {
-  chol::diag_chol_block(A, lda, nd, k0, b, st, rdev, accepted, dinv, spd);
+  __shared__ chol::DiagScratch sc;
+  chol::diag_chol_block(A, lda, nd, k0, b, st, rdev, accepted, dinv, spd, sc);
 }
 
 // One block per problem of a batch of equal-shaped problems (strides in
@@ -78,8 +79,10 @@ __global__ void __launch_bounds__(chol::kDiagThreads) diag_chol_kernel(double* A
 __global__ void __launch_bounds__(chol::kDiagThreads) diag_chol_batched_kernel(DiagBatch p) {
   const int64_t z = blockIdx.x;
   DevState* st = p.st + z;
+  __shared__ chol::DiagScratch sc;
   chol::diag_chol_block(p.A + z * p.zA, p.lda, p.nd, p.k0, p.b, st, &st->rank,
-                  p.accepted ? p.accepted + z * p.zAcc : nullptr, p.dinv + z * p.zDinv, p.spd);
+                        p.accepted ? p.accepted + z * p.zAcc : nullptr, p.dinv + z * p.zDinv,
+                        p.spd, sc);
 }
 
 // Rows below the diagonal block of panel k0: L(i, P) solves L(i, P) T' =

@@ -190,8 +190,17 @@ __global__ void __launch_bounds__(kPanelThreads, 4) chol_panel_exact_kernel(Pane
   const bool helper = p.has_update && blockIdx.x >= 1 && (int)blockIdx.x <= p.helpers;
   if (blockIdx.x > 0 && row0 >= n && !helper) return;  // nothing for this CTA
   __shared__ crt::CrtShared sh;
-  __shared__ double Ts[32][33];
-  __shared__ double dv[32];
+  // CTA 0 factors the diagonal block; the other CTAs solve their rows
+  // against it: the two phases' shared memory is one
+  __shared__ union {
+    chol::DiagScratch diag;
+    struct {
+      double Ts[32][33];
+      double dv[32];
+    } rows;
+  } u;
+  double(&Ts)[32][33] = u.rows.Ts;
+  double* dv = u.rows.dv;
   __shared__ int64_t Lt[kMaxLast][32];  // Lt[k][j]: scaled integer of L(k0 + j, kb + k)
   __shared__ int go;
   double* A = p.A;
@@ -342,7 +351,8 @@ __global__ void __launch_bounds__(kPanelThreads, 4) chol_panel_exact_kernel(Pane
       __syncthreads();
     }
     if (warp < chol::kDiagWarps)
-      chol::diag_chol_block(A, lda, p.nd, k0, p.b, p.st, p.rdev, p.accepted, p.dinv, p.spd);
+      chol::diag_chol_block(A, lda, p.nd, k0, p.b, p.st, p.rdev, p.accepted, p.dinv, p.spd,
+                            u.diag);
     // publish the block (factor and 1/T_cc written by warps 0-3) ...
     __threadfence();
     __syncthreads();
