@@ -65,8 +65,11 @@ extern "C" {
 
 typedef struct cpinv_opts {
   int32_t mode;      /* CPINV_MODE_* (default CPINV_MODE_FP64) */
-  int32_t slices;    /* exact-slice mode: number of 8-bit slices per operand,
-                        0 = default (7); ignored by the other modes */
+  int32_t slices;    /* reserved for the exact-slice mode, ignored: that mode
+                        picks its moduli count itself from the inner dimension
+                        and the operands' integer width (62 bits for the Gram
+                        matrix, 60 for the factorisation, 53 for the other
+                        products); any value is accepted */
   int32_t panel;     /* Cholesky panel width: 1, 2, 4, 8, 16 or 32; 0 = default (32) */
   int32_t reserved;  /* must be 0 */
   double rel_tol;    /* pivot threshold factor; default 1e-9 (Appendix) */
@@ -133,6 +136,42 @@ int cpinv_lstsq_gram(const double* A, int64_t n, int64_t lda, const double* B, i
                      int64_t ldb, double* W, int64_t ldw,
                      void* workspace, size_t workspace_bytes,
                      const cpinv_opts* o, int64_t* rank_out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Gaussian radial-basis design matrices (Sec. 1 and Sec. 4: an RBF network's
+ * output weights are W = G+ F for the design matrix G of its hidden layer):
+ *   G_ij = exp(-|x_i - c_j|^2 / (2 w^2)),
+ * the squared distance summed over the d coordinates in order (FP64, fused
+ * multiply-adds), the exponential in FP64.
+ *   X : m x d data (row-major, ldx >= d), C : n x d centres (ldc >= d),
+ *   width w > 0 and finite, 0 <= d <= CPINV_RBF_MAX_D (else
+ *   CPINV_ERR_UNSUPPORTED).  Device pointers.
+ * cpinv_rbf_design: G (m x n, ldg >= n) written to device memory.  Enqueues
+ *   only (non-finite X or C give non-finite G).
+ * cpinv_rbf_normal_equations: the normal equations of W = G+ F without G
+ *   in memory: A = G'G (n x n, lower triangle written, lda >= n) and, if F !=
+ *   NULL, B = G'F (n x k, ldb >= k; F m x k, ldf >= k), in the exact-slice
+ *   arithmetic (each chunk of at most 4096 rows of X summed exactly and
+ *   rounded once, chunks added in FP64 -- as cpinv_gram_update in that mode).
+ *   Each tile of G is generated in FP64 and cut into the tensor-core residue
+ *   planes directly.  Solve with cpinv_lstsq_gram.  Workspace:
+ *   cpinv_rbf_normal_equations_workspace_size(m, n, d, k) bytes, 256-byte
+ *   aligned.  `check` != 0 synchronizes the stream and reports
+ *   CPINV_ERR_NONFINITE_INPUT (NaN/Inf in X or C) and CPINV_ERR_NUMERICAL
+ *   (the per-centre scale bound did not cover an entry; not expected);
+ *   with check = 0 the call only enqueues.
+ * ------------------------------------------------------------------------- */
+#define CPINV_RBF_MAX_D 32
+int cpinv_rbf_design(const double* X, int64_t m, int64_t d, int64_t ldx,
+                     const double* C, int64_t n, int64_t ldc, double width,
+                     double* G, int64_t ldg, void* stream);
+size_t cpinv_rbf_normal_equations_workspace_size(int64_t m, int64_t n, int64_t d, int64_t k);
+int cpinv_rbf_normal_equations(const double* X, int64_t m, int64_t d, int64_t ldx,
+                               const double* C, int64_t n, int64_t ldc, double width,
+                               const double* F, int64_t k, int64_t ldf,
+                               double* A, int64_t lda, double* B, int64_t ldb,
+                               void* workspace, size_t workspace_bytes, int32_t check,
+                               void* stream);
 
 /* ---------------------------------------------------------------------------
  * Failure path of the device-side waits, exercised without a fault: one
@@ -267,12 +306,20 @@ int cpinv_matmul(int32_t transA, int32_t transB, int64_t M, int64_t N, int64_t K
  * keeps until the process exits.  No cudaMalloc, cudaFree or other allocating
  * routine is called.
  *   Limit: min(m, n) <= CPINV_STATIC_MAX_ORDER (128) and a workspace that fits
- *          in the array (cpinv_pinv_workspace_size(m, n, o) <= 1 MiB, true for
- *          every panel width at that order); larger inputs return
- *          CPINV_ERR_UNSUPPORTED before any GPU work.
+ *          in the array (cpinv_pinv_workspace_size(m, n, o) <= 1 MiB); larger
+ *          requests return CPINV_ERR_UNSUPPORTED before any GPU work.  In
+ *          practice that means CPINV_MODE_FP64: it fits for every order up
+ *          to 128 and every panel width.  CPINV_MODE_EXACT_SLICE never fits
+ *          (the residue buffers of its tensor-core Gram product alone exceed
+ *          1 MiB, even for a 40 x 20 input) and CPINV_MODE_SPLIT_BF16X3 fits
+ *          only for orders of about 32 and below; both are refused with
+ *          CPINV_ERR_UNSUPPORTED when they do not fit.
  *   Set-up: the first call on each device looks up the array's device address
- *          (cudaGetSymbolAddress) with that device current; make that first
- *          call before any stream capture begins.
+ *          (cudaGetSymbolAddress) with that device current and keeps it for
+ *          later calls on that device; make that first call before any stream
+ *          capture begins.  The address belongs to the device's context: do
+ *          not reset the device (cudaDeviceReset) between calls in one
+ *          process, or later calls would launch kernels on a stale address.
  *   Sharing: all calls on a device use the same array, which keeps whatever
  *          the last call left in it (each call clears the state it needs).
  *          Calls that overlap on the GPU -- on different streams, or from

@@ -101,6 +101,13 @@ SIGNATURES = {
                                     ctypes.c_double, _c_vp, _c_i64, _c_vp, _c_i64, ctypes.c_double,
                                     _c_vp, _c_i64, ctypes.c_int32, ctypes.c_int32, _c_vp, _c_sz,
                                     ctypes.c_int32, _c_vp]),
+    "cpinv_rbf_design": (ctypes.c_int, [_c_vp, _c_i64, _c_i64, _c_i64, _c_vp, _c_i64, _c_i64,
+                                        ctypes.c_double, _c_vp, _c_i64, _c_vp]),
+    "cpinv_rbf_normal_equations_workspace_size": (_c_sz, [_c_i64, _c_i64, _c_i64, _c_i64]),
+    "cpinv_rbf_normal_equations": (ctypes.c_int, [_c_vp, _c_i64, _c_i64, _c_i64, _c_vp, _c_i64,
+                                                  _c_i64, ctypes.c_double, _c_vp, _c_i64, _c_i64,
+                                                  _c_vp, _c_i64, _c_vp, _c_i64, _c_vp, _c_sz,
+                                                  ctypes.c_int32, _c_vp]),
     "cpinv_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "cpinv_profile_read": (ctypes.c_int, [ctypes.POINTER(ProfileEntry), ctypes.c_int]),
     "cpinv_profile_timeline": (ctypes.c_int, [ctypes.POINTER(TimelineEntry), ctypes.c_int]),
@@ -275,6 +282,59 @@ def lstsq_gram(A: torch.Tensor, B: torch.Tensor, mode="fp64", rel_tol: float = 1
                                 ctypes.byref(r), _stream(A.device))
     _check(st)
     return W, int(r.value)
+
+
+def rbf_design(X: torch.Tensor, C: torch.Tensor, width: float,
+               out: torch.Tensor | None = None) -> torch.Tensor:
+    """Gaussian RBF design matrix G_ij = exp(-|x_i - c_j|^2 / (2 width^2)),
+    m x n, computed on the GPU (``cpinv_rbf_design``)."""
+    X = _mat(X, "X")
+    C = _mat(C, "C")
+    m, d = X.shape
+    n = C.shape[0]
+    if C.shape[1] != d:
+        raise ValueError("X and C must have the same number of columns")
+    G = out if out is not None else torch.empty((m, n), dtype=torch.float64, device=X.device)
+    if G.shape != (m, n) or not G.is_contiguous() or G.dtype != torch.float64:
+        raise ValueError("out must be a contiguous float64 m x n tensor")
+    st = lib().cpinv_rbf_design(X.data_ptr(), m, d, _ld(X), C.data_ptr(), n, _ld(C),
+                                float(width), G.data_ptr(), n, _stream(X.device))
+    _check(st)
+    return G
+
+
+def rbf_normal_equations(X: torch.Tensor, C: torch.Tensor, width: float,
+                         F: torch.Tensor | None = None, A: torch.Tensor | None = None,
+                         B: torch.Tensor | None = None, check: bool = True):
+    """A = G'G (lower triangle) and, with F, B = G'F for the RBF design
+    matrix G of (X, C, width), without G in memory (exact-slice arithmetic,
+    ``cpinv_rbf_normal_equations``).  Returns (A, B)."""
+    X = _mat(X, "X")
+    C = _mat(C, "C")
+    m, d = X.shape
+    n = C.shape[0]
+    k = 0
+    if F is not None:
+        F = _mat(F, "F")
+        k = F.shape[1]
+        if F.shape[0] != m:
+            raise ValueError("F must have m rows")
+    if A is None:
+        A = torch.zeros((n, n), dtype=torch.float64, device=X.device)
+    if F is not None and B is None:
+        B = torch.zeros((n, k), dtype=torch.float64, device=X.device)
+    nbytes = lib().cpinv_rbf_normal_equations_workspace_size(m, n, d, k)
+    if nbytes == 0:
+        raise CpinvError(6, "unsupported sizes")
+    ws = _workspace(nbytes, X.device)
+    st = lib().cpinv_rbf_normal_equations(
+        X.data_ptr(), m, d, _ld(X), C.data_ptr(), n, _ld(C), float(width),
+        F.data_ptr() if F is not None else None, k, _ld(F) if F is not None else 1,
+        A.data_ptr(), _ld(A), B.data_ptr() if B is not None else None,
+        _ld(B) if B is not None else 1, ws.data_ptr(), ws.numel(), 1 if check else 0,
+        _stream(X.device))
+    _check(st)
+    return A, B
 
 
 def selftest_wait_timeout(device=None) -> int:
