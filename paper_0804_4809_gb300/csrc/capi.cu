@@ -57,8 +57,8 @@ double gemm_flops(const Dim& Md, const Dim& Nd, const Dim& Kd, int lower, int64_
 // ---------------------------------------------------------------------------
 // Tracing: events around every launch (when enabled) and a launch counter.
 // ---------------------------------------------------------------------------
-const char* const kKindName[KT_COUNT] = {"gemm_fp64", "tc_mma", "diag_factor",
-                                         "aux",       "split",  "crt_reconstruct"};
+const char* const kKindName[KT_COUNT] = {"gemm_fp64", "tc_mma",          "diag_factor", "aux",
+                                         "split",     "crt_reconstruct", "chol_panel"};
 
 struct TraceRec {
   cudaEvent_t e0, e1;
@@ -601,8 +601,20 @@ int factor_exact(const Ctx& c, double* a, int64_t lda, int spd) {
       p.diag_shares += pp.helpers;
       pp.diag_target = p.diag_shares;
     }
-    CK(diag_timer(c, k0, b, spd).run(KT_DIAG, c.s,
-                                     [&] { return launch_chol_panel_exact(pp, c.s); }));
+    // traced work of the fused launch, in FP64-equivalent flops: for the
+    // rows k0 .. n of the panel (its diagonal block included), the exact sum
+    // over the last k0 - kb columns (2 per term) and the forward substitution
+    // against the block (b per entry) -- 2 (n - k0) b (k0 - kb + b / 2) --
+    // which covers the block's own b^3/3 factorisation as well; the bulk
+    // columns 0 .. kb are the look-ahead product's work
+    DiagTimer pt;
+    std::memset(&pt.g, 0, sizeof(pt.g));
+    pt.g.M = spd ? rdim(-k0, nA - k0) : hdim(nA - k0);
+    pt.g.N = hdim(nA - k0 < b ? nA - k0 : b);
+    pt.g.K = hdim(k0 - kb + b / 2);
+    pt.g.rdev = c.rdev();
+    pt.t.flops_mult = 1.0;
+    CK(pt.run(KT_PANEL, c.s, [&] { return launch_chol_panel_exact(pp, c.s); }));
     CK(cudaEventRecord(side->done[pi % kSideEvents], c.s));
   }
   // join the second stream back

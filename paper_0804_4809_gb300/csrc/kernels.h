@@ -20,7 +20,8 @@ enum : int {
   KT_AUX = 3,        // small O(n^2) kernels
   KT_SPLIT = 4,      // residue split of the operands
   KT_RECON = 5,      // CRT reconstruction
-  KT_COUNT = 6
+  KT_PANEL = 6,      // chol_panel_exact_kernel (fused panel of the exact factorisation)
+  KT_COUNT = 7
 };
 
 void trace_count();
@@ -37,7 +38,9 @@ struct KernelTimer {
     if (!trace_on()) return f();
     const int rec = trace_begin(s);
     cudaError_t e = f();
-    trace_end(rec, s, kind, kind == KT_MMA || kind == KT_GEMM_FP64 || kind == KT_DIAG ? gemm : nullptr,
+    trace_end(rec, s, kind,
+              kind == KT_MMA || kind == KT_GEMM_FP64 || kind == KT_DIAG || kind == KT_PANEL ? gemm
+                                                                                          : nullptr,
               flops_mult);
     return e;
   }

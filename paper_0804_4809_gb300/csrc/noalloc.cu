@@ -12,7 +12,14 @@
 // (1 MiB).  Every GPU that loads the library holds it until the process exits.
 // Host code may not use the array's name as a device address (on the host it
 // is only a stand-in), so the first call on each device looks the real address
-// up with cudaGetSymbolAddress, with that device current, and caches it.
+// up with cudaGetSymbolAddress, with that device current, and caches it.  The
+// cached address is only valid for the context it was looked up in: a device
+// reset between calls makes it stale (documented in the header).
+//
+// Only the FP64 mode fits in the array at every order up to 128; the
+// exact-slice mode's tensor-core residue buffers exceed it at any size, so
+// those calls (and BF16x3 calls above order ~32) are refused by the size
+// check before any GPU work.
 #include <cstdint>
 #include <mutex>
 #include <unordered_map>
