@@ -761,6 +761,24 @@ def rbf_and_adjoint_bench(args, device, flush, steps: int = 3) -> dict:
         _, _, _, r = cpinv.lstsq_backward(G2d, F2d, dW, mode=md)
         ms = time_steps(lambda: cpinv.lstsq_backward(G2d, F2d, dW, mode=md), steps, flush, s)
         out["adjoint"][md] = {"ms": round(sum(ms) / steps, 3), "rank": r}
+
+        # a training step: the forward W = G+ F and the reverse pass, either
+        # sharing the factors (cpinv_lstsq_forward + ..._backward_from_state,
+        # as LstsqFunction does) or recomputing them (cpinv_lstsq, then
+        # cpinv_lstsq_backward)
+        def saved():
+            _, _, state = cpinv.lstsq_forward(G2d, F2d, mode=md)
+            cpinv.lstsq_backward_from_state(G2d, F2d, dW, state, mode=md)
+
+        def recompute():
+            cpinv.lstsq(G2d, F2d, mode=md, sync_rank=False)
+            cpinv.lstsq_backward(G2d, F2d, dW, mode=md)
+        saved()
+        recompute()
+        ms_s = time_steps(saved, steps, flush, s)
+        ms_r = time_steps(recompute, steps, flush, s)
+        out["adjoint"][md]["train_step_saved_factors_ms"] = round(sum(ms_s) / steps, 3)
+        out["adjoint"][md]["train_step_recomputed_factors_ms"] = round(sum(ms_r) / steps, 3)
     return out
 
 

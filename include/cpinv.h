@@ -212,6 +212,34 @@ int cpinv_lstsq_backward(const double* G, int64_t m, int64_t n, int64_t ldg,
                          const cpinv_opts* o, int64_t* rank_out, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * The same adjoint without recomputing the forward pass (training loops:
+ * the forward W = G+ F and the reverse pass share the factors).
+ * cpinv_lstsq_forward: W = G+ F as cpinv_lstsq, and leaves the forward
+ *   factors -- L, M = (L'L)^-1, the kept-pivot mask and index, the rank --
+ *   in `state`, a caller-owned device buffer of cpinv_lstsq_state_size(m,
+ *   n, k, o) bytes (256-byte aligned).  Requires m >= n and m, n, k >= 1
+ *   (else CPINV_ERR_UNSUPPORTED).
+ * cpinv_lstsq_backward_from_state: dG (and dF if non-NULL) for the
+ *   cotangent dW, as cpinv_lstsq_backward, reading the factors from
+ *   `state` instead of factoring again.  G, F, the sizes, the options and
+ *   the state must be those of the forward call, and the state must not
+ *   have been touched since (the call reads and overwrites its scratch part,
+ *   so one forward serves one reverse pass).
+ * ------------------------------------------------------------------------- */
+size_t cpinv_lstsq_state_size(int64_t m, int64_t n, int64_t k, const cpinv_opts* o);
+int cpinv_lstsq_forward(const double* G, int64_t m, int64_t n, int64_t ldg,
+                        const double* F, int64_t k, int64_t ldf,
+                        double* W, int64_t ldw, void* state, size_t state_bytes,
+                        const cpinv_opts* o, int64_t* rank_out, void* stream);
+int cpinv_lstsq_backward_from_state(const double* G, int64_t m, int64_t n, int64_t ldg,
+                                    const double* F, int64_t k, int64_t ldf,
+                                    const double* dW, int64_t lddw,
+                                    double* dG, int64_t lddg, double* dF, int64_t lddf,
+                                    void* state, size_t state_bytes,
+                                    const cpinv_opts* o, int64_t* rank_out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched least squares/* ---------------------------------------------------------------------------
  * Batched least squares: W_p = G_p+ F_p for P independent problems of
  * uneven size (Theorem 1 and the Appendix applied to each problem on its
  * own, with its own tolerance and rank), all enqueued on `stream` as one

@@ -79,6 +79,15 @@ SIGNATURES = {
                                             _c_vp, _c_i64, _c_vp, _c_i64, _c_vp, _c_i64, _c_vp,
                                             _c_i64, _c_vp, _c_sz, ctypes.POINTER(Opts),
                                             ctypes.POINTER(_c_i64), _c_vp]),
+    "cpinv_lstsq_state_size": (_c_sz, [_c_i64, _c_i64, _c_i64, ctypes.POINTER(Opts)]),
+    "cpinv_lstsq_forward": (ctypes.c_int, [_c_vp, _c_i64, _c_i64, _c_i64, _c_vp, _c_i64, _c_i64,
+                                           _c_vp, _c_i64, _c_vp, _c_sz, ctypes.POINTER(Opts),
+                                           ctypes.POINTER(_c_i64), _c_vp]),
+    "cpinv_lstsq_backward_from_state": (ctypes.c_int, [_c_vp, _c_i64, _c_i64, _c_i64, _c_vp,
+                                                       _c_i64, _c_i64, _c_vp, _c_i64, _c_vp,
+                                                       _c_i64, _c_vp, _c_i64, _c_vp, _c_sz,
+                                                       ctypes.POINTER(Opts),
+                                                       ctypes.POINTER(_c_i64), _c_vp]),
     "cpinv_selftest_wait_timeout": (ctypes.c_int, [_c_vp, _c_sz, _c_vp]),
     "cpinv_gram_update_workspace_size": (_c_sz, [_c_i64, _c_i64, _c_i64, ctypes.c_int32]),
     "cpinv_gram_update": (ctypes.c_int, [_c_vp, _c_i64, _c_i64, _c_i64, _c_vp, _c_i64, _c_i64,
@@ -377,17 +386,75 @@ def lstsq_backward(G: torch.Tensor, F: torch.Tensor, dW: torch.Tensor, mode="fp6
     return dG, dF, W, int(r.value)
 
 
+def lstsq_forward(G: torch.Tensor, F: torch.Tensor, mode="fp64", rel_tol: float = 1e-9,
+                  panel: int = 0):
+    """W = G+ F (m >= n) keeping the forward factors for a later reverse
+    pass (``cpinv_lstsq_forward``).  Returns (W, rank, state); the state is
+    a device buffer for ``lstsq_backward_from_state``."""
+    G = _mat(G, "G")
+    F = _mat(F, "F")
+    m, n = G.shape
+    k = F.shape[1]
+    if F.shape[0] != m:
+        raise ValueError("F must have m rows")
+    o = make_opts(mode, rel_tol, panel)
+    nbytes = lib().cpinv_lstsq_state_size(m, n, k, ctypes.byref(o))
+    if nbytes == 0:
+        raise CpinvError(1, "invalid options or sizes")
+    state = _workspace(nbytes, G.device)
+    W = torch.empty((n, k), dtype=torch.float64, device=G.device)
+    r = _c_i64(-1)
+    st = lib().cpinv_lstsq_forward(G.data_ptr(), m, n, _ld(G), F.data_ptr(), k, _ld(F),
+                                   W.data_ptr(), _ld(W), state.data_ptr(), state.numel(),
+                                   ctypes.byref(o), ctypes.byref(r), _stream(G.device))
+    _check(st)
+    return W, int(r.value), state
+
+
+def lstsq_backward_from_state(G: torch.Tensor, F: torch.Tensor, dW: torch.Tensor,
+                              state: torch.Tensor, mode="fp64", rel_tol: float = 1e-9,
+                              panel: int = 0, need_dF: bool = True):
+    """The adjoint of W = G+ F from the factors ``lstsq_forward`` kept
+    (``cpinv_lstsq_backward_from_state``): returns (dG, dF or None, rank)."""
+    G = _mat(G, "G")
+    F = _mat(F, "F")
+    dW = _mat(dW, "dW")
+    m, n = G.shape
+    k = F.shape[1]
+    if F.shape[0] != m or tuple(dW.shape) != (n, k):
+        raise ValueError("shapes: G m x n, F m x k, dW n x k")
+    o = make_opts(mode, rel_tol, panel)
+    dG = torch.empty((m, n), dtype=torch.float64, device=G.device)
+    dF = torch.empty((m, k), dtype=torch.float64, device=G.device) if need_dF else None
+    r = _c_i64(-1)
+    st = lib().cpinv_lstsq_backward_from_state(
+        G.data_ptr(), m, n, _ld(G), F.data_ptr(), k, _ld(F), dW.data_ptr(), _ld(dW),
+        dG.data_ptr(), _ld(dG), dF.data_ptr() if dF is not None else None,
+        _ld(dF) if dF is not None else max(k, 1), state.data_ptr(), state.numel(),
+        ctypes.byref(o), ctypes.byref(r), _stream(G.device))
+    _check(st)
+    return dG, dF, int(r.value)
+
+
 class LstsqFunction(torch.autograd.Function):
-    """W = G+ F as a differentiable op: forward through cpinv_lstsq, backward
-    through the hand-written adjoint cpinv_lstsq_backward (kept-pivot set held
-    fixed)."""
+    """W = G+ F as a differentiable op: forward through cpinv_lstsq_forward,
+    which keeps the factors L, (L'L)^-1, the kept-pivot set and the rank, and
+    backward through the hand-written adjoint from those factors
+    (cpinv_lstsq_backward_from_state; kept-pivot set held fixed), so a
+    training step factors once.  Wide G (m < n) goes through cpinv_lstsq and
+    the recomputing adjoint's error (unsupported)."""
 
     @staticmethod
     def forward(ctx, G, F, mode="fp64", rel_tol=1e-9):
-        W, r = lstsq(G, F, mode=mode, rel_tol=rel_tol)
-        ctx.save_for_backward(G, F)
         ctx.mode = mode
         ctx.rel_tol = rel_tol
+        if G.shape[0] >= G.shape[1] > 0 and F.shape[1] > 0:
+            W, r, state = lstsq_forward(G, F, mode=mode, rel_tol=rel_tol)
+            ctx.state = state
+        else:
+            W, r = lstsq(G, F, mode=mode, rel_tol=rel_tol)
+            ctx.state = None
+        ctx.save_for_backward(G, F)
         ctx.rank = r
         return W
 
@@ -397,8 +464,14 @@ class LstsqFunction(torch.autograd.Function):
         need_G, need_F = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
         if not (need_G or need_F):
             return None, None, None, None
-        dG, dF, _, _ = lstsq_backward(G, F, dW.contiguous(), mode=ctx.mode, rel_tol=ctx.rel_tol,
-                                      need_dF=need_F)
+        if ctx.state is not None:
+            dG, dF, _ = lstsq_backward_from_state(G, F, dW.contiguous(), ctx.state,
+                                                  mode=ctx.mode, rel_tol=ctx.rel_tol,
+                                                  need_dF=need_F)
+            ctx.state = None  # one reverse pass per forward
+        else:
+            dG, dF, _, _ = lstsq_backward(G, F, dW.contiguous(), mode=ctx.mode,
+                                          rel_tol=ctx.rel_tol, need_dF=need_F)
         return (dG if need_G else None), dF, None, None
 
 

@@ -124,7 +124,15 @@ void trace_end(int rec, cudaStream_t s, int kind, const GemmParams* g, double mu
 
 namespace {
 
-enum Job { JOB_RANK = 0, JOB_PINV = 1, JOB_LSTSQ = 2, JOB_BACKWARD = 3, JOB_GRAM_LSTSQ = 4 };
+enum Job {
+  JOB_RANK = 0,
+  JOB_PINV = 1,
+  JOB_LSTSQ = 2,
+  JOB_BACKWARD = 3,
+  JOB_GRAM_LSTSQ = 4,
+  JOB_FORWARD_SAVE = 5,     // W = G+ F, factors kept in a backward-sized state
+  JOB_BACKWARD_STATE = 6,   // the reverse pass from that state
+};
 
 struct Plan {
   int64_t m, n, nA, k;
@@ -915,11 +923,15 @@ GraphKey make_key(int job, const Plan& p, int64_t ld1, int64_t ld2, int64_t ld3,
 }
 
 // Runs body(ctx) on `user` directly, or captured / replayed as a graph.
+// keep_state: the call continues from the DevState a previous call left in
+// the workspace (the reverse pass from a saved forward state), so it is not
+// cleared.
 template <class Body>
-int run_pipeline(const Plan& p, cudaStream_t user, const GraphKey& key, Body&& body) {
+int run_pipeline(const Plan& p, cudaStream_t user, const GraphKey& key, Body&& body,
+                 bool keep_state = false) {
   auto direct = [&]() -> int {
     Ctx c{user, &p};
-    CK(cudaMemsetAsync(p.st, 0, sizeof(DevState), user));
+    if (!keep_state) CK(cudaMemsetAsync(p.st, 0, sizeof(DevState), user));
     p.diag_shares = 0;
     return body(c);
   };
@@ -958,8 +970,9 @@ int run_pipeline(const Plan& p, cudaStream_t user, const GraphKey& key, Body&& b
     CK(cudaStreamBeginCapture(side, cudaStreamCaptureModeThreadLocal));
     Ctx c{side, &p};
     p.diag_shares = 0;
-    int rc = cudaMemsetAsync(p.st, 0, sizeof(DevState), side) == cudaSuccess ? body(c)
-                                                                               : CPINV_ERR_CUDA;
+    int rc = (keep_state || cudaMemsetAsync(p.st, 0, sizeof(DevState), side) == cudaSuccess)
+                 ? body(c)
+                 : CPINV_ERR_CUDA;
     cudaGraph_t graph = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(side, &graph);
     if (rc != CPINV_OK || ce != cudaSuccess) {
@@ -1377,6 +1390,78 @@ int cpinv_lstsq_backward(const double* G, int64_t m, int64_t n, int64_t ldg, con
     if (int r = front_inverse(c)) return r;
     return backward_body(c, G, ldg, F, ldf, dW, lddw, dG, lddg, dF, lddf, W, ldw);
   });
+  if (rc) return rc;
+  return finish(Ctx{us, &p}, rank_out);
+}
+
+size_t cpinv_lstsq_state_size(int64_t m, int64_t n, int64_t k, const cpinv_opts* o) {
+  return cpinv_lstsq_backward_workspace_size(m, n, k, o);
+}
+
+int cpinv_lstsq_forward(const double* G, int64_t m, int64_t n, int64_t ldg, const double* F,
+                        int64_t k, int64_t ldf, double* W, int64_t ldw, void* state,
+                        size_t state_bytes, const cpinv_opts* o, int64_t* rank_out,
+                        void* stream) {
+  if (rank_out) *rank_out = -1;
+  if (int rc = check_opts(o)) return rc;
+  if (m < 0 || n < 0 || k < 0 || ldg < n || ldf < k || ldw < k) return CPINV_ERR_INVALID_ARG;
+  if (m < n) return CPINV_ERR_UNSUPPORTED;
+  if (m == 0 || n == 0 || k == 0) return CPINV_ERR_UNSUPPORTED;  // nothing to differentiate
+  if (!G || !F || !W) return CPINV_ERR_INVALID_ARG;
+  Plan p{};
+  if (!make_plan(p, m, n, k, o)) return CPINV_ERR_INVALID_ARG;
+  if (int rc = begin(p, JOB_BACKWARD, state, state_bytes)) return rc;
+  cudaStream_t us = (cudaStream_t)stream;
+  const GraphKey key = make_key(JOB_FORWARD_SAVE, p, ldg, ldf, ldw, G, F, W, state, state_bytes);
+  int rc = run_pipeline(p, us, key, [&](const Ctx& c) -> int {
+    if (int r = front_rank(c, G, ldg, true)) return r;
+    if (int r = front_inverse(c)) return r;
+    const int64_t nA = p.nA;
+    const Dim R = rdim(0, nA);
+    // W = L (M (M (L' (G'F)))), as cpinv_lstsq (m >= n)
+    CK(matmul(c, S_CHAIN, G, ldg, true, F, ldf, false, p.c1, k, hdim(n), hdim(k), hdim(m), 1.0,
+              0.0, 0));
+    CK(matmul(c, S_CHAIN, p.bufL, nA, true, p.c1, k, false, p.c2, k, R, hdim(k), hdim(nA), 1.0,
+              0.0, 0));
+    CK(matmul(c, S_CHAIN, p.bufM, nA, false, p.c2, k, false, p.c3, k, R, hdim(k), R, 1.0, 0.0, 0));
+    CK(matmul(c, S_CHAIN, p.bufM, nA, false, p.c3, k, false, p.c2, k, R, hdim(k), R, 1.0, 0.0, 0));
+    CK(matmul(c, S_CHAIN, p.bufL, nA, false, p.c2, k, false, W, ldw, hdim(n), hdim(k), R, 1.0, 0.0,
+              0));
+    return CPINV_OK;
+  });
+  if (rc) return rc;
+  return finish(Ctx{us, &p}, rank_out);
+}
+
+int cpinv_lstsq_backward_from_state(const double* G, int64_t m, int64_t n, int64_t ldg,
+                                    const double* F, int64_t k, int64_t ldf, const double* dW,
+                                    int64_t lddw, double* dG, int64_t lddg, double* dF,
+                                    int64_t lddf, void* state, size_t state_bytes,
+                                    const cpinv_opts* o, int64_t* rank_out, void* stream) {
+  if (rank_out) *rank_out = -1;
+  if (int rc = check_opts(o)) return rc;
+  if (m < 0 || n < 0 || k < 0 || ldg < n || ldf < k || lddw < k || lddg < n ||
+      (dF && lddf < k))
+    return CPINV_ERR_INVALID_ARG;
+  if (m < n || m == 0 || n == 0 || k == 0) return CPINV_ERR_UNSUPPORTED;
+  if (!G || !F || !dW || !dG) return CPINV_ERR_INVALID_ARG;
+  Plan p{};
+  if (!make_plan(p, m, n, k, o)) return CPINV_ERR_INVALID_ARG;
+  if (int rc = begin(p, JOB_BACKWARD, state, state_bytes)) return rc;
+  cudaStream_t us = (cudaStream_t)stream;
+  GraphKey key = make_key(JOB_BACKWARD_STATE, p, ldg, ldf, lddw, G, F, dW, state, state_bytes);
+  key.ld4 = lddg;
+  key.ld5 = dF ? lddf : 0;
+  key.p4 = dG;
+  key.p5 = dF;
+  // L, M, the kept mask, the kept index of each pivot and the rank are the
+  // forward call's, in the state: only the reverse pass runs
+  int rc = run_pipeline(
+      p, us, key,
+      [&](const Ctx& c) -> int {
+        return backward_body(c, G, ldg, F, ldf, dW, lddw, dG, lddg, dF, lddf, nullptr, 0);
+      },
+      /*keep_state=*/true);
   if (rc) return rc;
   return finish(Ctx{us, &p}, rank_out);
 }

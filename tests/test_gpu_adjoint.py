@@ -210,3 +210,50 @@ def test_autograd_rbf_loss_full_size(mode):
     err = rel(g, g_x)
     print(f"c5 {mode}: rank {int(keep.sum())}, rel err vs oracle {err:.3e}, bar {bar:.3e}")
     assert err <= bar, (err, bar)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("name", ["rank_deficient", "early_dependent", "full_rank", "tiles"])
+def test_backward_from_saved_state_equals_recomputing_adjoint(name, mode):
+    """cpinv_lstsq_forward keeps L, (L'L)^-1, the kept set and the rank;
+    cpinv_lstsq_backward_from_state then runs the reverse pass alone.  The
+    factors are those the recomputing adjoint forms again, so both give the
+    same W, dG and dF (same kernels, same inputs)."""
+    cp = _cp()
+    G, F, dW = CASES[name]()
+    Gd, Fd, dWd = to_dev(G), to_dev(F), to_dev(dW)
+    W_s, r_s, state = cp.lstsq_forward(Gd, Fd, mode=mode)
+    dG_s, dF_s, r_b = cp.lstsq_backward_from_state(Gd, Fd, dWd, state, mode=mode)
+    dG, dF, W, r = cp.lstsq_backward(Gd, Fd, dWd, mode=mode, need_W=True)
+    assert r_s == r_b == r
+    assert rel(W_s.cpu().numpy(), W.cpu().numpy()) <= 1e-14
+    assert rel(dG_s.cpu().numpy(), dG.cpu().numpy()) <= 1e-13
+    assert rel(dF_s.cpu().numpy(), dF.cpu().numpy()) <= 1e-13
+    # and against the oracle's adjoint
+    _, dG_o, dF_o = lstsq_vjp(G, F, dW)
+    assert rel(dG_s.cpu().numpy(), dG_o) <= 1e-8
+
+
+def test_saved_state_zero_matrix_and_autograd_uses_it():
+    cp = _cp()
+    Gd = to_dev(np.zeros((6, 4)))
+    Fd = to_dev(np.ones((6, 2)))
+    W, r, state = cp.lstsq_forward(Gd, Fd, mode="fp64")
+    assert r == 0 and float(W.abs().max()) == 0.0
+    dG, dF, _ = cp.lstsq_backward_from_state(Gd, Fd, to_dev(np.ones((4, 2))), state)
+    assert float(dG.abs().max()) == 0.0 and float(dF.abs().max()) == 0.0
+    # the autograd Function goes through the saved state: one forward launch
+    # sequence and one reverse pass (fewer kernels than forward + recompute)
+    G, F, _ = CASES["tiles"]()
+    Gd = to_dev(G).requires_grad_(True)
+    n0 = cp.launch_count()
+    W = cp.lstsq_autograd(Gd, to_dev(F), mode="exact")
+    W.sum().backward()
+    torch.cuda.synchronize()
+    used = cp.launch_count() - n0
+    Gd2 = to_dev(G)
+    n1 = cp.launch_count()
+    cp.lstsq(Gd2, to_dev(F), mode="exact")
+    cp.lstsq_backward(Gd2, to_dev(F), torch.ones_like(W), mode="exact")
+    torch.cuda.synchronize()
+    assert used < cp.launch_count() - n1
