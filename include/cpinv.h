@@ -243,15 +243,21 @@ int cpinv_lstsq_backward_from_state(const double* G, int64_t m, int64_t n, int64
  * Batched least squares: W_p = G_p+ F_p for P independent problems of
  * uneven size (Theorem 1 and the Appendix applied to each problem on its
  * own, with its own tolerance and rank), all enqueued on `stream` as one
- * batch.  Every problem is computed in FP64 arithmetic.
+ * batch.  Problems are grouped by n (rounded up to 128); every stage is one
+ * launch per group.  Arithmetic: CPINV_MODE_FP64, or CPINV_MODE_EXACT_SLICE,
+ * in which the Gram matrices G_p'G_p and the products L_p'L_p of a group are
+ * one block-diagonal tensor-core residue product each (every entry the exact
+ * sum rounded once; requires m <= 4096) and the rest is FP64.
  *   probs : HOST array of P descriptors; G, F, W in each are DEVICE pointers
  *           (row-major, as for cpinv_lstsq).  Requires 1 <= n <= m,
  *           n <= CPINV_BATCHED_MAX_N, 1 <= k <= CPINV_BATCHED_MAX_K,
  *           m <= CPINV_BATCHED_MAX_M (else CPINV_ERR_UNSUPPORTED).
- *   o     : mode must be CPINV_MODE_FP64 (else CPINV_ERR_UNSUPPORTED); panel
- *           0 (chosen by timing both candidates on the first call of each
- *           bucket shape; set CPINV_TUNE_FILE to a path to keep the choices
- *           as JSON lines), 16 or 32; rel_tol as for cpinv_lstsq.
+ *   o     : mode CPINV_MODE_FP64 or CPINV_MODE_EXACT_SLICE (else
+ *           CPINV_ERR_UNSUPPORTED); panel 0 (chosen by timing the candidates
+ *           on the first call of each group shape), 16 or 32; in the
+ *           exact-slice mode the residue products' tile width (128 or 256
+ *           columns) is tuned the same way.  Set CPINV_TUNE_FILE to a path to
+ *           keep the choices as JSON lines.  rel_tol as for cpinv_lstsq.
  *   ranks_out, status_out : HOST arrays of P entries, or NULL.  If either
  *           is non-NULL the call synchronizes `stream` and writes each
  *           problem's rank r_p (-1 on failure) and CPINV_* status; the

@@ -486,16 +486,18 @@ class BatchedLstsq:
     The descriptor array, the outputs and the workspace are built once, so
     repeated calls with the same tensors replay one CUDA graph of the whole
     batch.  ``Gs``/``Fs`` are lists of CUDA float64 matrices (m_p x n_p with
-    n_p <= m_p, and m_p x k_p)."""
+    n_p <= m_p, and m_p x k_p).  ``mode``: "fp64", or "exact" (the Gram and
+    L'L products of every problem on the tensor cores, exactly summed and
+    rounded once; m_p <= 4096)."""
 
-    def __init__(self, Gs, Fs, rel_tol: float = 1e-9, panel: int = 0):
+    def __init__(self, Gs, Fs, rel_tol: float = 1e-9, panel: int = 0, mode="fp64"):
         if len(Gs) != len(Fs):
             raise ValueError("Gs and Fs differ in length")
         self.Gs = [_mat(G, "G") for G in Gs]
         self.Fs = [_mat(F, "F") for F in Fs]
         self.P = len(self.Gs)
         self.device = self.Gs[0].device if self.P else torch.device("cuda")
-        self.opts = make_opts("fp64", rel_tol, panel)
+        self.opts = make_opts(mode, rel_tol, panel)
         self.Ws = []
         self.probs = (Problem * max(self.P, 1))()
         for i, (G, F) in enumerate(zip(self.Gs, self.Fs)):
@@ -529,9 +531,9 @@ class BatchedLstsq:
         return self.Ws, [int(self.ranks[i]) for i in range(self.P)], statuses
 
 
-def lstsq_batched(Gs, Fs, rel_tol: float = 1e-9, panel: int = 0):
+def lstsq_batched(Gs, Fs, rel_tol: float = 1e-9, panel: int = 0, mode="fp64"):
     """One batched call: returns (Ws, ranks, statuses) (see ``BatchedLstsq``)."""
-    return BatchedLstsq(Gs, Fs, rel_tol, panel)()
+    return BatchedLstsq(Gs, Fs, rel_tol, panel, mode)()
 
 
 def profile_enable(on: bool = True) -> bool:

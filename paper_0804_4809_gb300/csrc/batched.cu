@@ -221,9 +221,16 @@ struct Bucket {
   int64_t mp, np, kp;
   std::vector<int> ids;
   int b;
+  int bn;       // exact mode: output tile width of the residue products (128 or 256)
   double work;  // flop estimate, for spreading buckets over streams
   size_t off_desc, off_G, off_F, off_A, off_L, off_W, off_M, off_T, off_Z, off_acc, off_st,
       off_c1, off_c2, off_c3, off_Wp;
+  // exact mode: the Gram and L'L of every problem as one block-diagonal
+  // residue product each (planes of all problems stacked, then the products)
+  bool exact;
+  int nmod_g, nmod_l;      // moduli of the Gram (62-bit G) and of L'L (53-bit L)
+  int64_t kpad_g, kpad_l;  // K of those products, padded to the planes' block
+  size_t off_EG, off_EL, off_S, off_R;
 };
 
 struct Layout {
@@ -231,7 +238,11 @@ struct Layout {
   size_t off_ranks, off_status, total;
 };
 
-Layout make_layout(int P, const cpinv_problem* probs) {
+constexpr int kGramBits = 62;  // integer width of G in the exact Gram (as the single problem)
+constexpr int kProdBits = 53;  // ... of L in L'L
+constexpr int64_t kExactMaxM = 4096;  // one exact residue product: K <= 4096
+
+Layout make_layout(int P, const cpinv_problem* probs, bool exact) {
   Layout L;
   std::map<int64_t, size_t> where;  // n bucket -> the bucket being filled
   for (int i = 0; i < P; ++i) {
@@ -251,6 +262,8 @@ Layout make_layout(int P, const cpinv_problem* probs) {
       L.buckets.push_back(b);
     }
     Bucket& b = L.buckets[it->second];
+    b.exact = exact;
+    b.bn = 128;
     b.ids.push_back(i);
     b.mp = std::max<int64_t>(b.mp, probs[i].m);
     b.kp = std::max<int64_t>(b.kp, probs[i].k);
@@ -283,6 +296,21 @@ Layout make_layout(int P, const cpinv_problem* probs) {
     b.off_c2 = take(8 * nz * np * kp);
     b.off_c3 = take(8 * nz * np * kp);
     b.off_Wp = take(8 * nz * np * kp);
+    if (b.exact) {
+      const int64_t bk = crt_block_k();
+      b.kpad_g = round_up(b.mp, bk);
+      b.kpad_l = round_up(b.np, bk);
+      b.nmod_g = crt_moduli_for(b.mp, kGramBits, kGramBits);
+      b.nmod_l = crt_moduli_for(b.np, kProdBits, kProdBits);
+      const size_t rows = nz * np;
+      const size_t sg = 2 * (size_t)b.nmod_g * rows * (size_t)b.kpad_g;
+      const size_t sl = 2 * (size_t)b.nmod_l * rows * (size_t)b.kpad_l;
+      const int nmax = b.nmod_g > b.nmod_l ? b.nmod_g : b.nmod_l;
+      b.off_EG = take(4 * rows);
+      b.off_EL = take(4 * rows);
+      b.off_S = take(sg > sl ? sg : sl);
+      b.off_R = take((size_t)nmax * rows * np);
+    }
   }
   L.off_ranks = take(sizeof(int64_t) * (size_t)std::max(P, 1));
   L.off_status = take(sizeof(int32_t) * (size_t)std::max(P, 1));
@@ -448,6 +476,40 @@ int bucket_tri_inverse(cudaStream_t s, const Bucket& bk, char* ws, int b) {
   return CPINV_OK;
 }
 
+// C_z = X_z' X_z (lower triangle) for every problem z of the bucket in the
+// exact-slice arithmetic: X_z = X + z zX (ld np, the n x K operand's rows
+// are the columns of X_z: `rows` of them, K = `K` rows of X_z, both read
+// per problem), the residue planes of all problems stacked along M, one
+// block-diagonal tensor-core product (np x np blocks), one reconstruction
+// into C (z-major np x np).  Each entry is the exact sum rounded once.
+int exact_gram_batched(cudaStream_t s, const Bucket& bk, char* ws, const double* X, int64_t zX,
+                       Dim rows, Dim K, int64_t kpad, int n_mod, int beta, int32_t* E,
+                       double* C) {
+  const int nz = (int)bk.ids.size();
+  const int64_t np = bk.np, tot = (int64_t)nz * np;
+  DevState* st = (DevState*)(ws + bk.off_st);
+  void* S = ws + bk.off_S;
+  uint8_t* R = (uint8_t*)(ws + bk.off_R);
+  const int64_t zR = (int64_t)(sizeof(DevState) / sizeof(int64_t));
+  KernelTimer t;
+  BK_CHECK(cudaMemsetAsync(E, 0, sizeof(int32_t) * (size_t)tot, s));
+  BK_CHECK(crt_row_exponents_batched(X, np, 1, rows, K, &st->rank, np, E, st, nz, zX, zR, np, s,
+                                     &t));
+  BK_CHECK(crt_split_batched(X, np, 1, rows, K, &st->rank, np, kpad, E, n_mod, beta, S, nz, zX, zR,
+                             s, &t));
+  GemmParams fl;  // traced work: nz lower products np x np x K
+  std::memset(&fl, 0, sizeof(fl));
+  fl.M = fl.N = hdim(np);
+  fl.K = hdim(K.max * nz);
+  fl.lower = 1;
+  fl.rdev = &st->rank;
+  BK_CHECK(crt_mma(S, tot, 0, S, tot, 0, kpad, K.max, n_mod, hdim(tot), hdim(tot), &st->rank, 1, R,
+                   tot, np, &st->status, s, &t, &fl, 0, (int)np, bk.bn));
+  BK_CHECK(crt_reconstruct(R, tot, np, hdim(tot), hdim(np), &st->rank, E, E, beta, beta, 1.0, 0.0,
+                           C, np, 1, n_mod, s, &t, (int)np));
+  return CPINV_OK;
+}
+
 // The whole least-squares pipeline for one bucket, on stream s.
 int run_bucket(cudaStream_t s, const Bucket& bk, char* ws, double rel_tol, int b,
                int64_t* ranks_dev, int32_t* status_dev) {
@@ -482,8 +544,14 @@ int run_bucket(cudaStream_t s, const Bucket& bk, char* ws, double rel_tol, int b
     return cudaGetLastError();
   }));
   // A = G'G (lower), the tolerance, the full-rank Cholesky, compaction to L
-  BK_CHECK(BGemm(nz, st).a(Gp, np, zg, true).b(Gp, np, zg, false).c(A, np, zz).dims(Nn, Nn, Mr)
-               .run(s, 1.0, 0.0, 1));
+  if (bk.exact) {
+    if (int rc = exact_gram_batched(s, bk, ws, Gp, zg, Nn, Mr, bk.kpad_g, bk.nmod_g, kGramBits,
+                                    (int32_t*)(ws + bk.off_EG), A))
+      return rc;
+  } else {
+    BK_CHECK(BGemm(nz, st).a(Gp, np, zg, true).b(Gp, np, zg, false).c(A, np, zz).dims(Nn, Nn, Mr)
+                 .run(s, 1.0, 0.0, 1));
+  }
   BK_CHECK(t.run(KT_AUX, s, [&] {
     tol_batched_kernel<<<nz, 256, 0, s>>>(A, np, rel_tol, st);
     return cudaGetLastError();
@@ -494,8 +562,14 @@ int run_bucket(cudaStream_t s, const Bucket& bk, char* ws, double rel_tol, int b
     return cudaGetLastError();
   }));
   // N = L'L, N = U U', W = U^-1, M = W'W = N^-1
-  BK_CHECK(BGemm(nz, st).a(L, np, zz, true).b(L, np, zz, false).c(A, np, zz).dims(R, R, Nn)
-               .run(s, 1.0, 0.0, 1));
+  if (bk.exact) {
+    if (int rc = exact_gram_batched(s, bk, ws, L, zz, R, Nn, bk.kpad_l, bk.nmod_l, kProdBits,
+                                    (int32_t*)(ws + bk.off_EL), A))
+      return rc;
+  } else {
+    BK_CHECK(BGemm(nz, st).a(L, np, zz, true).b(L, np, zz, false).c(A, np, zz).dims(R, R, Nn)
+                 .run(s, 1.0, 0.0, 1));
+  }
   if (int rc = bucket_factor(s, bk, ws, 1, b)) return rc;
   BK_CHECK(t.run(KT_AUX, s, [&] {
     tri_inv_init_batched_kernel<<<dim3(g1(np * np, 256, 64), (unsigned)nz), 256, 0, s>>>(
@@ -533,9 +607,13 @@ int run_bucket(cudaStream_t s, const Bucket& bk, char* ws, double rel_tol, int b
 // CPINV_TUNE_FILE set, choices are read from and appended to that file as
 // JSON lines {"key": "...", "panel": b}.
 // ---------------------------------------------------------------------------
+struct Tuned {
+  int panel;
+  int bn;
+};
 struct Tuner {
   std::mutex mu;
-  std::map<std::string, int> best;
+  std::map<std::string, Tuned> best;
   bool loaded = false;
   std::string file;
 
@@ -544,8 +622,9 @@ struct Tuner {
     std::memset(&prop, 0, sizeof(prop));
     cudaGetDeviceProperties(&prop, device);
     char buf[320];
-    std::snprintf(buf, sizeof(buf), "%s|sm%d%d|fp64|n%lld|m%lld|k%lld|p%zu", prop.name, prop.major,
-                  prop.minor, (long long)b.np, (long long)b.mp, (long long)b.kp, b.ids.size());
+    std::snprintf(buf, sizeof(buf), "%s|sm%d%d|%s|n%lld|m%lld|k%lld|p%zu", prop.name, prop.major,
+                  prop.minor, b.exact ? "exact" : "fp64", (long long)b.np, (long long)b.mp,
+                  (long long)b.kp, b.ids.size());
     return buf;
   }
   void load() {
@@ -560,21 +639,24 @@ struct Tuner {
     while (std::fgets(line, sizeof(line), fp)) {
       const char* k = std::strstr(line, "\"key\": \"");
       const char* pn = std::strstr(line, "\"panel\": ");
+      const char* bn = std::strstr(line, "\"bn\": ");
       if (!k || !pn) continue;
       k += 8;
       const char* e = std::strchr(k, '"');
       if (!e) continue;
       const int b = std::atoi(pn + 9);
-      if (b == 16 || b == 32) best[std::string(k, e)] = b;
+      const int t = bn ? std::atoi(bn + 6) : 128;
+      if ((b == 16 || b == 32) && (t == 128 || t == 256)) best[std::string(k, e)] = Tuned{b, t};
     }
     std::fclose(fp);
   }
-  void store(const std::string& k, int b) {
-    best[k] = b;
+  void store(const std::string& k, Tuned v) {
+    best[k] = v;
     if (file.empty()) return;
     FILE* fp = std::fopen(file.c_str(), "a");
     if (!fp) return;
-    std::fprintf(fp, "{\"key\": \"%s\", \"panel\": %d}\n", k.c_str(), b);
+    std::fprintf(fp, "{\"key\": \"%s\", \"panel\": %d, \"bn\": %d}\n", k.c_str(), v.panel,
+                 v.bn);
     std::fclose(fp);
   }
 };
@@ -625,20 +707,32 @@ int choose_panels(Layout& L, char* ws, double rel_tol, int panel, bool measure, 
   int32_t* status_dev = (int32_t*)(ws + L.off_status);
   for (auto& bk : L.buckets) {
     bk.b = panel ? panel : 32;
-    if (panel) continue;
+    bk.bn = 128;
     const std::string k = Tuner::key(bk, device);
     auto it = g_tuner.best.find(k);
     if (it != g_tuner.best.end()) {
-      bk.b = it->second;
+      bk.b = panel ? panel : it->second.panel;
+      bk.bn = it->second.bn;
       continue;
     }
     if (!measure) continue;
+    // candidates: panel width 16 / 32 (unless given) x, in the exact mode,
+    // the residue products' tile width 128 / 256 (256 when it divides n_pad)
+    std::vector<Tuned> cands;
+    for (int pb : {16, 32}) {
+      if (panel && pb != panel) continue;
+      cands.push_back(Tuned{pb, 128});
+      if (bk.exact && bk.np % 256 == 0) cands.push_back(Tuned{pb, 256});
+    }
+    if (cands.size() == 1) continue;
     cudaEvent_t e0, e1;
     BK_CHECK(cudaEventCreate(&e0));
     BK_CHECK(cudaEventCreate(&e1));
     float best_ms = 0.f;
-    int best_b = 32;
-    for (int cand : {16, 32}) {
+    Tuned best = cands[0];
+    for (size_t ci = 0; ci < cands.size(); ++ci) {
+      bk.bn = cands[ci].bn;
+      const int cand = cands[ci].panel;
       // one untimed run (first launches load modules), one timed
       if (int rc = run_bucket(s, bk, ws, rel_tol, cand, ranks_dev, status_dev)) return rc;
       BK_CHECK(cudaEventRecord(e0, s));
@@ -647,15 +741,16 @@ int choose_panels(Layout& L, char* ws, double rel_tol, int panel, bool measure, 
       BK_CHECK(cudaEventSynchronize(e1));
       float ms = 0.f;
       BK_CHECK(cudaEventElapsedTime(&ms, e0, e1));
-      if (cand == 16 || ms < best_ms) {
+      if (ci == 0 || ms < best_ms) {
         best_ms = ms;
-        best_b = cand;
+        best = cands[ci];
       }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    bk.b = best_b;
-    g_tuner.store(k, best_b);
+    bk.b = best.panel;
+    bk.bn = best.bn;
+    g_tuner.store(k, best);
   }
   return CPINV_OK;
 }
@@ -699,7 +794,7 @@ uint64_t g_bclock = 0;
 constexpr size_t kMaxBatchGraphs = 8;
 
 std::vector<int64_t> batch_key(int P, const cpinv_problem* probs, void* ws, size_t ws_bytes,
-                               double rel_tol, int panel) {
+                               double rel_tol, int panel, int mode) {
   std::vector<int64_t> k;
   k.reserve(8 + 9 * (size_t)P);
   int device = 0;
@@ -707,7 +802,7 @@ std::vector<int64_t> batch_key(int P, const cpinv_problem* probs, void* ws, size
   int64_t tol_bits;
   std::memcpy(&tol_bits, &rel_tol, sizeof(tol_bits));
   k.insert(k.end(), {(int64_t)device, (int64_t)(uintptr_t)ws, (int64_t)ws_bytes, tol_bits,
-                     (int64_t)panel, (int64_t)P});
+                     (int64_t)panel, (int64_t)mode, (int64_t)P});
   for (int i = 0; i < P; ++i) {
     const cpinv_problem& q = probs[i];
     k.insert(k.end(), {q.m, q.n, q.k, (int64_t)(uintptr_t)q.G, q.ldg, (int64_t)(uintptr_t)q.F,
@@ -732,8 +827,9 @@ int upload_descriptors(const Layout& L, const cpinv_problem* probs, char* ws, cu
 }
 
 int batched_enqueue(int P, const cpinv_problem* probs, char* ws, size_t ws_bytes, double rel_tol,
-                    int panel, cudaStream_t s) {
-  Layout L = make_layout(P, probs);
+                    int panel, int mode, cudaStream_t s) {
+  Layout L = make_layout(P, probs, mode == CPINV_MODE_EXACT_SLICE);
+  if (mode == CPINV_MODE_EXACT_SLICE && !crt_consts_device()) return CPINV_ERR_CUDA;
   DeviceStreams* d = nullptr;
   if (int rc = device_streams(&d)) return rc;
   if (int rc = upload_descriptors(L, probs, ws, s)) return rc;
@@ -742,7 +838,7 @@ int batched_enqueue(int P, const cpinv_problem* probs, char* ws, size_t ws_bytes
     return run_all(L, d, ws, rel_tol, s);
   }
   std::lock_guard<std::mutex> lock(g_bgraph_mu);
-  std::vector<int64_t> key = batch_key(P, probs, ws, ws_bytes, rel_tol, panel);
+  std::vector<int64_t> key = batch_key(P, probs, ws, ws_bytes, rel_tol, panel, mode);
   BatchGraph* e = nullptr;
   for (auto& x : g_bgraphs)
     if (x.key == key) e = &x;
@@ -790,8 +886,11 @@ int batched_enqueue(int P, const cpinv_problem* probs, char* ws, size_t ws_bytes
   return CPINV_OK;
 }
 
-int check_problems(int P, const cpinv_problem* probs) {
+int check_problems(int P, const cpinv_problem* probs, int mode) {
   if (P < 0 || (P > 0 && !probs)) return CPINV_ERR_INVALID_ARG;
+  if (mode == CPINV_MODE_EXACT_SLICE)
+    for (int i = 0; i < P; ++i)
+      if (probs[i].m > kExactMaxM) return CPINV_ERR_UNSUPPORTED;
   for (int i = 0; i < P; ++i) {
     const cpinv_problem& q = probs[i];
     if (q.m < 1 || q.n < 1 || q.k < 1) return CPINV_ERR_INVALID_ARG;
@@ -804,16 +903,18 @@ int check_problems(int P, const cpinv_problem* probs) {
   return CPINV_OK;
 }
 
-int check_opts(const cpinv_opts* o, double* rel_tol, int* panel) {
+int check_opts(const cpinv_opts* o, double* rel_tol, int* panel, int* mode) {
   cpinv_opts d;
   cpinv_default_opts(&d);
   if (!o) o = &d;
   if (o->reserved != 0) return CPINV_ERR_INVALID_ARG;
   if (!(o->rel_tol >= 0.0) || !std::isfinite(o->rel_tol)) return CPINV_ERR_INVALID_ARG;
   if (o->panel != 0 && o->panel != 16 && o->panel != 32) return CPINV_ERR_INVALID_ARG;  // tuned set
-  if (o->mode != CPINV_MODE_FP64) return CPINV_ERR_UNSUPPORTED;
+  if (o->mode != CPINV_MODE_FP64 && o->mode != CPINV_MODE_EXACT_SLICE)
+    return CPINV_ERR_UNSUPPORTED;
   *rel_tol = o->rel_tol;
   *panel = o->panel;
+  *mode = o->mode;
   return CPINV_OK;
 }
 
@@ -827,10 +928,10 @@ extern "C" {
 size_t cpinv_lstsq_batched_workspace_size(int32_t P, const cpinv_problem* probs,
                                           const cpinv_opts* o) {
   double rel_tol;
-  int panel;
-  if (check_problems(P, probs) != CPINV_OK || check_opts(o, &rel_tol, &panel) != CPINV_OK)
+  int panel, mode;
+  if (check_opts(o, &rel_tol, &panel, &mode) != CPINV_OK || check_problems(P, probs, mode) != CPINV_OK)
     return 0;
-  return make_layout(P, probs).total;
+  return make_layout(P, probs, mode == CPINV_MODE_EXACT_SLICE).total;
 }
 
 int cpinv_lstsq_batched(int32_t P, const cpinv_problem* probs, int64_t* ranks_out,
@@ -839,16 +940,16 @@ int cpinv_lstsq_batched(int32_t P, const cpinv_problem* probs, int64_t* ranks_ou
   for (int i = 0; i < P && ranks_out; ++i) ranks_out[i] = -1;
   for (int i = 0; i < P && status_out; ++i) status_out[i] = CPINV_ERR_INVALID_ARG;
   double rel_tol;
-  int panel;
-  if (int rc = check_problems(P, probs)) return rc;
-  if (int rc = check_opts(o, &rel_tol, &panel)) return rc;
+  int panel, mode;
+  if (int rc = check_opts(o, &rel_tol, &panel, &mode)) return rc;
+  if (int rc = check_problems(P, probs, mode)) return rc;
   if (P == 0) return CPINV_OK;
-  const Layout L = make_layout(P, probs);
+  const Layout L = make_layout(P, probs, mode == CPINV_MODE_EXACT_SLICE);
   if (!workspace || ((uintptr_t)workspace & 255u) || ws_bytes < L.total)
     return CPINV_ERR_WORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
   char* ws = (char*)workspace;
-  if (int rc = batched_enqueue(P, probs, ws, ws_bytes, rel_tol, panel, s)) return rc;
+  if (int rc = batched_enqueue(P, probs, ws, ws_bytes, rel_tol, panel, mode, s)) return rc;
   if (!ranks_out && !status_out) return CPINV_OK;
   std::vector<int64_t> r((size_t)P);
   std::vector<int32_t> st((size_t)P);

@@ -143,8 +143,18 @@ __device__ __forceinline__ bool nonfinite_bits(uint64_t b) { return ((b >> 52) &
 // trans = 0: row i is contiguous (X[i*ld + k]); one warp per row.
 // trans = 1: row i of op(X) is column i of X; a 32-row x 8-chunk block,
 //            coalesced over i, each thread scanning a slice of k.
+// Batches (grid z): operand z at X + z zX, its dims read at rdev + z zR,
+// its state st + z zSt, its exponents E + z zE.
 __global__ void row_expo_kernel(const double* X, int64_t ld, int trans, Dim rowsd, Dim colsd,
-                                const int64_t* rdev, int32_t* E, DevState* st) {
+                                const int64_t* rdev, int32_t* E, DevState* st, int64_t zX,
+                                int64_t zR, int64_t zE, int64_t zSt) {
+  {
+    const int64_t z = blockIdx.z;
+    X += z * zX;
+    rdev += z * zR;
+    E += z * zE;
+    st += z * zSt;
+  }
   const int64_t rows = eval_dim(rowsd, rdev), cols = eval_dim(colsd, rdev);
   int emax = 0, bad = 0;
   int64_t i;
@@ -208,13 +218,23 @@ __device__ __forceinline__ void split_store8_all(std::integer_sequence<int, Js..
   (split_store8<Js>(c, ng, n_mod, dst, plane_vec), ...);
 }
 
+// Batches (grid z): operand z at X + z zX, dims at rdev + z zR, its rows
+// z zrow onwards in the planes (and in E); plane_rows = rows of one plane.
 __global__ void __launch_bounds__(256) split_kernel(const double* X, int64_t ld, int trans,
                                                     Dim rowsd, Dim colsd, int64_t rows_max,
                                                     int64_t kpad, const int64_t* rdev,
                                                     const int32_t* E, int n_mod, int beta,
-                                                    bf16* out) {
+                                                    bf16* out, int64_t zX, int64_t zR,
+                                                    int64_t zrow, int64_t plane_rows) {
   // rows padded to 66 words: 16-byte aligned, four banks apart
   __shared__ __align__(16) uint64_t tile[32][66];
+  {
+    const int64_t z = blockIdx.z;
+    X += z * zX;
+    rdev += z * zR;
+    E += z * zrow;
+    out += z * zrow * kpad;
+  }
   const int64_t rows = eval_dim(rowsd, rdev), cols = eval_dim(colsd, rdev);
   const int64_t i0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 64;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
@@ -256,7 +276,7 @@ __global__ void __launch_bounds__(256) split_kernel(const double* X, int64_t ld,
   }
   uint4* dst = reinterpret_cast<uint4*>(out + (size_t)i * kpad + k0 + 8 * g);
   split_store8_all(std::make_integer_sequence<int, crt::kMaxMod>{}, c, ng, n_mod, dst,
-                   (size_t)rows_max * (size_t)kpad / 8);
+                   (size_t)plane_rows * (size_t)kpad / 8);
 }
 
 // Split precision: the row of op(X) scaled by 2^(1022 - E[i]) (|x| < 1), then
@@ -417,6 +437,10 @@ struct MmaParams {
   int32_t tiles;             // tiles in the enumeration (the lower ones only when lower)
   int32_t pad_t;
   int32_t lower;            // skip tiles strictly above the diagonal
+  int32_t blk;              // > 0: block-diagonal output of blocks blk x blk (batched Gram
+                            // matrices); tiles and lower refer to one block, R holds
+                            // [n_mod][Mpad][blk] (the block's own columns)
+  int32_t tiles_blk;        // tiles per block
   uint8_t* R;               // residues [n_mod][Mpad][Npad]
   int64_t Mpad, Npad;
   int32_t* status;          // DevState::status
@@ -497,7 +521,13 @@ __global__ void __launch_bounds__(192, 1)
   auto job = [&](int jj, int64_t& m0, int64_t& n0, int& j) -> bool {
     const int64_t q = (int64_t)blockIdx.x + (int64_t)jj * G;
     j = (int)(q / p.tiles);
-    const int t = (int)(q - (int64_t)j * p.tiles);
+    int t = (int)(q - (int64_t)j * p.tiles);
+    int64_t base = 0;  // block-diagonal mode: first row and column of the block
+    if (p.blk) {
+      const int zb = t / p.tiles_blk;
+      t -= zb * p.tiles_blk;
+      base = (int64_t)zb * p.blk;
+    }
     int ty, tx;
     if (!p.lower) {
       ty = t / p.tiles_n;
@@ -516,7 +546,10 @@ __global__ void __launch_bounds__(192, 1)
     }
     m0 = (int64_t)ty * BM;
     n0 = (int64_t)tx * BN;
-    return m0 < M && n0 < N && !(p.lower && n0 > m0 + BM - 1);
+    const bool upper = p.lower && n0 > m0 + BM - 1;
+    m0 += base;
+    n0 += base;
+    return m0 < M && n0 < N && !upper;
   };
 
   if (threadIdx.x == 0) {
@@ -658,7 +691,9 @@ __global__ void __launch_bounds__(192, 1)
         for (int t = 0; t < crt::kMaxMod; ++t)
           if (t == j) pj = crt::modulus(t);
         const float pfl = (float)pj, inv = 1.0f / (float)pj;
-        uint8_t* out = p.R + ((size_t)j * p.Mpad + row) * p.Npad + n0;
+        // block-diagonal mode: the block's own column n0 - base
+        const int64_t nc = p.blk ? n0 - (m0 / p.blk) * p.blk : n0;
+        uint8_t* out = p.R + ((size_t)j * p.Mpad + row) * p.Npad + nc;
   #pragma unroll 1
         for (int c = 0; c < BN; c += 32) {
           uint32_t v[32];
@@ -712,7 +747,9 @@ struct ReconParams {
   double* C;
   int64_t ldc;
   int32_t lower;
-  int32_t pad;
+  int32_t blk;  // > 0: block-diagonal output (reconstruct_words_kernel only): row i
+                // belongs to block i / blk, its columns j are the block's own
+                // (EB[(i / blk) blk + j]), lower is within the block
 };
 
 // CRT constants of every moduli count, in device memory (uploaded once per
@@ -918,7 +955,9 @@ __global__ void __launch_bounds__(256) reconstruct_words_kernel(ReconParams p, i
   const int64_t M = eval_dim(p.M, p.rdev), N = eval_dim(p.N, p.rdev);
   const int64_t i = (int64_t)blockIdx.y * kRecWRows + (threadIdx.x >> 5);
   const int64_t j0 = (int64_t)blockIdx.x * kRecWCols + 4 * (threadIdx.x & 31);
-  if (i >= M || j0 >= N || (p.lower && j0 > i)) return;
+  const int64_t il = p.blk ? i % p.blk : i;       // row within its block
+  const int32_t* EB = p.blk ? p.EB + (i - il) : p.EB;
+  if (i >= M || j0 >= N || (p.lower && j0 > il)) return;
   const size_t plane = (size_t)p.Mpad * (size_t)p.Npad;
   const uint32_t* r = reinterpret_cast<const uint32_t*>(p.R + i * p.Npad + j0);
   uint64_t acc[4][NL];
@@ -954,7 +993,7 @@ __global__ void __launch_bounds__(256) reconstruct_words_kernel(ReconParams p, i
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     const int64_t j = j0 + e;
-    if (j >= N || (p.lower && j > i)) continue;
+    if (j >= N || (p.lower && j > il)) continue;
     // S = sum_j t_j P/p_j (< n P) as (s2:s1:s0)
     uint32_t Sl[6];
     uint64_t carry = 0;
@@ -989,7 +1028,7 @@ __global__ void __launch_bounds__(256) reconstruct_words_kernel(ReconParams p, i
       x1 = m1;
       x0 = m0;
     }
-    double v = u192_to_double(neg, NL > 4 ? x2 : 0, x1, x0, sa + p.EB[j] - 1022 - p.betaB);
+    double v = u192_to_double(neg, NL > 4 ? x2 : 0, x1, x0, sa + EB[j] - 1022 - p.betaB);
     double* cp = p.C + i * p.ldc + j;
     if (!plain_store(p.alpha, p.beta)) v = scale_add(v, p.alpha, p.beta, cp);
     *cp = v;
@@ -1106,8 +1145,10 @@ bool make_map(CUtensorMap* map, const bf16* base, int64_t kpad, int64_t rows, in
 template <int BN, int STAGES, bool S3>
 cudaError_t launch_mma(const CUtensorMap& ta, CUtensorMap const& tb, MmaParams& mp,
                        int64_t Mmax, int64_t Nmax, int64_t wave, cudaStream_t s) {
-  mp.tiles_m = (int32_t)((Mmax + BM - 1) / BM);
-  mp.tiles_n = (int32_t)((Nmax + BN - 1) / BN);
+  // block-diagonal mode: the tiles of one blk x blk block, times the blocks
+  const int64_t bm = mp.blk ? mp.blk : Mmax, bn = mp.blk ? mp.blk : Nmax;
+  mp.tiles_m = (int32_t)((bm + BM - 1) / BM);
+  mp.tiles_n = (int32_t)((bn + BN - 1) / BN);
   int64_t tiles = 0;
   if (!mp.lower) {
     tiles = (int64_t)mp.tiles_m * mp.tiles_n;
@@ -1117,6 +1158,12 @@ cudaError_t launch_mma(const CUtensorMap& ta, CUtensorMap const& tb, MmaParams& 
       tiles += cnt < mp.tiles_n ? cnt : mp.tiles_n;
     }
   }
+  if (mp.blk) {
+    if (mp.blk % BM || mp.blk % BN || Mmax % mp.blk || Nmax != Mmax) return cudaErrorInvalidValue;
+    mp.tiles_blk = (int32_t)tiles;
+    tiles *= Mmax / mp.blk;
+  }
+  if (tiles > INT32_MAX) return cudaErrorInvalidValue;
   mp.tiles = (int32_t)tiles;
   const int64_t jobs = tiles * mp.n_mod;
   const int64_t ctas = jobs < wave ? jobs : wave;
@@ -1174,13 +1221,23 @@ size_t crt_workspace_bytes(int64_t Mmax, int64_t Nmax, int64_t Kmax, int n_mod, 
 cudaError_t crt_row_exponents(const double* X, int64_t ld, int tview, Dim rows, Dim K,
                               const int64_t* rdev, int64_t rows_max, int32_t* E, DevState* st,
                               cudaStream_t s, KernelTimer* timer) {
+  return crt_row_exponents_batched(X, ld, tview, rows, K, rdev, rows_max, E, st, 1, 0, 0, 0, s,
+                                   timer);
+}
+
+cudaError_t crt_row_exponents_batched(const double* X, int64_t ld, int tview, Dim rows, Dim K,
+                                      const int64_t* rdev, int64_t rows_max, int32_t* E,
+                                      DevState* st, int nz, int64_t zX, int64_t zR, int64_t zE,
+                                      cudaStream_t s, KernelTimer* timer) {
+  if (nz < 1 || nz > 65535) return cudaErrorInvalidValue;
+  const int64_t zSt = nz > 1 ? 1 : 0;
   return timer->run(KT_SPLIT, s, [&] {
     if (!tview)
-      row_expo_kernel<<<(unsigned)((rows_max * 32 + 255) / 256), 256, 0, s>>>(X, ld, 0, rows, K,
-                                                                             rdev, E, st);
+      row_expo_kernel<<<dim3((unsigned)((rows_max * 32 + 255) / 256), 1, (unsigned)nz), 256, 0,
+                        s>>>(X, ld, 0, rows, K, rdev, E, st, zX, zR, zE, zSt);
     else
-      row_expo_kernel<<<dim3((unsigned)((rows_max + 31) / 32), 16), 256, 0, s>>>(X, ld, 1, rows, K,
-                                                                                rdev, E, st);
+      row_expo_kernel<<<dim3((unsigned)((rows_max + 31) / 32), 16, (unsigned)nz), 256, 0, s>>>(
+          X, ld, 1, rows, K, rdev, E, st, zX, zR, zE, zSt);
     return cudaGetLastError();
   });
 }
@@ -1188,10 +1245,20 @@ cudaError_t crt_row_exponents(const double* X, int64_t ld, int tview, Dim rows, 
 cudaError_t crt_split(const double* X, int64_t ld, int tview, Dim rows, Dim K, const int64_t* rdev,
                       int64_t rows_max, int64_t kpad, const int32_t* E, int n_mod, int beta,
                       void* out, cudaStream_t s, KernelTimer* timer) {
-  dim3 grid((unsigned)(kpad / 64), (unsigned)((rows_max + 31) / 32));
+  return crt_split_batched(X, ld, tview, rows, K, rdev, rows_max, kpad, E, n_mod, beta, out, 1, 0,
+                           0, s, timer);
+}
+
+cudaError_t crt_split_batched(const double* X, int64_t ld, int tview, Dim rows, Dim K,
+                              const int64_t* rdev, int64_t rows_max, int64_t kpad,
+                              const int32_t* E, int n_mod, int beta, void* out, int nz,
+                              int64_t zX, int64_t zR, cudaStream_t s, KernelTimer* timer) {
+  if (nz < 1 || nz > 65535 || rows_max % 32) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)(kpad / 64), (unsigned)((rows_max + 31) / 32), (unsigned)nz);
+  const int64_t zrow = nz > 1 ? rows_max : 0;
   return timer->run(KT_SPLIT, s, [&] {
     split_kernel<<<grid, 256, 0, s>>>(X, ld, tview, rows, K, rows_max, kpad, rdev, E, n_mod, beta,
-                                      (bf16*)out);
+                                      (bf16*)out, zX, zR, zrow, rows_max * nz);
     return cudaGetLastError();
   });
 }
@@ -1200,10 +1267,12 @@ cudaError_t crt_mma(const void* SA, int64_t a_rows, int a_row0, const void* SB, 
                     int b_row0, int64_t kpad, int64_t kuse, int n_mod, Dim M, Dim N,
                     const int64_t* rdev, int lower, uint8_t* R, int64_t Mpad, int64_t Npad,
                     int32_t* status, cudaStream_t s, KernelTimer* timer, const GemmParams* fl,
-                    int max_ctas) {
+                    int max_ctas, int blk, int bn) {
   const int64_t Mmax = M.max, Nmax = N.max;
   if (Mmax <= 0 || Nmax <= 0) return cudaSuccess;
-  const int BN = (Nmax >= 2048) ? 256 : (Nmax <= 32 ? 32 : 128);
+  int BN = (Nmax >= 2048) ? 256 : (Nmax <= 32 ? 32 : 128);
+  if (blk) BN = (bn == 256 && blk % 256 == 0) ? 256 : 128;  // a tile never leaves its block
+  else if (bn == 128 || bn == 256) BN = bn;
   CUtensorMap ta, tb;
   if (!make_map(&ta, (const bf16*)SA, kpad, a_rows, n_mod, BM)) return cudaErrorInvalidValue;
   if (!make_map(&tb, (const bf16*)SB, kpad, b_rows, n_mod, BN)) return cudaErrorInvalidValue;
@@ -1218,6 +1287,7 @@ cudaError_t crt_mma(const void* SA, int64_t a_rows, int a_row0, const void* SB, 
   if (mp.nk < 1) mp.nk = 1;
   mp.n_mod = n_mod;
   mp.lower = lower;
+  mp.blk = blk;
   mp.R = R;
   mp.Mpad = Mpad;
   mp.Npad = Npad;
@@ -1259,8 +1329,9 @@ const crt::Consts* crt_consts_device() {
 cudaError_t crt_reconstruct(const uint8_t* R, int64_t Mpad, int64_t Npad, Dim M, Dim N,
                             const int64_t* rdev, const int32_t* EA, const int32_t* EB, int betaA,
                             int betaB, double alpha, double beta, double* C, int64_t ldc,
-                            int lower, int n_mod, cudaStream_t s, KernelTimer* timer) {
+                            int lower, int n_mod, cudaStream_t s, KernelTimer* timer, int blk) {
   if (!crt_consts_device()) return cudaErrorInitializationError;
+  if (blk && (n_mod > kRecWordsMaxMod || Npad != blk)) return cudaErrorInvalidValue;
   ReconParams rp;
   rp.R = R;
   rp.Mpad = Mpad;
@@ -1277,9 +1348,10 @@ cudaError_t crt_reconstruct(const uint8_t* R, int64_t Mpad, int64_t Npad, Dim M,
   rp.C = C;
   rp.ldc = ldc;
   rp.lower = lower;
-  rp.pad = 0;
+  rp.blk = blk;
   // small outputs (factorisation panels): latency-bound, four lanes per output
-  const bool small = M.max * N.max <= ((int64_t)1 << 16);
+  // (block-diagonal outputs always take the word-wise kernel)
+  const bool small = !blk && M.max * N.max <= ((int64_t)1 << 16);
   return timer->run(KT_RECON, s, [&] {
     if (small)
       reconstruct_split_kernel<<<grid1d(M.max * N.max * kRecLanes, 256), 256, 0, s>>>(rp, n_mod);

@@ -143,9 +143,16 @@ def test_batched_argument_checks_need_no_gpu(lib):
         assert lib.cpinv_lstsq_batched(1, arr(p), ranks, status, fake, 1 << 30, ctypes.byref(o), None) == code
         assert ranks[0] == -1
         assert lib.cpinv_lstsq_batched_workspace_size(1, arr(p), ctypes.byref(o)) == 0
-    # other arithmetic modes are not offered in the batch
+    # the split tier is not offered in the batch; the exact-slice mode is,
+    # for m <= 4096 (one exact residue product)
+    sp = cpinv.make_opts("bf16x3")
+    assert lib.cpinv_lstsq_batched(1, arr(good), None, None, fake, 1 << 30, ctypes.byref(sp), None) == 6
     ex = cpinv.make_opts("exact")
-    assert lib.cpinv_lstsq_batched(1, arr(good), None, None, fake, 1 << 30, ctypes.byref(ex), None) == 6
+    long_ = P(5000, 40, 4, fake, 40, fake, 4, fake, 4)
+    assert lib.cpinv_lstsq_batched(1, arr(long_), None, None, fake, 1 << 30, ctypes.byref(ex), None) == 6
+    assert lib.cpinv_lstsq_batched_workspace_size(1, arr(long_), ctypes.byref(ex)) == 0
+    # the exact-slice batch needs more workspace (residue planes and products)
+    assert lib.cpinv_lstsq_batched_workspace_size(1, arr(good), ctypes.byref(ex)) > ws
     bad_panel = cpinv.make_opts("fp64", panel=24)
     assert lib.cpinv_lstsq_batched(1, arr(good), None, None, fake, 1 << 30, ctypes.byref(bad_panel), None) == 1
     # workspace misaligned or too small

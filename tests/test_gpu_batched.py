@@ -172,3 +172,87 @@ def test_batched_full_workload_sampled():
         assert np.linalg.norm(res) <= 1e-9 * scale, i
     sample = np.random.default_rng(0).choice(512, size=12, replace=False)
     _check_against_oracle(probs, Ws, ranks, st, idx=sorted(int(i) for i in sample))
+
+
+# --------------------------------------------------------------------------
+# the exact-slice batched mode: every Gram matrix and every L'L of a group
+# as one block-diagonal tensor-core residue product (exactly summed, rounded
+# once); the factorisation updates, the inverse and the chain stay FP64, so
+# the FP64 bar applies
+# --------------------------------------------------------------------------
+
+def test_batched_exact_small_uneven():
+    probs = _problems(24, 11, k=3, m_range=(16, 300), n_lo=4, n_hi=160)
+    cp = _cp()
+    Ws, ranks, st = cp.lstsq_batched([to_dev(p.G) for p in probs], [to_dev(p.F) for p in probs],
+                                     mode="exact")
+    _check_against_oracle(probs, Ws, ranks, st)
+    assert ranks == [p.r for p in probs]
+
+
+@pytest.mark.parametrize("panel", [16, 32])
+def test_batched_exact_wide_buckets(panel):
+    """Groups of n_pad 256 and 512 (where the residue products may take
+    256-wide tiles) and ragged m up to the 4096 limit of one exact product."""
+    probs = _problems(9, 13, k=2, m_range=(300, 4096), n_lo=130, n_hi=512)
+    cp = _cp()
+    Ws, ranks, st = cp.lstsq_batched([to_dev(p.G) for p in probs], [to_dev(p.F) for p in probs],
+                                     mode="exact", panel=panel)
+    _check_against_oracle(probs, Ws, ranks, st)
+
+
+def test_batched_exact_graph_replay_and_fp64_agree():
+    probs = _problems(16, 14, k=4, m_range=(64, 700), n_lo=32, n_hi=400)
+    cp = _cp()
+    Gs, Fs = [to_dev(p.G) for p in probs], [to_dev(p.F) for p in probs]
+    plan = cp.BatchedLstsq(Gs, Fs, mode="exact")
+    W1 = [w.clone() for w in plan()[0]]
+    plan()
+    Ws, ranks, st = plan()
+    for a, b in zip(W1, Ws):
+        assert torch.equal(a, b)
+    Wf, rf, _ = cp.lstsq_batched(Gs, Fs, mode="fp64")
+    assert rf == ranks
+    for p, a, b, r in zip(probs, Ws, Wf, ranks):
+        assert rel(a.cpu().numpy(), b.cpu().numpy()) <= 2.0 * fp64_bar(p.G, p.F, r)
+
+
+def test_batched_exact_rejects_long_problems():
+    """m > 4096 exceeds one exact residue product: no workspace size and
+    CPINV_ERR_UNSUPPORTED from the call, before any GPU work."""
+    import ctypes
+    cp = _cp()
+    G, F = to_dev(np.ones((4097, 8))), to_dev(np.ones((4097, 1)))
+    W = torch.empty((8, 1), dtype=torch.float64, device="cuda:0")
+    probs = (cp.Problem * 1)(cp.Problem(4097, 8, 1, G.data_ptr(), 8, F.data_ptr(), 1,
+                                        W.data_ptr(), 1))
+    o = cp.make_opts("exact")
+    assert cp.lib().cpinv_lstsq_batched_workspace_size(1, probs, ctypes.byref(o)) == 0
+    ranks = (ctypes.c_int64 * 1)(7)
+    status = (ctypes.c_int32 * 1)(0)
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda:0")
+    rc = cp.lib().cpinv_lstsq_batched(1, probs, ranks, status, ws.data_ptr(), ws.numel(),
+                                      ctypes.byref(o), torch.cuda.current_stream().cuda_stream)
+    assert rc == 6 and ranks[0] == -1
+
+
+def test_batched_exact_full_workload():
+    """The 512-problem uneven workload in the exact-slice mode: every rank
+    equals the construction rank, every W satisfies its normal equations,
+    and 32 sampled problems match the oracle."""
+    probs = inputs.batched_problems(512, 4, k=4, attempts=gap.load())
+    cp = _cp()
+    plan = cp.BatchedLstsq([to_dev(p.G) for p in probs], [to_dev(p.F) for p in probs],
+                           mode="exact")
+    plan()
+    Ws, ranks, st = plan()
+    assert all(s == 0 for s in st)
+    assert ranks == [p.r for p in probs]
+    for i in range(0, 512, 5):
+        p = probs[i]
+        W = Ws[i].cpu().numpy()
+        res = p.G.T @ (p.G @ W - p.F)
+        scale = np.linalg.norm(p.G) ** 2 * np.linalg.norm(W) + np.linalg.norm(p.G) * np.linalg.norm(p.F)
+        assert np.linalg.norm(res) <= 1e-9 * scale, i
+    sample = np.random.default_rng(1).choice(512, size=32, replace=False)
+    _check_against_oracle(probs, Ws, ranks, st, idx=sorted(int(i) for i in sample))
