@@ -245,9 +245,10 @@ int cpinv_lstsq_backward_from_state(const double* G, int64_t m, int64_t n, int64
  * own, with its own tolerance and rank), all enqueued on `stream` as one
  * batch.  Problems are grouped by n (rounded up to 128); every stage is one
  * launch per group.  Arithmetic: CPINV_MODE_FP64, or CPINV_MODE_EXACT_SLICE,
- * in which the Gram matrices G_p'G_p and the products L_p'L_p of a group are
- * one block-diagonal tensor-core residue product each (every entry the exact
- * sum rounded once; requires m <= 4096) and the rest is FP64.
+ * in which the Gram matrices G_p'G_p, the products L_p'L_p and the inverses
+ * (L_p'L_p)^-1 = W_p'W_p of a group are one block-diagonal tensor-core
+ * residue product each (every entry the exact sum rounded once; requires
+ * m <= 4096) and the rest is FP64.
  *   probs : HOST array of P descriptors; G, F, W in each are DEVICE pointers
  *           (row-major, as for cpinv_lstsq).  Requires 1 <= n <= m,
  *           n <= CPINV_BATCHED_MAX_N, 1 <= k <= CPINV_BATCHED_MAX_K,

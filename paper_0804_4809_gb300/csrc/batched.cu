@@ -1,7 +1,9 @@
 // Batched minimum-norm least squares, W_p = G_p+ F_p for many independent
 // problems of uneven size (cpinv_lstsq_batched in include/cpinv.h); each
 // problem follows the Appendix pipeline exactly as the single-problem path
-// does, in FP64 arithmetic.
+// does, in FP64 arithmetic, or in the exact-slice mode with its Gram matrix,
+// L'L and W'W (W = U^-1) as block-diagonal tensor-core residue products
+// (exact_gram_batched).
 //
 // The problems are grouped into buckets by n rounded up to a multiple of 128.
 // Inside a bucket every problem keeps its own m, n and rank in its DevState,
@@ -476,15 +478,16 @@ int bucket_tri_inverse(cudaStream_t s, const Bucket& bk, char* ws, int b) {
   return CPINV_OK;
 }
 
-// C_z = X_z' X_z (lower triangle) for every problem z of the bucket in the
-// exact-slice arithmetic: X_z = X + z zX (ld np, the n x K operand's rows
-// are the columns of X_z: `rows` of them, K = `K` rows of X_z, both read
-// per problem), the residue planes of all problems stacked along M, one
+// C_z = X_z' X_z (the lower triangle, or whole when lower = 0) for every
+// problem z of the bucket in the exact-slice arithmetic: X_z = X + z zX (ld
+// np; the operand's rows are the columns of X_z, `rows` of them, and K =
+// `K` rows of X_z, both read per problem), the residue planes of all
+// problems stacked along M, one
 // block-diagonal tensor-core product (np x np blocks), one reconstruction
 // into C (z-major np x np).  Each entry is the exact sum rounded once.
 int exact_gram_batched(cudaStream_t s, const Bucket& bk, char* ws, const double* X, int64_t zX,
                        Dim rows, Dim K, int64_t kpad, int n_mod, int beta, int32_t* E,
-                       double* C) {
+                       double* C, int lower = 1) {
   const int nz = (int)bk.ids.size();
   const int64_t np = bk.np, tot = (int64_t)nz * np;
   DevState* st = (DevState*)(ws + bk.off_st);
@@ -501,12 +504,12 @@ int exact_gram_batched(cudaStream_t s, const Bucket& bk, char* ws, const double*
   std::memset(&fl, 0, sizeof(fl));
   fl.M = fl.N = hdim(np);
   fl.K = hdim(K.max * nz);
-  fl.lower = 1;
+  fl.lower = lower;
   fl.rdev = &st->rank;
-  BK_CHECK(crt_mma(S, tot, 0, S, tot, 0, kpad, K.max, n_mod, hdim(tot), hdim(tot), &st->rank, 1, R,
-                   tot, np, &st->status, s, &t, &fl, 0, (int)np, bk.bn));
+  BK_CHECK(crt_mma(S, tot, 0, S, tot, 0, kpad, K.max, n_mod, hdim(tot), hdim(tot), &st->rank,
+                   lower, R, tot, np, &st->status, s, &t, &fl, 0, (int)np, bk.bn));
   BK_CHECK(crt_reconstruct(R, tot, np, hdim(tot), hdim(np), &st->rank, E, E, beta, beta, 1.0, 0.0,
-                           C, np, 1, n_mod, s, &t, (int)np));
+                           C, np, lower, n_mod, s, &t, (int)np));
   return CPINV_OK;
 }
 
@@ -577,8 +580,16 @@ int run_bucket(cudaStream_t s, const Bucket& bk, char* ws, double rel_tol, int b
     return cudaGetLastError();
   }));
   if (int rc = bucket_tri_inverse(s, bk, ws, b)) return rc;
-  BK_CHECK(BGemm(nz, st).a(W, np, zz, true).b(W, np, zz, false).c(Mm, np, zz).dims(R, R, R)
-               .run(s, 1.0, 0.0, 0));
+  if (bk.exact) {
+    // M = W'W whole (the chain reads both triangles), the same block-diagonal
+    // residue product as L'L (K = r <= n_pad, 53-bit operands)
+    if (int rc = exact_gram_batched(s, bk, ws, W, zz, R, R, bk.kpad_l, bk.nmod_l, kProdBits,
+                                    (int32_t*)(ws + bk.off_EL), Mm, 0))
+      return rc;
+  } else {
+    BK_CHECK(BGemm(nz, st).a(W, np, zz, true).b(W, np, zz, false).c(Mm, np, zz).dims(R, R, R)
+                 .run(s, 1.0, 0.0, 0));
+  }
   // W = L (M (M (L' (G'F))))   (Theorem 1 applied to F, right to left)
   BK_CHECK(BGemm(nz, st).a(Gp, np, zg, true).b(Fp, kp, zf, false).c(c1, kp, zk).dims(Nn, Kk, Mr)
                .run(s, 1.0, 0.0, 0));
