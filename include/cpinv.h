@@ -184,6 +184,13 @@ int cpinv_rbf_normal_equations(const double* X, int64_t m, int64_t d, int64_t ld
  * ------------------------------------------------------------------------- */
 int cpinv_selftest_wait_timeout(void* workspace, size_t workspace_bytes, void* stream);
 
+/* The same for the batched path's queue-fed factorisation: one task whose
+ * input no task produces (workspace: >= 64 KiB of device memory, 256-byte
+ * aligned, overwritten).  Its bounded wait gives up after about a second,
+ * records the timeout and raises the launch's abort flag.  Returns
+ * CPINV_ERR_TIMEOUT when that happened (expected), CPINV_OK if not. */
+int cpinv_selftest_queue_timeout(void* workspace, size_t workspace_bytes, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Adjoint of the least-squares weights (reverse mode): given the cotangent
  * Wbar = dL/dW (n x k) of a scalar L of W = G+ F, returns

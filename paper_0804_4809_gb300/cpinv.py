@@ -89,6 +89,7 @@ SIGNATURES = {
                                                        ctypes.POINTER(Opts),
                                                        ctypes.POINTER(_c_i64), _c_vp]),
     "cpinv_selftest_wait_timeout": (ctypes.c_int, [_c_vp, _c_sz, _c_vp]),
+    "cpinv_selftest_queue_timeout": (ctypes.c_int, [_c_vp, _c_sz, _c_vp]),
     "cpinv_gram_update_workspace_size": (_c_sz, [_c_i64, _c_i64, _c_i64, ctypes.c_int32]),
     "cpinv_gram_update": (ctypes.c_int, [_c_vp, _c_i64, _c_i64, _c_i64, _c_vp, _c_i64, _c_i64,
                                          _c_vp, _c_i64, _c_vp, _c_i64, ctypes.c_int32, _c_vp,
@@ -353,6 +354,14 @@ def selftest_wait_timeout(device=None) -> int:
     dev = torch.device("cuda", 0) if device is None else torch.device(device)
     ws = _workspace(256, dev)
     return int(lib().cpinv_selftest_wait_timeout(ws.data_ptr(), ws.numel(), _stream(dev)))
+
+
+def selftest_queue_timeout(device=None) -> int:
+    """Runs the batched queue's bounded wait on an input no task produces;
+    returns the library status (CPINV_ERR_TIMEOUT expected)."""
+    dev = torch.device("cuda", 0) if device is None else torch.device(device)
+    ws = _workspace(64 * 1024, dev)
+    return int(lib().cpinv_selftest_queue_timeout(ws.data_ptr(), ws.numel(), _stream(dev)))
 
 
 def lstsq_backward(G: torch.Tensor, F: torch.Tensor, dW: torch.Tensor, mode="fp64",

@@ -113,6 +113,38 @@ cudaError_t crt_split_batched(const double* X, int64_t ld, int tview, Dim rows, 
                               const int32_t* E, int n_mod, int beta, void* out, int nz,
                               int64_t zX, int64_t zR, cudaStream_t s, KernelTimer* timer);
 
+// chol_queue.cu: the factorisations of a batch in one persistent launch
+// fed by a device task queue (tasks on 32 x 32 tiles, listed in dependency
+// order by the host; see the file's comment).
+enum : int32_t { kQDiag = 0, kQSolve = 1, kQUpd = 2 };
+struct QueueTask {
+  int32_t kind;  // kQDiag, kQSolve, kQUpd
+  int32_t z;     // problem (within the bucket)
+  int16_t p;     // panel
+  int16_t i, j;  // block row / block column (SOLVE: i; UPD: i >= j)
+  int16_t pad;
+};
+static_assert(sizeof(QueueTask) == 16, "QueueTask layout");
+struct QueueFactor {
+  double* A;          // problem z at A + z zA, row-major, ld np
+  int64_t np, zA;
+  int32_t sel;        // SEL_N: order n_z, Appendix tolerance; SEL_RANK: order r_z, tol 0
+  int32_t spd;
+  DevState* st;       // per problem
+  uint8_t* acc;       // kept mask (spd = 0), acc + z zAcc
+  int64_t zAcc;
+  double* dinv;       // 1 / L_cc per column, dinv + z zDinv (np per problem)
+  int64_t zDinv;
+  int32_t* flags;     // per problem (zeroed): ver[nb][nb], solved[nb], diag[nb]
+  int64_t zFlags;
+  int32_t nb_max;     // blocks of np
+  int32_t ntasks;
+  const QueueTask* tasks;
+  int32_t* head;      // [0] next task (zeroed), [1] abort flag (zeroed)
+};
+cudaError_t launch_chol_queue(const QueueFactor& q, int ctas, cudaStream_t s);
+int chol_queue_ctas();  // CTAs of one wave on this device (0 on error)
+
 // chol_exact.cu
 cudaError_t launch_rowscale(const double* A, int64_t lda, Dim nd, const int64_t* rdev,
                             int64_t rows_max, int32_t* E, cudaStream_t s);

@@ -256,3 +256,60 @@ def test_batched_exact_full_workload():
         assert np.linalg.norm(res) <= 1e-9 * scale, i
     sample = np.random.default_rng(1).choice(512, size=32, replace=False)
     _check_against_oracle(probs, Ws, ranks, st, idx=sorted(int(i) for i in sample))
+
+
+# --------------------------------------------------------------------------
+# the factorisations as one persistent launch fed by a device task queue
+# (CPINV_BATCH_FACTOR=queue), against the oracle and against the per-panel
+# launches
+# --------------------------------------------------------------------------
+
+@pytest.fixture
+def factor_form(monkeypatch):
+    def use(form):
+        monkeypatch.setenv("CPINV_BATCH_FACTOR", form)
+    return use
+
+
+@pytest.mark.parametrize("mode", ["fp64", "exact"])
+def test_batched_queue_small_uneven(factor_form, mode):
+    probs = _problems(24, 11, k=3, m_range=(16, 300), n_lo=4, n_hi=160)
+    cp = _cp()
+    factor_form("queue")
+    Ws, ranks, st = cp.lstsq_batched([to_dev(p.G) for p in probs], [to_dev(p.F) for p in probs],
+                                     mode=mode)
+    _check_against_oracle(probs, Ws, ranks, st)
+    assert ranks == [p.r for p in probs]
+
+
+def test_batched_queue_matches_panel_launches(factor_form):
+    """Same batch, both forms of the factorisation: same ranks, and W within
+    rounding (the queue applies the same updates in the same panel order,
+    tile by tile)."""
+    probs = _problems(40, 15, k=4, m_range=(64, 1024), n_lo=32, n_hi=512)
+    cp = _cp()
+    Gs, Fs = [to_dev(p.G) for p in probs], [to_dev(p.F) for p in probs]
+    factor_form("queue")
+    Wq, rq, sq = cp.lstsq_batched(Gs, Fs, mode="fp64")
+    factor_form("panels")
+    Wp, rp, sp = cp.lstsq_batched(Gs, Fs, mode="fp64", panel=32)
+    assert all(x == 0 for x in sq + sp)
+    assert rq == rp == [p.r for p in probs]
+    for p, a, b, r in zip(probs, Wq, Wp, rq):
+        assert rel(a.cpu().numpy(), b.cpu().numpy()) <= 2.0 * fp64_bar(p.G, p.F, r)
+    sample = list(range(0, 40, 5))
+    _check_against_oracle(probs, Wq, rq, sq, idx=sample)
+
+
+def test_batched_queue_full_workload(factor_form):
+    probs = inputs.batched_problems(512, 4, k=4, attempts=gap.load())
+    cp = _cp()
+    factor_form("queue")
+    plan = cp.BatchedLstsq([to_dev(p.G) for p in probs], [to_dev(p.F) for p in probs],
+                           mode="exact")
+    plan()
+    Ws, ranks, st = plan()
+    assert all(s == 0 for s in st)
+    assert ranks == [p.r for p in probs]
+    sample = np.random.default_rng(2).choice(512, size=16, replace=False)
+    _check_against_oracle(probs, Ws, ranks, st, idx=sorted(int(i) for i in sample))
