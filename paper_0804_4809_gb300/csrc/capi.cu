@@ -143,7 +143,7 @@ struct Plan {
   DevState* st;
   uint8_t* acc;
   int32_t* colidx;
-  double* dinv;  // 1/L_cc of the current diagonal block (0: rejected)
+  double* dinv;  // 1/L_cc of the current diagonal block(s) (0: rejected); two slots of 32
   double* Tinv;
   double* bufA;  // A -> L_full -> N -> U -> K
   double* bufL;  // compact L (nA x nA, r columns used)
@@ -169,7 +169,6 @@ struct Plan {
   double* S2;
   void* crt;     // exact-slice scratch (residues, exponents)
   size_t crt_bytes;
-  mutable int64_t diag_shares;  // exact factorisation: helper shares so far in this call
 };
 
 // Where a product sits in the pipeline decides its arithmetic:
@@ -276,7 +275,7 @@ void carve(Plan& p, Arena& a, Job job) {
   p.crt = p.crt_bytes ? a.take(p.crt_bytes) : nullptr;
   p.acc = (uint8_t*)a.take((size_t)(nA > 0 ? nA : 1));
   p.colidx = (int32_t*)a.take(sizeof(int32_t) * (size_t)(nA > 0 ? nA : 1));
-  p.dinv = (double*)a.take(sizeof(double) * (size_t)b);
+  p.dinv = (double*)a.take(sizeof(double) * 64);  // two slots of 32
   p.bufA = (double*)a.take(sizeof(double) * (size_t)(nA * nA));
   if (job == JOB_RANK) return;
   p.Tinv = (double*)a.take(sizeof(double) * (size_t)(nb * b * b));
@@ -543,11 +542,6 @@ int factor_exact(const Ctx& c, double* a, int64_t lda, int spd) {
   CK(cudaMemsetAsync(RL, 0, Ly.rl_bytes, c.s));
   const crt::Consts* consts = crt_consts_device();
   if (!consts) return CPINV_ERR_CUDA;
-  // Look-ahead: the update of panel p splits into the columns 0 .. kb (kb a
-  // multiple of the residue planes' K block, kb <= k0 - b), whose residue
-  // product runs on a second stream as soon as panel p - 2 is done, i.e.
-  // while panel p - 1 is factored, and the last columns kb .. k0, summed
-  // exactly inside panel p's own launch.  Two residue buffers alternate.
   SideStream* side = side_stream();
   if (!side) return CPINV_ERR_CUDA;
   std::lock_guard<std::mutex> side_lock(side->mu);
@@ -555,75 +549,101 @@ int factor_exact(const Ctx& c, double* a, int64_t lda, int spd) {
   CK(cudaEventRecord(side->fork, c.s));
   CK(cudaStreamWaitEvent(s2, side->fork, 0));
   const int64_t kblk = crt_block_k();
-  for (int64_t k0 = 0, pi = 0; k0 < nA; k0 += b, ++pi) {
-    const int64_t kb = k0 >= b ? (k0 - b) / kblk * kblk : 0;
-    uint8_t* R = Rbuf[pi & 1];
+  const int nbr = chol_panel_exact_nbr(b), helpers = chol_panel_exact_helpers(b);
+  // this factorisation's completion counters start at zero
+  CK(cudaMemsetAsync(&p.st->panel_flag, 0, 2 * sizeof(int64_t), c.s));
+  int64_t rows_target = 0, diag_target = 0;
+  PanelExactParams pp;
+  std::memset(&pp, 0, sizeof(pp));
+  pp.Mpad = Ly.rows;
+  pp.Npad = 256;
+  pp.n_upd = Ly.n_mod;
+  pp.consts = consts;
+  pp.A = a;
+  pp.lda = lda;
+  pp.nd = nd;
+  pp.rdev = c.rdev();
+  pp.b = b;
+  pp.spd = spd;
+  pp.st = p.st;
+  pp.accepted = spd ? nullptr : p.acc;
+  pp.E = E;
+  pp.n_mod = Ly.n_mod;
+  pp.beta = kCholBits;
+  pp.RL = (__nv_bfloat16*)RL;
+  pp.rl_rows = Ly.rows;
+  pp.rl_kpad = Ly.kpad;
+  pp.nbr = nbr;
+  pp.helpers = helpers;
+  // 1/T_cc of block j in slot j & 1 (the launch that solves against block j
+  // runs while the next block is factored)
+  auto dinv_slot = [&](int64_t j) { return p.dinv + 32 * (j & 1); };
+  // Launch L(-1) factors block 0; launch L(q), q = 0 .. np - 2, solves the
+  // rows below block q and factors block q + 1 (see chol_exact.cu).  The
+  // update of panel q + 1 that L(q) applies splits into the columns 0 .. kb,
+  // whose residue product runs on the second stream once L(q - 2) is done
+  // (while L(q - 1) runs; kb, a multiple of the residue planes' K block, is
+  // at most the first column of panel q - 1), and the last columns kb .. kn,
+  // summed exactly inside L(q).  Two residue buffers alternate.
+  const int64_t np = (nA + b - 1) / b;
+  {
+    pp.has_update = 0;
+    pp.ks = -b;
+    pp.kn = 0;
+    pp.dinv_next = dinv_slot(0);
+    DiagTimer pt = diag_timer(c, 0, b, spd);
+    CK(pt.run(KT_PANEL, c.s, [&] { return launch_chol_panel_exact(pp, c.s); }));
+    CK(cudaEventRecord(side->done[0], c.s));
+  }
+  for (int64_t q = 0; q + 1 < np; ++q) {
+    const int64_t ks = q * b, kn = ks + b;
+    const int64_t kb = q >= 1 ? (q - 1) * b / kblk * kblk : 0;
+    uint8_t* R = Rbuf[q & 1];
     if (kb > 0) {
-      // residues of L(k0:n, 0:kb) L(P, 0:kb)', exactly, from the residue planes
-      if (pi >= 2) CK(cudaStreamWaitEvent(s2, side->done[(pi - 2) % kSideEvents], 0));
-      const Dim M = spd ? rdim(-k0, nA - k0) : hdim(nA - k0);
-      const Dim N = spd ? rdim(-k0, b) : hdim(nA - k0 < b ? nA - k0 : b);
+      // residues of L(kn:n, 0:kb) L(P, 0:kb)', exactly, from the residue planes,
+      // once launch L(q - 2) (launch number q - 1) has finished
+      CK(cudaStreamWaitEvent(s2, side->done[(q - 1) % kSideEvents], 0));
+      const Dim M = spd ? rdim(-kn, nA - kn) : hdim(nA - kn);
+      const Dim N = spd ? rdim(-kn, b) : hdim(nA - kn < b ? nA - kn : b);
       GemmParams fl;
       std::memset(&fl, 0, sizeof(fl));
       fl.M = M;
       fl.N = N;
       fl.K = spd ? rdim(0, kb) : hdim(kb);
       fl.rdev = c.rdev();
-      CK(crt_mma(RL, Ly.rows, (int)k0, RL, Ly.rows, (int)k0, Ly.kpad, kb, Ly.n_mod, M, N,
+      CK(crt_mma(RL, Ly.rows, (int)kn, RL, Ly.rows, (int)kn, Ly.kpad, kb, Ly.n_mod, M, N,
                  c.rdev(), 0, R, Ly.rows, 256, &p.st->status, s2, &t, &fl, kLookaheadCtas));
-      CK(cudaEventRecord(side->mma[pi % kSideEvents], s2));
-      CK(cudaStreamWaitEvent(c.s, side->mma[pi % kSideEvents], 0));
+      CK(cudaEventRecord(side->mma[q % kSideEvents], s2));
+      CK(cudaStreamWaitEvent(c.s, side->mma[q % kSideEvents], 0));
     }
-    // A(k0:n, P) -= the update, the diagonal block, the rows below, residues
-    PanelExactParams pp;
-    std::memset(&pp, 0, sizeof(pp));
     pp.R = R;
-    pp.Mpad = Ly.rows;
-    pp.Npad = 256;
-    pp.has_update = k0 > 0;
+    pp.has_update = 1;
     pp.has_bulk = kb > 0;
     pp.kb = kb;
-    pp.k_last = (int32_t)(k0 - kb);
-    pp.n_upd = Ly.n_mod;
-    pp.consts = consts;
-    pp.A = a;
-    pp.lda = lda;
-    pp.nd = nd;
-    pp.rdev = c.rdev();
-    pp.k0 = k0;
-    pp.b = b;
-    pp.spd = spd;
-    pp.st = p.st;
-    pp.accepted = spd ? nullptr : p.acc;
-    pp.dinv = p.dinv;
-    pp.E = E;
-    pp.n_mod = Ly.n_mod;
-    pp.beta = kCholBits;
-    pp.RL = (__nv_bfloat16*)RL;
-    pp.rl_rows = Ly.rows;
-    pp.rl_kpad = Ly.kpad;
-    pp.epoch = 1 + k0 / b + (spd ? ((int64_t)1 << 32) : 0);
-    if (pp.has_update) {
-      const int64_t ctas = chol_panel_exact_ctas(nd.max, k0, b);
-      pp.helpers = (int32_t)(ctas - 1 < kPanelHelpers ? ctas - 1 : kPanelHelpers);
-      p.diag_shares += pp.helpers;
-      pp.diag_target = p.diag_shares;
-    }
-    // traced work of the fused launch, in FP64-equivalent flops: for the
-    // rows k0 .. n of the panel (its diagonal block included), the exact sum
-    // over the last k0 - kb columns (2 per term) and the forward substitution
-    // against the block (b per entry) -- 2 (n - k0) b (k0 - kb + b / 2) --
-    // which covers the block's own b^3/3 factorisation as well; the bulk
-    // columns 0 .. kb are the look-ahead product's work
+    pp.k_last = (int32_t)(kn - kb);
+    pp.ks = ks;
+    pp.kn = kn;
+    pp.dinv_prev = dinv_slot(q);
+    pp.dinv_next = dinv_slot(q + 1);
+    rows_target += nbr;
+    diag_target += helpers;
+    pp.rows_target = rows_target;
+    pp.diag_target = diag_target;
+    // traced work of the launch, in FP64-equivalent flops: for the rows
+    // kn .. n, the forward substitution against block ks (b per entry) and
+    // the exact sum over the last kn - kb columns (2 per term) --
+    // 2 (n - kn) b (kn - kb + b / 2) -- which covers the block's own b^3/3
+    // factorisation as well; the bulk columns 0 .. kb are the look-ahead
+    // product's work
     DiagTimer pt;
     std::memset(&pt.g, 0, sizeof(pt.g));
-    pt.g.M = spd ? rdim(-k0, nA - k0) : hdim(nA - k0);
-    pt.g.N = hdim(nA - k0 < b ? nA - k0 : b);
-    pt.g.K = hdim(k0 - kb + b / 2);
+    pt.g.M = spd ? rdim(-kn, nA - kn) : hdim(nA - kn);
+    pt.g.N = hdim(b);
+    pt.g.K = hdim(kn - kb + b / 2);
     pt.g.rdev = c.rdev();
     pt.t.flops_mult = 1.0;
     CK(pt.run(KT_PANEL, c.s, [&] { return launch_chol_panel_exact(pp, c.s); }));
-    CK(cudaEventRecord(side->done[pi % kSideEvents], c.s));
+    CK(cudaEventRecord(side->done[(q + 1) % kSideEvents], c.s));
   }
   // join the second stream back
   CK(cudaEventRecord(side->join, s2));
@@ -932,7 +952,6 @@ int run_pipeline(const Plan& p, cudaStream_t user, const GraphKey& key, Body&& b
   auto direct = [&]() -> int {
     Ctx c{user, &p};
     if (!keep_state) CK(cudaMemsetAsync(p.st, 0, sizeof(DevState), user));
-    p.diag_shares = 0;
     return body(c);
   };
   if (!graphs_enabled()) return direct();
@@ -969,7 +988,6 @@ int run_pipeline(const Plan& p, cudaStream_t user, const GraphKey& key, Body&& b
     const int64_t l0 = g_launches.load();
     CK(cudaStreamBeginCapture(side, cudaStreamCaptureModeThreadLocal));
     Ctx c{side, &p};
-    p.diag_shares = 0;
     int rc = (keep_state || cudaMemsetAsync(p.st, 0, sizeof(DevState), side) == cudaSuccess)
                  ? body(c)
                  : CPINV_ERR_CUDA;

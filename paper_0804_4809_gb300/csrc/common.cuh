@@ -46,8 +46,8 @@ struct DevState {
   double min_pos;   // that minimum
   int64_t dim_m;    // batched problems: this problem's m and n (else 0)
   int64_t dim_n;
-  int64_t panel_flag;  // last panel whose diagonal block is published (exact factorisation)
-  int64_t diag_count;  // diagonal-block update shares done (exact factorisation)
+  int64_t panel_flag;  // block-row CTAs done (exact factorisation, cumulative over launches)
+  int64_t diag_count;  // diagonal-block update CTAs done (exact factorisation, cumulative)
   int64_t spare[7];
 };
 static_assert(sizeof(DevState) == 128, "DevState layout");

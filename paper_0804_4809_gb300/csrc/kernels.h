@@ -151,36 +151,40 @@ cudaError_t launch_rowscale(const double* A, int64_t lda, Dim nd, const int64_t*
 // One fused launch per panel of the exact-slice factorisation (update
 // reconstruction, diagonal block, rows below, residue split).
 struct PanelExactParams {
-  const uint8_t* R;   // residues of the update over columns 0 .. kb, R[j][row][col] (rows from k0)
+  const uint8_t* R;   // residues of the update of panel kn over columns 0 .. kb, R[j][row][col] (rows from kn)
   int64_t Mpad, Npad;
-  int32_t has_update, n_upd;  // moduli count of the update
+  int32_t has_update, n_upd;  // has_update = 0: the first launch (block 0 only); moduli count of the update
   int32_t has_bulk;   // kb > 0: R holds the part over columns 0 .. kb
-  int32_t k_last;     // columns kb .. k0 (<= 64) summed exactly in the kernel
+  int32_t k_last;     // columns kb .. kn (<= 96) summed exactly in the kernel
   int64_t kb;
   const crt::Consts* consts;  // crt_consts_device()
   double* A;
   int64_t lda;
   Dim nd;
   const int64_t* rdev;
-  int64_t k0;
+  int64_t ks;         // panel whose rows below its block are solved here (block factored by the previous launch)
+  int64_t kn;         // ks + b: the block factored here
   int32_t b, spd;
   DevState* st;
   uint8_t* accepted;
-  double* dinv;
+  const double* dinv_prev;  // 1/T_cc of block ks
+  double* dinv_next;        // 1/T_cc of block kn (written here)
   const int32_t* E;   // row scales (biased exponent bounds)
   int32_t n_mod, beta;  // residues of the factor: moduli count and bits
   __nv_bfloat16* RL;
   int64_t rl_rows, rl_kpad;
-  int64_t epoch;      // published into st->panel_flag when the block is done
-  int32_t helpers;    // CTAs 1..helpers update the diagonal block (0: CTA 0 does)
-  int32_t pad;
-  int64_t diag_target;  // st->diag_count once this panel's helpers are done
+  int32_t nbr;        // CTAs 1..nbr solve the rows of block kn (chol_panel_exact_nbr)
+  int32_t helpers;    // the next CTAs update block kn (chol_panel_exact_helpers)
+  int64_t rows_target;  // st->panel_flag once this launch's block-row CTAs are done
+  int64_t diag_target;  // st->diag_count once its helpers are done
 };
 // One CTA waits, bounded, on st->spare[0] >= 1 (nothing sets it): records
 // ST_TIMEOUT in st->status after about a second and returns.
 cudaError_t launch_wait_selftest(DevState* st, cudaStream_t s);
 cudaError_t launch_chol_panel_exact(const PanelExactParams& p, cudaStream_t s);
-int64_t chol_panel_exact_ctas(int64_t nmax, int64_t k0, int b);  // grid size of that launch
+int64_t chol_panel_exact_ctas(int64_t nmax, int64_t kn, int b);  // grid size of that launch
+int chol_panel_exact_nbr(int b);      // block-row CTAs of a launch factoring a block of order b
+int chol_panel_exact_helpers(int b);  // helper CTAs of that launch
 
 // gemm_fp64.cu
 cudaError_t launch_dgemm(const GemmParams& p, bool transA, bool transB, cudaStream_t s);
