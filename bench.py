@@ -435,11 +435,13 @@ def ours(args):
         if dom == "chol_panel":
             pr = line["roofline"]
             pr["note"] = ("chol_panel_exact_kernel, the fused panel launch of the exact "
-                          "factorisation (both factorisations of a step): latency-bound by the "
+                          "factorisation (both factorisations of a step; a launch solves the rows "
+                          "below block ks and factors block kn = ks + b): latency-bound by the "
                           "chain of 32 dependent pivots of its diagonal block; work counted per "
-                          "launch: 2 (n - k0) b (k0 - kb + b/2) FP64-equivalent flops (the exact "
-                          "sum over the last k0 - kb columns and the forward substitution of rows "
-                          "k0..n; the bulk columns are the tensor-core product's work)")
+                          "launch: 2 (n - kn) b (kn - kb + b/2) FP64-equivalent flops (the "
+                          "forward substitution of rows kn..n and the exact sum over the last "
+                          "kn - kb columns of their update; the bulk columns are the "
+                          "tensor-core product's work)")
             pr["algorithmic_bytes_per_launch"] = panel_bytes_per_launch(N, R, 32)
             traffic = profile_value(PANEL_PROFILE, "dram_bytes_per_launch:")
             pr["traffic"] = traffic
@@ -499,17 +501,24 @@ def profile_value(path, key):
 
 def panel_bytes_per_launch(n, r, b, n_mod=20):
     """Algorithmic DRAM bytes of the fused panel launches of one step (both
-    factorisations: order n, then order r), averaged per launch: per row of
-    the panel, the panel's FP64 entries read and the factor written (16 b),
-    the last columns' FP64 entries read (8 (k0 - kb)), the bulk update's
-    residues read (n_mod b bytes) and the factor's residue planes written
-    (2 n_mod b)."""
+    factorisations: order n, then order r), averaged per launch.  The launch
+    that solves panel ks = q b and factors block kn = ks + b, per row kn..n:
+    the panel's FP64 entries read and the factor written (16 b), the next
+    panel's entries read and updated (16 b), the last columns' FP64 entries
+    read (8 (kn - kb), kb = the bulk columns, a multiple of 64 at most
+    (q - 1) b), the bulk update's residues read (n_mod b bytes) and the
+    factor's residue planes written (2 n_mod b); the first launch of a
+    factorisation reads and writes one diagonal block."""
     tot, cnt = 0.0, 0
     for order in (n, r):
-        for k0 in range(0, order, b):
-            kb = (k0 - b) // 64 * 64 if k0 >= b else 0
-            rows = order - k0
-            tot += rows * (16 * b + 8 * (k0 - kb) + n_mod * b + 2 * n_mod * b)
+        np_ = (order + b - 1) // b
+        tot += 16 * b * b
+        cnt += 1
+        for q in range(np_ - 1):
+            ks, kn = q * b, q * b + b
+            kb = (q - 1) * b // 64 * 64 if q >= 1 else 0
+            rows = order - kn
+            tot += rows * (32 * b + 8 * (kn - kb) + n_mod * b + 2 * n_mod * b)
             cnt += 1
     return int(tot / max(cnt, 1))
 
