@@ -42,32 +42,39 @@ __device__ __forceinline__ void store_residues(uint64_t a, bool neg, int n_mod, 
     if (j >= n_mod) break;
     const uint32_t p = (uint32_t)modulus(j);
     const uint32_t c1 = (uint32_t)((1ull << 21) % p), c2 = (uint32_t)((1ull << 42) % p);
-    uint32_t r = (a2 * c2 + a1 * c1 + a0) % p;
-    if (neg && r) r = p - r;
-    const int v = (int)r > (int)(p / 2) ? (int)r - (int)p : (int)r;
-    o[j * plane] = __float2bfloat16_rn((float)v);
+    const uint32_t h = (p - 1) / 2;
+    // v = ((a + h) mod p) - h, |v| <= 64; the residue of -a is -v
+    const uint32_t r = (a2 * c2 + a1 * c1 + a0 + h) % p;
+    const float f = __int_as_float((int)(0x4B400000u - h) + (int)r) - 12582912.0f;
+    const unsigned short bits = (unsigned short)((__float_as_uint(f) >> 16) ^ (neg ? 0x8000u : 0u));
+    o[j * plane] = __ushort_as_bfloat16(bits);
   }
 }
 
-// BF16 bits of a small integer |v| <= 64 (exact): the float with those bits is
-// formed by adding v to 1.5 * 2^23 in the integer domain and subtracting it
-// back in FP32 (exact), and its top 16 bits are the BF16 encoding.
-__device__ __forceinline__ uint32_t small_int_bf16_bits(int v) {
-  const float f = __int_as_float(0x4B400000 + v) - 12582912.0f;
-  return __float_as_uint(f) >> 16;
-}
-
-// Balanced residue of (neg ? -a : a) modulo the j-th modulus, from the three
-// 21-bit chunks of a < 2^63 (one reduction of a value below 2^29).
+// The balanced residues of two integers modulo the J-th modulus as BF16
+// bits packed two per word (the first in the low half): a, b < 2^63 given by
+// their three 21-bit chunks, the signs in sgn (0x8000 for a negative first,
+// 0x80000000 for a negative second).  With h = (p - 1) / 2 the balanced
+// residue of a is v = ((a + h) mod p) - h (|v| <= 64), one reduction of a
+// value below 2^29; the offset h rides in the sum and in the FP32 constant
+// that turns r - h into its float, whose top 16 bits are its BF16 bits (an
+// integer of at most 7 bits is exact in BF16); the residue of -a is -v, a
+// sign flip of those bits.
 template <int J>
-__device__ __forceinline__ int residue21(uint32_t a0, uint32_t a1, uint32_t a2, bool neg) {
+__device__ __forceinline__ uint32_t residue_pair_bf16(uint32_t a0, uint32_t a1, uint32_t a2,
+                                                      uint32_t b0, uint32_t b1, uint32_t b2,
+                                                      uint32_t sgn) {
   constexpr uint32_t p = (uint32_t)modulus(J);
   constexpr uint32_t c1 = (uint32_t)((1ull << 21) % p);
   constexpr uint32_t c2 = (uint32_t)((1ull << 42) % p);
-  uint32_t r = (a2 * c2 + a1 * c1 + a0) % p;
-  if (neg && r) r = p - r;
-  return (int)r > (int)(p / 2) ? (int)r - (int)p : (int)r;
+  constexpr uint32_t h = (p - 1) / 2;
+  const uint32_t ra = (a2 * c2 + a1 * c1 + a0 + h) % p;
+  const uint32_t rb = (b2 * c2 + b1 * c1 + b0 + h) % p;
+  const float fa = __int_as_float((int)(0x4B400000u - h) + (int)ra) - 12582912.0f;
+  const float fb = __int_as_float((int)(0x4B400000u - h) + (int)rb) - 12582912.0f;
+  return __byte_perm(__float_as_uint(fa), __float_as_uint(fb), 0x7632) ^ sgn;
 }
+
 
 
 // ---------------------------------------------------------------------------

@@ -196,26 +196,22 @@ __global__ void row_expo_kernel(const double* X, int64_t ld, int trans, Dim rows
 // 256 threads, each one row x eight adjacent columns, so that every modulus
 // is written as one 16-byte store (eight BF16) per thread.
 template <int J>
-__device__ __forceinline__ void split_store8(const uint32_t (&c)[8][3], const bool (&ng)[8],
+__device__ __forceinline__ void split_store8(const uint32_t (&c)[8][3], const uint32_t (&sg)[4],
                                              int n_mod, uint4* dst, size_t plane_vec) {
   if (J >= n_mod) return;
   uint32_t w[4];
 #pragma unroll
-  for (int h = 0; h < 4; ++h) {
-    const uint32_t lo =
-        crt::small_int_bf16_bits(crt::residue21<J>(c[2 * h][0], c[2 * h][1], c[2 * h][2], ng[2 * h]));
-    const uint32_t hi = crt::small_int_bf16_bits(
-        crt::residue21<J>(c[2 * h + 1][0], c[2 * h + 1][1], c[2 * h + 1][2], ng[2 * h + 1]));
-    w[h] = lo | (hi << 16);
-  }
+  for (int h = 0; h < 4; ++h)
+    w[h] = crt::residue_pair_bf16<J>(c[2 * h][0], c[2 * h][1], c[2 * h][2], c[2 * h + 1][0],
+                                     c[2 * h + 1][1], c[2 * h + 1][2], sg[h]);
   dst[J * plane_vec] = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 template <int... Js>
 __device__ __forceinline__ void split_store8_all(std::integer_sequence<int, Js...>,
-                                                 const uint32_t (&c)[8][3], const bool (&ng)[8],
+                                                 const uint32_t (&c)[8][3], const uint32_t (&sg)[4],
                                                  int n_mod, uint4* dst, size_t plane_vec) {
-  (split_store8<Js>(c, ng, n_mod, dst, plane_vec), ...);
+  (split_store8<Js>(c, sg, n_mod, dst, plane_vec), ...);
 }
 
 // Batches (grid z): operand z at X + z zX, dims at rdev + z zR, its rows
@@ -274,8 +270,11 @@ __global__ void __launch_bounds__(256) split_kernel(const double* X, int64_t ld,
       c[2 * h + u][2] = (uint32_t)(a >> 42);
     }
   }
+  uint32_t sg[4];
+#pragma unroll
+  for (int h = 0; h < 4; ++h) sg[h] = (ng[2 * h] ? 0x8000u : 0u) | (ng[2 * h + 1] ? 0x80000000u : 0u);
   uint4* dst = reinterpret_cast<uint4*>(out + (size_t)i * kpad + k0 + 8 * g);
-  split_store8_all(std::make_integer_sequence<int, crt::kMaxMod>{}, c, ng, n_mod, dst,
+  split_store8_all(std::make_integer_sequence<int, crt::kMaxMod>{}, c, sg, n_mod, dst,
                    (size_t)plane_rows * (size_t)kpad / 8);
 }
 

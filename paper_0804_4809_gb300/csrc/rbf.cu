@@ -170,13 +170,9 @@ __device__ __forceinline__ void store8(const uint32_t (&c)[8][3], int n_mod, uin
   if (J >= n_mod) return;
   uint32_t w[4];
 #pragma unroll
-  for (int h = 0; h < 4; ++h) {
-    const uint32_t lo = crt::small_int_bf16_bits(
-        crt::residue21<J>(c[2 * h][0], c[2 * h][1], c[2 * h][2], false));
-    const uint32_t hi = crt::small_int_bf16_bits(
-        crt::residue21<J>(c[2 * h + 1][0], c[2 * h + 1][1], c[2 * h + 1][2], false));
-    w[h] = lo | (hi << 16);
-  }
+  for (int h = 0; h < 4; ++h)
+    w[h] = crt::residue_pair_bf16<J>(c[2 * h][0], c[2 * h][1], c[2 * h][2], c[2 * h + 1][0],
+                                     c[2 * h + 1][1], c[2 * h + 1][2], 0u);
   dst[J * plane_vec] = make_uint4(w[0], w[1], w[2], w[3]);
 }
 template <int... Js>
