@@ -108,6 +108,96 @@ __global__ void __launch_bounds__(256) dgemm_kernel(GemmParams p) {
   }
 }
 
+// Narrow outputs (N <= NC <= 16, no aliasing, whole matrix): a CTA owns 64
+// rows and every column of C, four threads per row each summing a quarter of
+// the K range for all NC columns (partial sums met by shuffles), so that no
+// FP64 instruction computes a padding column -- with the 64 x 64 tiles a
+// product of 4 columns would spend 15 of every 16 FMAs on padding.
+constexpr int kSkRows = 64, kSkK = 32;
+template <bool TA, bool TB, int NC>
+__global__ void __launch_bounds__(256) dgemm_skinny_kernel(GemmParams p) {
+  if (blockIdx.z) {
+    int64_t z = blockIdx.z, zo = 0;
+    if (p.nzi > 1) {
+      zo = z / p.nzi;
+      z -= zo * p.nzi;
+    }
+    p.A += z * p.zA + zo * p.oA;
+    p.B += z * p.zB + zo * p.oB;
+    p.C += z * p.zC + zo * p.oC;
+    p.M.off += z * p.zM;
+    p.N.off += z * p.zN;
+    p.K.off += z * p.zK;
+    p.rdev += z * p.zR + zo * p.oR;
+  }
+  const int64_t M = eval_dim(p.M, p.rdev);
+  const int64_t N = eval_dim(p.N, p.rdev);
+  const int64_t K = eval_dim(p.K, p.rdev);
+  const int64_t i0 = (int64_t)blockIdx.y * kSkRows;
+  if (i0 >= M || N <= 0) return;
+  __shared__ double As[kSkK][kSkRows + 1];
+  __shared__ double Bs[kSkK][NC];
+  const int tid = threadIdx.x;
+  const int r = tid >> 2, sub = tid & 3;
+  double acc[NC];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) acc[j] = 0.0;
+  for (int64_t k0 = 0; k0 < K; k0 += kSkK) {
+#pragma unroll
+    for (int q = 0; q < (kSkRows * kSkK) / 256; ++q) {
+      const int e = tid + 256 * q;
+      int i, k;
+      if (TA) { k = e / kSkRows; i = e % kSkRows; } else { i = e / kSkK; k = e % kSkK; }
+      const int64_t gi = i0 + i, gk = k0 + k;
+      double v = 0.0;
+      if (gi < M && gk < K) v = TA ? p.A[gk * p.lda + gi] : p.A[gi * p.lda + gk];
+      As[k][i] = v;
+    }
+    for (int e = tid; e < kSkK * NC; e += 256) {
+      int j, k;
+      if (TB) { j = e / kSkK; k = e % kSkK; } else { k = e / NC; j = e % NC; }
+      const int64_t gk = k0 + k;
+      double v = 0.0;
+      if (j < N && gk < K) v = TB ? p.B[j * p.ldb + gk] : p.B[gk * p.ldb + j];
+      Bs[k][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = sub; kk < kSkK; kk += 4) {
+      const double a = As[kk][r];
+#pragma unroll
+      for (int j = 0; j < NC; ++j) acc[j] = fma(a, Bs[kk][j], acc[j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], 1);
+    acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], 2);
+  }
+  const int64_t gi = i0 + r;
+  if (sub != 0 || gi >= M) return;
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    if (j >= N) break;
+    double* c = p.C + gi * p.ldc + j;
+    double out = p.alpha * acc[j];
+    if (p.beta != 0.0) out = fma(p.beta, *c, out);
+    *c = out;
+  }
+}
+
+template <int NC>
+cudaError_t launch_skinny(const GemmParams& p, bool transA, bool transB, cudaStream_t s) {
+  dim3 grid(1u, (unsigned)((p.M.max + kSkRows - 1) / kSkRows), (unsigned)(p.nz > 1 ? p.nz : 1));
+  if (grid.y > 65535u || grid.z > 65535u) return cudaErrorInvalidConfiguration;
+  if (!transA && !transB) dgemm_skinny_kernel<false, false, NC><<<grid, 256, 0, s>>>(p);
+  else if (!transA && transB) dgemm_skinny_kernel<false, true, NC><<<grid, 256, 0, s>>>(p);
+  else if (transA && !transB) dgemm_skinny_kernel<true, false, NC><<<grid, 256, 0, s>>>(p);
+  else dgemm_skinny_kernel<true, true, NC><<<grid, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
 template <int T>
 cudaError_t launch_tile(const GemmParams& p, bool transA, bool transB, cudaStream_t s) {
   dim3 grid((unsigned)((p.N.max + T - 1) / T), (unsigned)((p.M.max + T - 1) / T),
@@ -134,6 +224,13 @@ cudaError_t launch_dgemm(const GemmParams& p, bool transA, bool transB, cudaStre
     return cudaErrorInvalidValue;
   }
   const int64_t nz = p.nz > 1 ? p.nz : 1;
+  // narrow outputs over enough rows to fill the GPU (with few rows and a
+  // long K the tiled kernel's more, smaller CTAs spread the FP64 work wider)
+  if (Nmax <= 16 && !p.lower && nz * ((Mmax + kSkRows - 1) / kSkRows) >= 152) {
+    if (Nmax <= 4) return launch_skinny<4>(p, transA, transB, s);
+    if (Nmax <= 8) return launch_skinny<8>(p, transA, transB, s);
+    return launch_skinny<16>(p, transA, transB, s);
+  }
   auto tiles = [&](int64_t t) { return nz * ((Mmax + t - 1) / t) * ((Nmax + t - 1) / t); };
   if (tiles(64) >= 152 || (Mmax >= 64 && Nmax >= 64 && tiles(32) > 4 * 152))
     return launch_tile<64>(p, transA, transB, s);
