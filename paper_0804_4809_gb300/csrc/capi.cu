@@ -687,6 +687,81 @@ int front_rank(const Ctx& c, const double* G, int64_t ldg, bool compact) {
   return rank_from_gram(c, compact);
 }
 
+// One product of a triangular-inverse level for all its nodes at once, in the
+// exact-slice arithmetic (53-bit rows): node z (lo = 2 s z, mid = lo + s) forms
+//   C_z = alpha A_z B_z,   A_z: rows mid.. x K, B_z: K x columns lo..,
+// from the node-0 blocks A0, B0, C0 (ld nA; node z's blocks 2 s (nA + 1)
+// further on), with the node-0 dims rows (of A and C), K and cols (of B and
+// C) moving by -2s per node.  Both operands' residues are stacked node after
+// node, so the level is one split per operand, one block-diagonal tensor-core
+// product (blocks s x s, the nodes past the rank skipped) and one
+// reconstruction writing each node's block in place.  False: the scratch is
+// too small or the shape is outside the block product's limits (the caller
+// then takes the per-node products).
+bool level_product_fits(const Plan& p, int64_t s, int64_t nodes) {
+  const int64_t bk = crt_block_k(), bm = crt_block_m();
+  if (s % bm || s > kCrtMaxK || nodes < 1 || nodes > 65535) return false;
+  const int nm = crt_moduli_for(s, 53, 53);
+  if (nm < 1 || nm > kRecBlockMaxMod) return false;
+  const int64_t kpad = (s + bk - 1) / bk * bk, tot = nodes * s;
+  const size_t need = 2 * (2 * (size_t)nm * tot * kpad + 1024) + (size_t)nm * tot * s + 1024 +
+                      2 * sizeof(int32_t) * (size_t)tot + 4096;
+  return p.crt && need <= p.crt_bytes;
+}
+
+cudaError_t level_product(const Ctx& c, int64_t s, int64_t nodes, const double* A0, Dim rows,
+                          Dim K, const double* B0, Dim cols, double* C0, double alpha) {
+  const Plan& p = *c.p;
+  const int64_t nA = p.nA, bk = crt_block_k();
+  const int nm = crt_moduli_for(s, 53, 53);
+  const int64_t kpad = (s + bk - 1) / bk * bk, tot = nodes * s;
+  const int64_t zX = 2 * s * nA + 2 * s, zoff = -2 * s;
+  char* w = (char*)p.crt;
+  size_t off = 0;
+  auto take = [&](size_t x) {
+    off = (off + 1023) / 1024 * 1024;
+    char* q = w + off;
+    off += x;
+    return q;
+  };
+  void* SA = take(2 * (size_t)nm * tot * kpad);
+  void* SB = take(2 * (size_t)nm * tot * kpad);
+  uint8_t* R = (uint8_t*)take((size_t)nm * tot * s);
+  int32_t* EA = (int32_t*)take(sizeof(int32_t) * (size_t)tot);
+  int32_t* EB = (int32_t*)take(sizeof(int32_t) * (size_t)tot);
+  const int64_t* rdev = c.rdev();
+  KernelTimer t;
+  cudaError_t e = cudaMemsetAsync(EA, 0, (size_t)((char*)(EB + tot) - (char*)EA), c.s);
+  if (e != cudaSuccess) return e;
+  // A_z row-wise; B_z through its transpose (rows = the output's columns)
+  e = crt_row_exponents_batched(A0, nA, 0, rows, K, rdev, s, EA, p.st, (int)nodes, zX, 0, s, c.s,
+                                &t, zoff);
+  if (e == cudaSuccess)
+    e = crt_row_exponents_batched(B0, nA, 1, cols, K, rdev, s, EB, p.st, (int)nodes, zX, 0, s,
+                                  c.s, &t, zoff);
+  if (e == cudaSuccess)
+    e = crt_split_batched(A0, nA, 0, rows, K, rdev, s, kpad, EA, nm, 53, SA, (int)nodes, zX, 0,
+                          c.s, &t, zoff);
+  if (e == cudaSuccess)
+    e = crt_split_batched(B0, nA, 1, cols, K, rdev, s, kpad, EB, nm, 53, SB, (int)nodes, zX, 0,
+                          c.s, &t, zoff);
+  if (e != cudaSuccess) return e;
+  BlockPlace place;
+  place.M = rows;
+  place.N = cols;
+  place.zoff = zoff;
+  place.zC = zX;
+  GemmParams fl;  // traced work: the nodes' s x s x s products
+  std::memset(&fl, 0, sizeof(fl));
+  fl.M = fl.N = hdim(s);
+  fl.K = hdim(tot);
+  e = crt_mma(SA, tot, 0, SB, tot, 0, kpad, s, nm, hdim(tot), hdim(tot), rdev, 0, R, tot, s,
+              &p.st->status, c.s, &t, &fl, 0, (int)s, 0, &place);
+  if (e != cudaSuccess) return e;
+  return crt_reconstruct(R, tot, s, hdim(tot), hdim(s), rdev, EA, EB, 53, 53, alpha, 0.0, C0, nA,
+                         0, nm, c.s, &t, (int)s, &place);
+}
+
 // W = U^-1 for the lower-triangular U (order r <= nA, ld nA), given the
 // inverted b x b diagonal blocks already in W (ld nA); Tmp is nA x nA scratch.  Recursive halving, done level
 // by level from the smallest blocks up: a node [lo, lo + 2s) with children
@@ -694,8 +769,8 @@ int front_rank(const Ctx& c, const double* G, int64_t ldg, bool compact) {
 //   W21 = -W22 (U21 W11)        (bufM holds U21 W11)
 // All nodes of a level have the same size (the block count is padded to a
 // power of two; nodes past the rank are empty), so a level is one batched
-// FP64 launch per product when its products are small, and per-node
-// tensor-core products when they are large.
+// FP64 launch per product when its products are small, and one batched
+// tensor-core product per product (level_product) when they are large.
 int tri_inverse(const Ctx& c, const double* U, double* W, double* Tmp) {
   const Plan& p = *c.p;
   const int64_t nA = p.nA, b = p.b;
@@ -704,7 +779,14 @@ int tri_inverse(const Ctx& c, const double* U, double* W, double* Tmp) {
   for (int64_t s = b; s < nb * b; s <<= 1) {
     const int64_t nodes = (nb * b) / (2 * s);
     const Dim rows = rdim(-s, s), cols = rdim(0, s);  // node 0: mid = s, lo = 0
-    if (prod_kind(p, S_PROD, s, s, s) == PK_FP64) {
+    // nodes whose rows start inside the matrix (the others are empty)
+    const int64_t live = nA > s ? (nA - s + 2 * s - 1) / (2 * s) : 0;
+    if (prod_kind(p, S_PROD, live * s, s, s) == PK_EXACT && level_product_fits(p, s, live)) {
+      // Tmp21 = U21 W11, then W21 = -W22 Tmp21
+      CK(level_product(c, s, live, U + s * nA, rows, cols, W, cols, Tmp + s * nA, 1.0));
+      CK(level_product(c, s, live, W + s * nA + s, rows, rows, Tmp + s * nA, cols, W + s * nA,
+                       -1.0));
+    } else if (prod_kind(p, S_PROD, s, s, s) == PK_FP64) {
       auto batched = [&](const double* A, const double* B, double* C, Dim M, Dim N, Dim K,
                          double alpha) -> cudaError_t {
         GemmParams g;

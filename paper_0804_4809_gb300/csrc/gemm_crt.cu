@@ -143,17 +143,19 @@ __device__ __forceinline__ bool nonfinite_bits(uint64_t b) { return ((b >> 52) &
 // trans = 0: row i is contiguous (X[i*ld + k]); one warp per row.
 // trans = 1: row i of op(X) is column i of X; a 32-row x 8-chunk block,
 //            coalesced over i, each thread scanning a slice of k.
-// Batches (grid z): operand z at X + z zX, its dims read at rdev + z zR,
-// its state st + z zSt, its exponents E + z zE.
+// Batches (grid z): operand z at X + z zX, its dims read at rdev + z zR with
+// z zoff added to both offsets, its state st + z zSt, its exponents E + z zE.
 __global__ void row_expo_kernel(const double* X, int64_t ld, int trans, Dim rowsd, Dim colsd,
                                 const int64_t* rdev, int32_t* E, DevState* st, int64_t zX,
-                                int64_t zR, int64_t zE, int64_t zSt) {
+                                int64_t zR, int64_t zE, int64_t zSt, int64_t zoff) {
   {
     const int64_t z = blockIdx.z;
     X += z * zX;
     rdev += z * zR;
     E += z * zE;
     st += z * zSt;
+    rowsd.off += z * zoff;
+    colsd.off += z * zoff;
   }
   const int64_t rows = eval_dim(rowsd, rdev), cols = eval_dim(colsd, rdev);
   int emax = 0, bad = 0;
@@ -214,14 +216,16 @@ __device__ __forceinline__ void split_store8_all(std::integer_sequence<int, Js..
   (split_store8<Js>(c, sg, n_mod, dst, plane_vec), ...);
 }
 
-// Batches (grid z): operand z at X + z zX, dims at rdev + z zR, its rows
-// z zrow onwards in the planes (and in E); plane_rows = rows of one plane.
+// Batches (grid z): operand z at X + z zX, dims at rdev + z zR with z zoff
+// added to both offsets, its rows z zrow onwards in the planes (and in E);
+// plane_rows = rows of one plane.
 __global__ void __launch_bounds__(256) split_kernel(const double* X, int64_t ld, int trans,
                                                     Dim rowsd, Dim colsd, int64_t rows_max,
                                                     int64_t kpad, const int64_t* rdev,
                                                     const int32_t* E, int n_mod, int beta,
                                                     bf16* out, int64_t zX, int64_t zR,
-                                                    int64_t zrow, int64_t plane_rows) {
+                                                    int64_t zrow, int64_t plane_rows,
+                                                    int64_t zoff) {
   // rows padded to 66 words: 16-byte aligned, four banks apart
   __shared__ __align__(16) uint64_t tile[32][66];
   {
@@ -230,6 +234,8 @@ __global__ void __launch_bounds__(256) split_kernel(const double* X, int64_t ld,
     rdev += z * zR;
     E += z * zrow;
     out += z * zrow * kpad;
+    rowsd.off += z * zoff;
+    colsd.off += z * zoff;
   }
   const int64_t rows = eval_dim(rowsd, rdev), cols = eval_dim(colsd, rdev);
   const int64_t i0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 64;
@@ -440,6 +446,9 @@ struct MmaParams {
                             // matrices); tiles and lower refer to one block, R holds
                             // [n_mod][Mpad][blk] (the block's own columns)
   int32_t tiles_blk;        // tiles per block
+  int32_t bdims;            // block mode: block z has rows < bM and columns < bN (z bzoff
+  int64_t bzoff;            // added to both offsets); the tiles past them are skipped
+  Dim bM, bN;
   uint8_t* R;               // residues [n_mod][Mpad][Npad]
   int64_t Mpad, Npad;
   int32_t* status;          // DevState::status
@@ -522,10 +531,18 @@ __global__ void __launch_bounds__(192, 1)
     j = (int)(q / p.tiles);
     int t = (int)(q - (int64_t)j * p.tiles);
     int64_t base = 0;  // block-diagonal mode: first row and column of the block
+    int64_t bmv = BM * (int64_t)p.tiles_m, bnv = BN * (int64_t)p.tiles_n;  // block's extent
     if (p.blk) {
       const int zb = t / p.tiles_blk;
       t -= zb * p.tiles_blk;
       base = (int64_t)zb * p.blk;
+      if (p.bdims) {
+        Dim dm = p.bM, dn = p.bN;
+        dm.off += zb * p.bzoff;
+        dn.off += zb * p.bzoff;
+        bmv = eval_dim(dm, p.rdev);
+        bnv = eval_dim(dn, p.rdev);
+      }
     }
     int ty, tx;
     if (!p.lower) {
@@ -546,9 +563,10 @@ __global__ void __launch_bounds__(192, 1)
     m0 = (int64_t)ty * BM;
     n0 = (int64_t)tx * BN;
     const bool upper = p.lower && n0 > m0 + BM - 1;
+    const bool inside = m0 < bmv && n0 < bnv;
     m0 += base;
     n0 += base;
-    return m0 < M && n0 < N && !upper;
+    return m0 < M && n0 < N && !upper && inside;
   };
 
   if (threadIdx.x == 0) {
@@ -747,8 +765,13 @@ struct ReconParams {
   int64_t ldc;
   int32_t lower;
   int32_t blk;  // > 0: block-diagonal output (reconstruct_words_kernel only): row i
-                // belongs to block i / blk, its columns j are the block's own
-                // (EB[(i / blk) blk + j]), lower is within the block
+                // belongs to block z = i / blk, its columns j are the block's own
+                // (EB[z blk + j]), lower is within the block; the row goes to
+                // C + z zC + (i - z blk) ldc
+  int32_t bdims;  // block mode: block z keeps its rows il < bM and columns j < bN,
+                  // both with z zoff added to their offsets
+  int64_t zC, zoff;
+  Dim bM, bN;
 };
 
 // CRT constants of every moduli count, in device memory (uploaded once per
@@ -845,6 +868,7 @@ __global__ void __launch_bounds__(256, 2) reconstruct_kernel(ReconParams p, int 
 // columns per block.
 constexpr int kRecWordsMaxMod = 22;
 constexpr int kRecWords4MaxMod = 19;
+static_assert(kRecWordsMaxMod == kRecBlockMaxMod, "block-diagonal reconstruction limit");
 constexpr int kRecWRows = 8, kRecWCols = 128;
 struct __align__(16) RecWShared {
   uint32_t Mj[crt::kMaxMod][8];  // P / p_j, limbs 0..4, padded
@@ -955,8 +979,19 @@ __global__ void __launch_bounds__(256) reconstruct_words_kernel(ReconParams p, i
   const int64_t i = (int64_t)blockIdx.y * kRecWRows + (threadIdx.x >> 5);
   const int64_t j0 = (int64_t)blockIdx.x * kRecWCols + 4 * (threadIdx.x & 31);
   const int64_t il = p.blk ? i % p.blk : i;       // row within its block
+  const int64_t zb = p.blk ? i / p.blk : 0;
   const int32_t* EB = p.blk ? p.EB + (i - il) : p.EB;
-  if (i >= M || j0 >= N || (p.lower && j0 > il)) return;
+  int64_t Nv = N;
+  bool row_ok = i < M;
+  if (p.bdims) {
+    Dim bm = p.bM, bn = p.bN;
+    bm.off += zb * p.zoff;
+    bn.off += zb * p.zoff;
+    row_ok = row_ok && il < eval_dim(bm, p.rdev);
+    Nv = eval_dim(bn, p.rdev);
+  }
+  if (!row_ok || j0 >= Nv || (p.lower && j0 > il)) return;
+  double* crow = p.C + (p.blk ? zb * p.zC + il * p.ldc : i * p.ldc);
   const size_t plane = (size_t)p.Mpad * (size_t)p.Npad;
   const uint32_t* r = reinterpret_cast<const uint32_t*>(p.R + i * p.Npad + j0);
   uint64_t acc[4][NL];
@@ -992,7 +1027,7 @@ __global__ void __launch_bounds__(256) reconstruct_words_kernel(ReconParams p, i
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     const int64_t j = j0 + e;
-    if (j >= N || (p.lower && j > il)) continue;
+    if (j >= Nv || (p.lower && j > il)) continue;
     // S = sum_j t_j P/p_j (< n P) as (s2:s1:s0)
     uint32_t Sl[6];
     uint64_t carry = 0;
@@ -1028,7 +1063,7 @@ __global__ void __launch_bounds__(256) reconstruct_words_kernel(ReconParams p, i
       x0 = m0;
     }
     double v = u192_to_double(neg, NL > 4 ? x2 : 0, x1, x0, sa + EB[j] - 1022 - p.betaB);
-    double* cp = p.C + i * p.ldc + j;
+    double* cp = crow + j;
     if (!plain_store(p.alpha, p.beta)) v = scale_add(v, p.alpha, p.beta, cp);
     *cp = v;
   }
@@ -1227,16 +1262,18 @@ cudaError_t crt_row_exponents(const double* X, int64_t ld, int tview, Dim rows, 
 cudaError_t crt_row_exponents_batched(const double* X, int64_t ld, int tview, Dim rows, Dim K,
                                       const int64_t* rdev, int64_t rows_max, int32_t* E,
                                       DevState* st, int nz, int64_t zX, int64_t zR, int64_t zE,
-                                      cudaStream_t s, KernelTimer* timer) {
+                                      cudaStream_t s, KernelTimer* timer, int64_t zoff) {
   if (nz < 1 || nz > 65535) return cudaErrorInvalidValue;
-  const int64_t zSt = nz > 1 ? 1 : 0;
+  // operands of separate problems have their own states; the nodes of one
+  // matrix (zR = 0) share its state
+  const int64_t zSt = (nz > 1 && zR != 0) ? 1 : 0;
   return timer->run(KT_SPLIT, s, [&] {
     if (!tview)
       row_expo_kernel<<<dim3((unsigned)((rows_max * 32 + 255) / 256), 1, (unsigned)nz), 256, 0,
-                        s>>>(X, ld, 0, rows, K, rdev, E, st, zX, zR, zE, zSt);
+                        s>>>(X, ld, 0, rows, K, rdev, E, st, zX, zR, zE, zSt, zoff);
     else
       row_expo_kernel<<<dim3((unsigned)((rows_max + 31) / 32), 16, (unsigned)nz), 256, 0, s>>>(
-          X, ld, 1, rows, K, rdev, E, st, zX, zR, zE, zSt);
+          X, ld, 1, rows, K, rdev, E, st, zX, zR, zE, zSt, zoff);
     return cudaGetLastError();
   });
 }
@@ -1251,13 +1288,14 @@ cudaError_t crt_split(const double* X, int64_t ld, int tview, Dim rows, Dim K, c
 cudaError_t crt_split_batched(const double* X, int64_t ld, int tview, Dim rows, Dim K,
                               const int64_t* rdev, int64_t rows_max, int64_t kpad,
                               const int32_t* E, int n_mod, int beta, void* out, int nz,
-                              int64_t zX, int64_t zR, cudaStream_t s, KernelTimer* timer) {
+                              int64_t zX, int64_t zR, cudaStream_t s, KernelTimer* timer,
+                              int64_t zoff) {
   if (nz < 1 || nz > 65535 || rows_max % 32) return cudaErrorInvalidValue;
   dim3 grid((unsigned)(kpad / 64), (unsigned)((rows_max + 31) / 32), (unsigned)nz);
   const int64_t zrow = nz > 1 ? rows_max : 0;
   return timer->run(KT_SPLIT, s, [&] {
     split_kernel<<<grid, 256, 0, s>>>(X, ld, tview, rows, K, rows_max, kpad, rdev, E, n_mod, beta,
-                                      (bf16*)out, zX, zR, zrow, rows_max * nz);
+                                      (bf16*)out, zX, zR, zrow, rows_max * nz, zoff);
     return cudaGetLastError();
   });
 }
@@ -1266,7 +1304,7 @@ cudaError_t crt_mma(const void* SA, int64_t a_rows, int a_row0, const void* SB, 
                     int b_row0, int64_t kpad, int64_t kuse, int n_mod, Dim M, Dim N,
                     const int64_t* rdev, int lower, uint8_t* R, int64_t Mpad, int64_t Npad,
                     int32_t* status, cudaStream_t s, KernelTimer* timer, const GemmParams* fl,
-                    int max_ctas, int blk, int bn) {
+                    int max_ctas, int blk, int bn, const BlockPlace* bplace) {
   const int64_t Mmax = M.max, Nmax = N.max;
   if (Mmax <= 0 || Nmax <= 0) return cudaSuccess;
   int BN = (Nmax >= 2048) ? 256 : (Nmax <= 32 ? 32 : 128);
@@ -1287,6 +1325,12 @@ cudaError_t crt_mma(const void* SA, int64_t a_rows, int a_row0, const void* SB, 
   mp.n_mod = n_mod;
   mp.lower = lower;
   mp.blk = blk;
+  if (blk && bplace) {
+    mp.bdims = 1;
+    mp.bzoff = bplace->zoff;
+    mp.bM = bplace->M;
+    mp.bN = bplace->N;
+  }
   mp.R = R;
   mp.Mpad = Mpad;
   mp.Npad = Npad;
@@ -1328,7 +1372,8 @@ const crt::Consts* crt_consts_device() {
 cudaError_t crt_reconstruct(const uint8_t* R, int64_t Mpad, int64_t Npad, Dim M, Dim N,
                             const int64_t* rdev, const int32_t* EA, const int32_t* EB, int betaA,
                             int betaB, double alpha, double beta, double* C, int64_t ldc,
-                            int lower, int n_mod, cudaStream_t s, KernelTimer* timer, int blk) {
+                            int lower, int n_mod, cudaStream_t s, KernelTimer* timer, int blk,
+                            const BlockPlace* bplace) {
   if (!crt_consts_device()) return cudaErrorInitializationError;
   if (blk && (n_mod > kRecWordsMaxMod || Npad != blk)) return cudaErrorInvalidValue;
   ReconParams rp;
@@ -1348,6 +1393,17 @@ cudaError_t crt_reconstruct(const uint8_t* R, int64_t Mpad, int64_t Npad, Dim M,
   rp.ldc = ldc;
   rp.lower = lower;
   rp.blk = blk;
+  rp.bdims = 0;
+  rp.zC = (int64_t)blk * ldc;
+  rp.zoff = 0;
+  rp.bM = rp.bN = hdim(0);
+  if (blk && bplace) {
+    rp.bdims = 1;
+    rp.zC = bplace->zC;
+    rp.zoff = bplace->zoff;
+    rp.bM = bplace->M;
+    rp.bN = bplace->N;
+  }
   // small outputs (factorisation panels): latency-bound, four lanes per output
   // (block-diagonal outputs always take the word-wise kernel)
   const bool small = !blk && M.max * N.max <= ((int64_t)1 << 16);

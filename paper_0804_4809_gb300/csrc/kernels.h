@@ -86,32 +86,49 @@ cudaError_t crt_row_exponents(const double* X, int64_t ld, int tview, Dim rows, 
 cudaError_t crt_split(const double* X, int64_t ld, int tview, Dim rows, Dim K, const int64_t* rdev,
                       int64_t rows_max, int64_t kpad, const int32_t* E, int n_mod, int beta,
                       void* out, cudaStream_t s, KernelTimer* timer);
+// Largest moduli count of a block-diagonal reconstruction (crt_reconstruct
+// with blk > 0).
+constexpr int kRecBlockMaxMod = 22;
+// Placement of the blocks of a block-diagonal output: block z keeps its rows
+// i < M and columns j < N (each with z zoff added to its offset) and writes
+// them to C + z zC + i ldc + j.
+struct BlockPlace {
+  Dim M, N;
+  int64_t zoff, zC;
+};
 // blk > 0: block-diagonal product (the Gram matrices of a batch stacked
 // along M = N): only the tiles inside the blk x blk diagonal blocks, R holds
-// [n_mod][Mpad][blk]; bn: output tile width (0 = by size; 128 or 256).
+// [n_mod][Mpad][blk]; bn: output tile width (0 = by size; 128 or 256);
+// bplace: the tiles past a block's rows or columns (bplace->M, N) skipped.
 cudaError_t crt_mma(const void* SA, int64_t a_rows, int a_row0, const void* SB, int64_t b_rows,
                     int b_row0, int64_t kpad, int64_t kuse, int n_mod, Dim M, Dim N,
                     const int64_t* rdev, int lower, uint8_t* R, int64_t Mpad, int64_t Npad,
                     int32_t* status, cudaStream_t s, KernelTimer* timer, const GemmParams* fl,
-                    int max_ctas = 0, int blk = 0, int bn = 0);
+                    int max_ctas = 0, int blk = 0, int bn = 0,
+                    const BlockPlace* bplace = nullptr);
 // blk > 0: the block-diagonal output of crt_mma (rows Mpad, Npad = blk),
-// written to C (row i, its block's column j) with EB per block.
+// written to C (row i, its block's column j) with EB per block; bplace: the
+// blocks placed and clipped as it says (default: block z at rows z blk of C,
+// every row and column kept).
 cudaError_t crt_reconstruct(const uint8_t* R, int64_t Mpad, int64_t Npad, Dim M, Dim N,
                             const int64_t* rdev, const int32_t* EA, const int32_t* EB, int betaA,
                             int betaB, double alpha, double beta, double* C, int64_t ldc,
                             int lower, int n_mod, cudaStream_t s, KernelTimer* timer,
-                            int blk = 0);
+                            int blk = 0, const BlockPlace* bplace = nullptr);
 // Batches of nz operands (z-major): operand z at X + z zX with its dims
-// read at rdev + z zR; its exponents and residue rows follow one another
-// (rows z rows_max .. in E and in the planes, plane rows = nz rows_max).
+// read at rdev + z zR and z zoff added to their offsets; its exponents and
+// residue rows follow one another (rows z rows_max .. in E and in the planes,
+// plane rows = nz rows_max).  zR = 0: the operands are blocks of one matrix
+// and share its state.
 cudaError_t crt_row_exponents_batched(const double* X, int64_t ld, int tview, Dim rows, Dim K,
                                       const int64_t* rdev, int64_t rows_max, int32_t* E,
                                       DevState* st, int nz, int64_t zX, int64_t zR, int64_t zE,
-                                      cudaStream_t s, KernelTimer* timer);
+                                      cudaStream_t s, KernelTimer* timer, int64_t zoff = 0);
 cudaError_t crt_split_batched(const double* X, int64_t ld, int tview, Dim rows, Dim K,
                               const int64_t* rdev, int64_t rows_max, int64_t kpad,
                               const int32_t* E, int n_mod, int beta, void* out, int nz,
-                              int64_t zX, int64_t zR, cudaStream_t s, KernelTimer* timer);
+                              int64_t zX, int64_t zR, cudaStream_t s, KernelTimer* timer,
+                              int64_t zoff = 0);
 
 // chol_queue.cu: the factorisations of a batch in one persistent launch
 // fed by a device task queue (tasks on 32 x 32 tiles, listed in dependency
