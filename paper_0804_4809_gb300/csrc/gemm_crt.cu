@@ -159,18 +159,27 @@ __global__ void row_expo_kernel(const double* X, int64_t ld, int trans, Dim rows
   }
   const int64_t rows = eval_dim(rowsd, rdev), cols = eval_dim(colsd, rdev);
   int emax = 0, bad = 0;
+  auto take = [&](uint64_t b) {
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e == 0x7FF) bad = 1;
+    else if ((b << 1) != 0 && e > emax) emax = e;
+  };
   int64_t i;
   if (!trans) {
     i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i < rows) {
       const uint64_t* row = reinterpret_cast<const uint64_t*>(X + i * ld);
-      for (int64_t k = lane; k < cols; k += 32) {
-        const uint64_t b = row[k];
-        const int e = (int)((b >> 52) & 0x7FF);
-        if (e == 0x7FF) bad = 1;
-        else if ((b << 1) != 0 && e > emax) emax = e;
+      int64_t k = lane;
+      // four loads in flight per lane
+      for (; k + 96 < cols; k += 128) {
+        const uint64_t b0 = row[k], b1 = row[k + 32], b2 = row[k + 64], b3 = row[k + 96];
+        take(b0);
+        take(b1);
+        take(b2);
+        take(b3);
       }
+      for (; k < cols; k += 32) take(row[k]);
     }
     for (int o = 16; o; o >>= 1) {
       emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
@@ -182,13 +191,19 @@ __global__ void row_expo_kernel(const double* X, int64_t ld, int trans, Dim rows
     const int64_t kc = (cols + gridDim.y * 8 - 1) / (gridDim.y * 8);
     const int64_t kb = ((int64_t)blockIdx.y * 8 + (threadIdx.x >> 5)) * kc;
     const int64_t ke = kb + kc < cols ? kb + kc : cols;
-    if (i < rows)
-      for (int64_t k = kb; k < ke; ++k) {
-        const uint64_t b = reinterpret_cast<const uint64_t*>(X)[k * ld + i];
-        const int e = (int)((b >> 52) & 0x7FF);
-        if (e == 0x7FF) bad = 1;
-        else if ((b << 1) != 0 && e > emax) emax = e;
+    if (i < rows) {
+      const uint64_t* col = reinterpret_cast<const uint64_t*>(X) + i;
+      int64_t k = kb;
+      for (; k + 3 < ke; k += 4) {
+        const uint64_t b0 = col[k * ld], b1 = col[(k + 1) * ld], b2 = col[(k + 2) * ld],
+                       b3 = col[(k + 3) * ld];
+        take(b0);
+        take(b1);
+        take(b2);
+        take(b3);
       }
+      for (; k < ke; ++k) take(col[k * ld]);
+    }
   }
   if (i < rows && emax > 0) atomicMax(&E[i], emax);
   if (bad) atomicOr(&st->status, ST_NONFINITE);
@@ -225,7 +240,7 @@ __global__ void __launch_bounds__(256) split_kernel(const double* X, int64_t ld,
                                                     const int32_t* E, int n_mod, int beta,
                                                     bf16* out, int64_t zX, int64_t zR,
                                                     int64_t zrow, int64_t plane_rows,
-                                                    int64_t zoff) {
+                                                    int64_t zoff, int trim) {
   // rows padded to 66 words: 16-byte aligned, four banks apart
   __shared__ __align__(16) uint64_t tile[32][66];
   {
@@ -239,6 +254,9 @@ __global__ void __launch_bounds__(256) split_kernel(const double* X, int64_t ld,
   }
   const int64_t rows = eval_dim(rowsd, rdev), cols = eval_dim(colsd, rdev);
   const int64_t i0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 64;
+  // trim: the product reads only the K blocks inside the device-side K (and
+  // always the first), so the blocks past it are not written
+  if (trim && k0 > 0 && k0 >= cols) return;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   const uint64_t* Xb = reinterpret_cast<const uint64_t*>(X);
   if (!trans) {
@@ -437,6 +455,8 @@ struct MmaParams {
   int32_t a_row0, b_row0;   // first residue row of op(A) / of the N x K view of op(B)
   const int64_t* rdev;
   int32_t nk;               // K / BK (K padded)
+  int32_t kdev;             // 1: only the K blocks inside Kd (a device-side K) are summed
+  Dim Kd;
   int32_t n_mod;
   int32_t tiles_m, tiles_n;  // output tiles (BM x BN) covering M.max x N.max
   int32_t tiles;             // tiles in the enumeration (the lower ones only when lower)
@@ -595,7 +615,13 @@ __global__ void __launch_bounds__(192, 1)
   const uint32_t tmem = sm.tmem_base;
   volatile int* abort = &sm.abort;
   constexpr uint32_t kStageBytes = PL * (BM + BN) * BK * sizeof(bf16);
-  const int nk = p.nk;
+  // K blocks past a device-side K hold zero residues: not summed (at least
+  // one block, so that every accumulator is written)
+  int nk = p.nk;
+  if (p.kdev) {
+    const int64_t kv = (eval_dim(p.Kd, p.rdev) + BK - 1) / BK;
+    nk = kv < 1 ? 1 : (kv < nk ? (int)kv : nk);
+  }
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
@@ -1280,22 +1306,23 @@ cudaError_t crt_row_exponents_batched(const double* X, int64_t ld, int tview, Di
 
 cudaError_t crt_split(const double* X, int64_t ld, int tview, Dim rows, Dim K, const int64_t* rdev,
                       int64_t rows_max, int64_t kpad, const int32_t* E, int n_mod, int beta,
-                      void* out, cudaStream_t s, KernelTimer* timer) {
+                      void* out, cudaStream_t s, KernelTimer* timer, bool trim_k) {
   return crt_split_batched(X, ld, tview, rows, K, rdev, rows_max, kpad, E, n_mod, beta, out, 1, 0,
-                           0, s, timer);
+                           0, s, timer, 0, trim_k);
 }
 
 cudaError_t crt_split_batched(const double* X, int64_t ld, int tview, Dim rows, Dim K,
                               const int64_t* rdev, int64_t rows_max, int64_t kpad,
                               const int32_t* E, int n_mod, int beta, void* out, int nz,
                               int64_t zX, int64_t zR, cudaStream_t s, KernelTimer* timer,
-                              int64_t zoff) {
+                              int64_t zoff, bool trim_k) {
   if (nz < 1 || nz > 65535 || rows_max % 32) return cudaErrorInvalidValue;
   dim3 grid((unsigned)(kpad / 64), (unsigned)((rows_max + 31) / 32), (unsigned)nz);
   const int64_t zrow = nz > 1 ? rows_max : 0;
   return timer->run(KT_SPLIT, s, [&] {
     split_kernel<<<grid, 256, 0, s>>>(X, ld, tview, rows, K, rows_max, kpad, rdev, E, n_mod, beta,
-                                      (bf16*)out, zX, zR, zrow, rows_max * nz, zoff);
+                                      (bf16*)out, zX, zR, zrow, rows_max * nz, zoff,
+                                      trim_k ? 1 : 0);
     return cudaGetLastError();
   });
 }
@@ -1304,7 +1331,8 @@ cudaError_t crt_mma(const void* SA, int64_t a_rows, int a_row0, const void* SB, 
                     int b_row0, int64_t kpad, int64_t kuse, int n_mod, Dim M, Dim N,
                     const int64_t* rdev, int lower, uint8_t* R, int64_t Mpad, int64_t Npad,
                     int32_t* status, cudaStream_t s, KernelTimer* timer, const GemmParams* fl,
-                    int max_ctas, int blk, int bn, const BlockPlace* bplace) {
+                    int max_ctas, int blk, int bn, const BlockPlace* bplace,
+                    const Dim* kdim) {
   const int64_t Mmax = M.max, Nmax = N.max;
   if (Mmax <= 0 || Nmax <= 0) return cudaSuccess;
   int BN = (Nmax >= 2048) ? 256 : (Nmax <= 32 ? 32 : 128);
@@ -1322,6 +1350,10 @@ cudaError_t crt_mma(const void* SA, int64_t a_rows, int a_row0, const void* SB, 
   mp.rdev = rdev;
   mp.nk = (int)((kuse + BK - 1) / BK);
   if (mp.nk < 1) mp.nk = 1;
+  if (kdim && kdim->sel) {
+    mp.kdev = 1;
+    mp.Kd = *kdim;
+  }
   mp.n_mod = n_mod;
   mp.lower = lower;
   mp.blk = blk;
@@ -1531,19 +1563,23 @@ cudaError_t launch_crt_gemm(const CrtGemm& g, cudaStream_t s, KernelTimer* timer
   if (e != cudaSuccess) return e;
   // op(A): rows x K; transA: element (i,k) at A[k*lda + i].  op(B) is K x N;
   // its N x K view: element (j,k) = transB ? B[j*ldb + k] : B[k*ldb + j].
+  // a device-side K: the residue planes end at its last block and the
+  // product sums only up to there
+  const bool kdev = p.K.sel != 0;
   e = crt_row_exponents(p.A, p.lda, g.transA ? 1 : 0, p.M, p.K, p.rdev, mpad, EA, g.st, s, timer);
   if (e == cudaSuccess)
     e = crt_split(p.A, p.lda, g.transA ? 1 : 0, p.M, p.K, p.rdev, mpad, kpad, EA, n_mod, g.betaA,
-                  SA, s, timer);
+                  SA, s, timer, kdev);
   if (e == cudaSuccess && !same) {
     e = crt_row_exponents(p.B, p.ldb, g.transB ? 0 : 1, p.N, p.K, p.rdev, npad, EB, g.st, s, timer);
     if (e == cudaSuccess)
       e = crt_split(p.B, p.ldb, g.transB ? 0 : 1, p.N, p.K, p.rdev, npad, kpad, EB, n_mod, g.betaB,
-                    SB, s, timer);
+                    SB, s, timer, kdev);
   }
   if (e != cudaSuccess) return e;
   e = crt_mma(SA, mpad, 0, SB, same ? mpad : npad, 0, kpad, Kmax, n_mod, p.M, p.N, p.rdev, p.lower,
-              R, mpad, npad, &g.st->status, s, timer, &g.p);
+              R, mpad, npad, &g.st->status, s, timer, &g.p, 0, 0, 0, nullptr,
+              kdev ? &p.K : nullptr);
   if (e != cudaSuccess) return e;
   return crt_reconstruct(R, mpad, npad, p.M, p.N, p.rdev, EA, EB, g.betaA,
                          same ? g.betaA : g.betaB, p.alpha, p.beta, p.C, p.ldc, p.lower, n_mod, s,

@@ -83,9 +83,11 @@ int crt_block_m();  // rows of an output tile (128)
 cudaError_t crt_row_exponents(const double* X, int64_t ld, int tview, Dim rows, Dim K,
                               const int64_t* rdev, int64_t rows_max, int32_t* E, DevState* st,
                               cudaStream_t s, KernelTimer* timer);
+// trim_k: the planes are written only up to the last BK block inside K (a
+// product that reads them must then sum only those blocks: crt_mma's kdim).
 cudaError_t crt_split(const double* X, int64_t ld, int tview, Dim rows, Dim K, const int64_t* rdev,
                       int64_t rows_max, int64_t kpad, const int32_t* E, int n_mod, int beta,
-                      void* out, cudaStream_t s, KernelTimer* timer);
+                      void* out, cudaStream_t s, KernelTimer* timer, bool trim_k = false);
 // Largest moduli count of a block-diagonal reconstruction (crt_reconstruct
 // with blk > 0).
 constexpr int kRecBlockMaxMod = 22;
@@ -99,13 +101,14 @@ struct BlockPlace {
 // blk > 0: block-diagonal product (the Gram matrices of a batch stacked
 // along M = N): only the tiles inside the blk x blk diagonal blocks, R holds
 // [n_mod][Mpad][blk]; bn: output tile width (0 = by size; 128 or 256);
-// bplace: the tiles past a block's rows or columns (bplace->M, N) skipped.
+// bplace: the tiles past a block's rows or columns (bplace->M, N) skipped;
+// kdim: a device-side K (at most kuse): the BK blocks past it are not summed.
 cudaError_t crt_mma(const void* SA, int64_t a_rows, int a_row0, const void* SB, int64_t b_rows,
                     int b_row0, int64_t kpad, int64_t kuse, int n_mod, Dim M, Dim N,
                     const int64_t* rdev, int lower, uint8_t* R, int64_t Mpad, int64_t Npad,
                     int32_t* status, cudaStream_t s, KernelTimer* timer, const GemmParams* fl,
                     int max_ctas = 0, int blk = 0, int bn = 0,
-                    const BlockPlace* bplace = nullptr);
+                    const BlockPlace* bplace = nullptr, const Dim* kdim = nullptr);
 // blk > 0: the block-diagonal output of crt_mma (rows Mpad, Npad = blk),
 // written to C (row i, its block's column j) with EB per block; bplace: the
 // blocks placed and clipped as it says (default: block z at rows z blk of C,
@@ -128,7 +131,7 @@ cudaError_t crt_split_batched(const double* X, int64_t ld, int tview, Dim rows, 
                               const int64_t* rdev, int64_t rows_max, int64_t kpad,
                               const int32_t* E, int n_mod, int beta, void* out, int nz,
                               int64_t zX, int64_t zR, cudaStream_t s, KernelTimer* timer,
-                              int64_t zoff = 0);
+                              int64_t zoff = 0, bool trim_k = false);
 
 // chol_queue.cu: the factorisations of a batch in one persistent launch
 // fed by a device task queue (tasks on 32 x 32 tiles, listed in dependency
