@@ -276,6 +276,7 @@ struct Layout {
 
 constexpr int kGramBits = 62;  // integer width of G in the exact Gram (as the single problem)
 constexpr int kProdBits = 53;  // ... of L in L'L
+constexpr int kLevelBits = 62;  // ... of the triangular-inverse level products' operands
 constexpr int64_t kExactMaxM = 4096;  // one exact residue product: K <= 4096
 
 Layout make_layout(int P, const cpinv_problem* probs, bool exact) {
@@ -519,9 +520,85 @@ int bucket_factor(cudaStream_t s, const Bucket& bk, char* ws, int spd, int b) {
   return CPINV_OK;
 }
 
+// One product of a triangular-inverse level over every node of every problem
+// of the bucket in the exact-slice arithmetic (62-bit rows): node zi of
+// problem zo (lo = 2 sz zi, mid = lo + sz) forms C = alpha A B from the
+// node-0 blocks A0 (rows x K), B0 (K x cols), C0 of problem 0 (ld np; problem
+// zo's matrices zo np^2 further on, node zi's blocks 2 sz (np + 1) further
+// on, the node dims moving by -2 sz per node and read with the problem's
+// rank).  The residues of all (problem, node) blocks are stacked, so the
+// level is one split per operand, one block-diagonal tensor-core product
+// (blocks sz x sz) and one reconstruction writing each block in place.
+int exact_level_batched(cudaStream_t s, const Bucket& bk, char* ws, int64_t sz, int64_t live,
+                        const double* A0, Dim rows, Dim K, const double* B0, Dim cols,
+                        double* C0, double alpha) {
+  const int nz = (int)bk.ids.size();
+  const int64_t np = bk.np, zz = np * np, bkk = crt_block_k();
+  const int64_t kpad = round_up(sz, bkk), tot = (int64_t)nz * live * sz;
+  const int nm = crt_moduli_for(sz, kLevelBits, kLevelBits);
+  const int64_t zR = (int64_t)(sizeof(DevState) / sizeof(int64_t));
+  DevState* st = (DevState*)(ws + bk.off_st);
+  char* S = ws + bk.off_S;
+  void* SA = S;
+  void* SB = S + round_up(2 * (int64_t)nm * tot * kpad, 1024);
+  uint8_t* R = (uint8_t*)(ws + bk.off_R);
+  int32_t* EA = (int32_t*)(ws + bk.off_EG);
+  int32_t* EB = (int32_t*)(ws + bk.off_EL);
+  const ZNest zn{(int32_t)live, 2 * sz * np + 2 * sz, -2 * sz};
+  const int nzl = (int)(nz * live);
+  KernelTimer t;
+  BK_CHECK(cudaMemsetAsync(EA, 0, sizeof(int32_t) * (size_t)tot, s));
+  BK_CHECK(cudaMemsetAsync(EB, 0, sizeof(int32_t) * (size_t)tot, s));
+  BK_CHECK(crt_row_exponents_batched(A0, np, 0, rows, K, &st->rank, sz, EA, st, nzl, zz, zR, sz,
+                                     s, &t, &zn));
+  BK_CHECK(crt_row_exponents_batched(B0, np, 1, cols, K, &st->rank, sz, EB, st, nzl, zz, zR, sz,
+                                     s, &t, &zn));
+  BK_CHECK(crt_split_batched(A0, np, 0, rows, K, &st->rank, sz, kpad, EA, nm, kLevelBits, SA, nzl,
+                             zz, zR, s, &t, &zn));
+  BK_CHECK(crt_split_batched(B0, np, 1, cols, K, &st->rank, sz, kpad, EB, nm, kLevelBits, SB, nzl,
+                             zz, zR, s, &t, &zn));
+  BlockPlace place;
+  place.M = rows;
+  place.N = cols;
+  place.zoff = -2 * sz;
+  place.zC = 2 * sz * np + 2 * sz;
+  place.nzi = (int32_t)live;
+  place.zR = zR;
+  place.zCo = zz;
+  GemmParams fl;  // traced work: the blocks' sz x sz x sz products
+  std::memset(&fl, 0, sizeof(fl));
+  fl.M = fl.N = hdim(sz);
+  fl.K = hdim(tot);
+  BK_CHECK(crt_mma(SA, tot, 0, SB, tot, 0, kpad, sz, nm, hdim(tot), hdim(tot), &st->rank, 0, R,
+                   tot, sz, &st->status, s, &t, &fl, 0, (int)sz, bk.bn, &place));
+  BK_CHECK(crt_reconstruct(R, tot, sz, hdim(tot), hdim(sz), &st->rank, EA, EB, kLevelBits,
+                           kLevelBits, alpha, 0.0, C0, np, 0, nm, s, &t, (int)sz, &place));
+  return CPINV_OK;
+}
+
+// The exact level product fits the bucket's residue scratch and the
+// block-diagonal product's limits, and repays its split and reconstruction.
+bool exact_level_ok(const Bucket& bk, int64_t sz, int64_t live) {
+  if (!bk.exact || sz % 128 || live < 1) return false;
+  const int nm = crt_moduli_for(sz, kLevelBits, kLevelBits);
+  if (nm < 1 || nm > kRecBlockMaxMod) return false;
+  const int64_t nz = (int64_t)bk.ids.size(), tot = nz * live * sz;
+  if (nz * live > 65535) return false;
+  if (2.0 * (double)tot * (double)sz * (double)sz < (double)(1 << 27)) return false;
+  const int64_t kpad = round_up(sz, crt_block_k()), np = bk.np, rows = nz * np;
+  const int64_t plane = 2 * (int64_t)nm * tot * kpad;  // one operand's residues
+  const int64_t planes = round_up(plane, 1024) + plane;
+  const int64_t s_bytes = std::max(2 * (int64_t)bk.nmod_g * rows * bk.kpad_g,
+                                   2 * (int64_t)bk.nmod_l * rows * bk.kpad_l);
+  const int64_t r_bytes = (int64_t)std::max(bk.nmod_g, bk.nmod_l) * rows * np;
+  return planes <= s_bytes && (int64_t)nm * tot * sz <= r_bytes && tot <= rows;
+}
+
 // W = U^-1 from its inverted diagonal blocks (already in W), level by level
 // of the recursive halving: node [lo, lo + 2s) gets W21 = -W22 (U21 W11).
-// One launch per product and level covers all nodes of all problems.
+// One launch per product and level covers all nodes of all problems (FP64),
+// or one block-diagonal residue product per product and level (exact mode,
+// large levels).
 int bucket_tri_inverse(cudaStream_t s, const Bucket& bk, char* ws, int b) {
   const int nz = (int)bk.ids.size();
   const int64_t np = bk.np, zz = np * np;
@@ -552,6 +629,17 @@ int bucket_tri_inverse(cudaStream_t s, const Bucket& bk, char* ws, int b) {
       return g.run(s, alpha, 0.0, 0);
     };
     const Dim rows = rdim(-sz, sz), cols = rdim(0, sz);  // node 0: lo = 0, mid = sz
+    // nodes whose rows start inside the padded order (the others are empty)
+    const int64_t live = np > sz ? std::min(nodes, (np - sz + 2 * sz - 1) / (2 * sz)) : 0;
+    if (exact_level_ok(bk, sz, live)) {
+      if (int rc = exact_level_batched(s, bk, ws, sz, live, U + sz * np, rows, cols, W, cols,
+                                       Tmp + sz * np, 1.0))
+        return rc;
+      if (int rc = exact_level_batched(s, bk, ws, sz, live, W + sz * np + sz, rows, rows,
+                                       Tmp + sz * np, cols, W + sz * np, -1.0))
+        return rc;
+      continue;
+    }
     BK_CHECK(level(U + sz * np, W, Tmp + sz * np, rows, cols, cols, 1.0));
     BK_CHECK(level(W + sz * np + sz, Tmp + sz * np, W + sz * np, rows, cols, rows, -1.0));
   }

@@ -687,8 +687,13 @@ int front_rank(const Ctx& c, const double* G, int64_t ldg, bool compact) {
   return rank_from_gram(c, compact);
 }
 
+// Integer width of the triangular-inverse level products' operands: wider than
+// the 53 bits of an FP64 significand, so that the small entries of a row of an
+// ill-conditioned inverse keep as many bits as an FP64 product gives them.
+constexpr int kLevelBits = 62;
+
 // One product of a triangular-inverse level for all its nodes at once, in the
-// exact-slice arithmetic (53-bit rows): node z (lo = 2 s z, mid = lo + s) forms
+// exact-slice arithmetic (62-bit rows): node z (lo = 2 s z, mid = lo + s) forms
 //   C_z = alpha A_z B_z,   A_z: rows mid.. x K, B_z: K x columns lo..,
 // from the node-0 blocks A0, B0, C0 (ld nA; node z's blocks 2 s (nA + 1)
 // further on), with the node-0 dims rows (of A and C), K and cols (of B and
@@ -701,7 +706,7 @@ int front_rank(const Ctx& c, const double* G, int64_t ldg, bool compact) {
 bool level_product_fits(const Plan& p, int64_t s, int64_t nodes) {
   const int64_t bk = crt_block_k(), bm = crt_block_m();
   if (s % bm || s > kCrtMaxK || nodes < 1 || nodes > 65535) return false;
-  const int nm = crt_moduli_for(s, 53, 53);
+  const int nm = crt_moduli_for(s, kLevelBits, kLevelBits);
   if (nm < 1 || nm > kRecBlockMaxMod) return false;
   const int64_t kpad = (s + bk - 1) / bk * bk, tot = nodes * s;
   const size_t need = 2 * (2 * (size_t)nm * tot * kpad + 1024) + (size_t)nm * tot * s + 1024 +
@@ -713,7 +718,7 @@ cudaError_t level_product(const Ctx& c, int64_t s, int64_t nodes, const double* 
                           Dim K, const double* B0, Dim cols, double* C0, double alpha) {
   const Plan& p = *c.p;
   const int64_t nA = p.nA, bk = crt_block_k();
-  const int nm = crt_moduli_for(s, 53, 53);
+  const int nm = crt_moduli_for(s, kLevelBits, kLevelBits);
   const int64_t kpad = (s + bk - 1) / bk * bk, tot = nodes * s;
   const int64_t zX = 2 * s * nA + 2 * s, zoff = -2 * s;
   char* w = (char*)p.crt;
@@ -734,23 +739,25 @@ cudaError_t level_product(const Ctx& c, int64_t s, int64_t nodes, const double* 
   cudaError_t e = cudaMemsetAsync(EA, 0, (size_t)((char*)(EB + tot) - (char*)EA), c.s);
   if (e != cudaSuccess) return e;
   // A_z row-wise; B_z through its transpose (rows = the output's columns)
-  e = crt_row_exponents_batched(A0, nA, 0, rows, K, rdev, s, EA, p.st, (int)nodes, zX, 0, s, c.s,
-                                &t, zoff);
+  const ZNest zn{(int32_t)nodes, zX, zoff};
+  e = crt_row_exponents_batched(A0, nA, 0, rows, K, rdev, s, EA, p.st, (int)nodes, 0, 0, s, c.s,
+                                &t, &zn);
   if (e == cudaSuccess)
-    e = crt_row_exponents_batched(B0, nA, 1, cols, K, rdev, s, EB, p.st, (int)nodes, zX, 0, s,
-                                  c.s, &t, zoff);
+    e = crt_row_exponents_batched(B0, nA, 1, cols, K, rdev, s, EB, p.st, (int)nodes, 0, 0, s,
+                                  c.s, &t, &zn);
   if (e == cudaSuccess)
-    e = crt_split_batched(A0, nA, 0, rows, K, rdev, s, kpad, EA, nm, 53, SA, (int)nodes, zX, 0,
-                          c.s, &t, zoff);
+    e = crt_split_batched(A0, nA, 0, rows, K, rdev, s, kpad, EA, nm, kLevelBits, SA, (int)nodes,
+                          0, 0, c.s, &t, &zn);
   if (e == cudaSuccess)
-    e = crt_split_batched(B0, nA, 1, cols, K, rdev, s, kpad, EB, nm, 53, SB, (int)nodes, zX, 0,
-                          c.s, &t, zoff);
+    e = crt_split_batched(B0, nA, 1, cols, K, rdev, s, kpad, EB, nm, kLevelBits, SB, (int)nodes,
+                          0, 0, c.s, &t, &zn);
   if (e != cudaSuccess) return e;
   BlockPlace place;
   place.M = rows;
   place.N = cols;
   place.zoff = zoff;
   place.zC = zX;
+  place.nzi = (int32_t)nodes;
   GemmParams fl;  // traced work: the nodes' s x s x s products
   std::memset(&fl, 0, sizeof(fl));
   fl.M = fl.N = hdim(s);
@@ -758,8 +765,8 @@ cudaError_t level_product(const Ctx& c, int64_t s, int64_t nodes, const double* 
   e = crt_mma(SA, tot, 0, SB, tot, 0, kpad, s, nm, hdim(tot), hdim(tot), rdev, 0, R, tot, s,
               &p.st->status, c.s, &t, &fl, 0, (int)s, 0, &place);
   if (e != cudaSuccess) return e;
-  return crt_reconstruct(R, tot, s, hdim(tot), hdim(s), rdev, EA, EB, 53, 53, alpha, 0.0, C0, nA,
-                         0, nm, c.s, &t, (int)s, &place);
+  return crt_reconstruct(R, tot, s, hdim(tot), hdim(s), rdev, EA, EB, kLevelBits, kLevelBits,
+                         alpha, 0.0, C0, nA, 0, nm, c.s, &t, (int)s, &place);
 }
 
 // W = U^-1 for the lower-triangular U (order r <= nA, ld nA), given the

@@ -33,6 +33,14 @@ __device__ __forceinline__ int64_t eval_dim(const Dim& d, const int64_t* rdev) {
   return v > d.max ? d.max : v;
 }
 
+// Inner index of a nested batch z = zo nzi + zi (zo: a problem, zi: a block
+// inside it): the inner blocks' operand stride and the offset added per inner
+// block to their dims.
+struct ZNest {
+  int32_t nzi;
+  int64_t zXi, zoff;
+};
+
 // Status bits recorded by kernels (OR-ed into DevState::status).
 enum : int32_t { ST_NONFINITE = 1, ST_NUMERICAL = 2, ST_TIMEOUT = 4 };
 

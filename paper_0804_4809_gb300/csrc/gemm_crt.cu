@@ -143,19 +143,21 @@ __device__ __forceinline__ bool nonfinite_bits(uint64_t b) { return ((b >> 52) &
 // trans = 0: row i is contiguous (X[i*ld + k]); one warp per row.
 // trans = 1: row i of op(X) is column i of X; a 32-row x 8-chunk block,
 //            coalesced over i, each thread scanning a slice of k.
-// Batches (grid z): operand z at X + z zX, its dims read at rdev + z zR with
-// z zoff added to both offsets, its state st + z zSt, its exponents E + z zE.
+// Batches (grid z = zo zn.nzi + zi): operand z at X + zo zX + zi zn.zXi, its
+// dims read at rdev + zo zR with zi zn.zoff added to both offsets, its state
+// st + zo zSt, its exponents E + z zE.
 __global__ void row_expo_kernel(const double* X, int64_t ld, int trans, Dim rowsd, Dim colsd,
                                 const int64_t* rdev, int32_t* E, DevState* st, int64_t zX,
-                                int64_t zR, int64_t zE, int64_t zSt, int64_t zoff) {
+                                int64_t zR, int64_t zE, int64_t zSt, ZNest zn) {
   {
     const int64_t z = blockIdx.z;
-    X += z * zX;
-    rdev += z * zR;
+    const int64_t zo = z / zn.nzi, zi = z - zo * zn.nzi;
+    X += zo * zX + zi * zn.zXi;
+    rdev += zo * zR;
     E += z * zE;
-    st += z * zSt;
-    rowsd.off += z * zoff;
-    colsd.off += z * zoff;
+    st += zo * zSt;
+    rowsd.off += zi * zn.zoff;
+    colsd.off += zi * zn.zoff;
   }
   const int64_t rows = eval_dim(rowsd, rdev), cols = eval_dim(colsd, rdev);
   int emax = 0, bad = 0;
@@ -231,26 +233,27 @@ __device__ __forceinline__ void split_store8_all(std::integer_sequence<int, Js..
   (split_store8<Js>(c, sg, n_mod, dst, plane_vec), ...);
 }
 
-// Batches (grid z): operand z at X + z zX, dims at rdev + z zR with z zoff
-// added to both offsets, its rows z zrow onwards in the planes (and in E);
-// plane_rows = rows of one plane.
+// Batches (grid z = zo zn.nzi + zi): operand z at X + zo zX + zi zn.zXi, dims
+// at rdev + zo zR with zi zn.zoff added to both offsets, its rows z zrow
+// onwards in the planes (and in E); plane_rows = rows of one plane.
 __global__ void __launch_bounds__(256) split_kernel(const double* X, int64_t ld, int trans,
                                                     Dim rowsd, Dim colsd, int64_t rows_max,
                                                     int64_t kpad, const int64_t* rdev,
                                                     const int32_t* E, int n_mod, int beta,
                                                     bf16* out, int64_t zX, int64_t zR,
                                                     int64_t zrow, int64_t plane_rows,
-                                                    int64_t zoff, int trim) {
+                                                    ZNest zn, int trim) {
   // rows padded to 66 words: 16-byte aligned, four banks apart
   __shared__ __align__(16) uint64_t tile[32][66];
   {
     const int64_t z = blockIdx.z;
-    X += z * zX;
-    rdev += z * zR;
+    const int64_t zo = z / zn.nzi, zi = z - zo * zn.nzi;
+    X += zo * zX + zi * zn.zXi;
+    rdev += zo * zR;
     E += z * zrow;
     out += z * zrow * kpad;
-    rowsd.off += z * zoff;
-    colsd.off += z * zoff;
+    rowsd.off += zi * zn.zoff;
+    colsd.off += zi * zn.zoff;
   }
   const int64_t rows = eval_dim(rowsd, rdev), cols = eval_dim(colsd, rdev);
   const int64_t i0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 64;
@@ -466,8 +469,9 @@ struct MmaParams {
                             // matrices); tiles and lower refer to one block, R holds
                             // [n_mod][Mpad][blk] (the block's own columns)
   int32_t tiles_blk;        // tiles per block
-  int32_t bdims;            // block mode: block z has rows < bM and columns < bN (z bzoff
-  int64_t bzoff;            // added to both offsets); the tiles past them are skipped
+  int32_t bdims;            // block mode: block z = zo bnzi + zi has rows < bM and columns
+  int32_t bnzi;             // < bN (zi bzoff added to both offsets, read at rdev + zo bzR);
+  int64_t bzoff, bzR;       // the tiles past them are skipped
   Dim bM, bN;
   uint8_t* R;               // residues [n_mod][Mpad][Npad]
   int64_t Mpad, Npad;
@@ -557,11 +561,12 @@ __global__ void __launch_bounds__(192, 1)
       t -= zb * p.tiles_blk;
       base = (int64_t)zb * p.blk;
       if (p.bdims) {
+        const int zo = zb / p.bnzi, zi = zb - zo * p.bnzi;
         Dim dm = p.bM, dn = p.bN;
-        dm.off += zb * p.bzoff;
-        dn.off += zb * p.bzoff;
-        bmv = eval_dim(dm, p.rdev);
-        bnv = eval_dim(dn, p.rdev);
+        dm.off += zi * p.bzoff;
+        dn.off += zi * p.bzoff;
+        bmv = eval_dim(dm, p.rdev + zo * p.bzR);
+        bnv = eval_dim(dn, p.rdev + zo * p.bzR);
       }
     }
     int ty, tx;
@@ -794,9 +799,11 @@ struct ReconParams {
                 // belongs to block z = i / blk, its columns j are the block's own
                 // (EB[z blk + j]), lower is within the block; the row goes to
                 // C + z zC + (i - z blk) ldc
-  int32_t bdims;  // block mode: block z keeps its rows il < bM and columns j < bN,
-                  // both with z zoff added to their offsets
-  int64_t zC, zoff;
+  int32_t bdims;  // block mode, z = zo bnzi + zi: block z keeps its rows il < bM and
+                  // columns j < bN (zi zoff added to their offsets, read at rdev +
+                  // zo bzR) and goes to C + zo zCo + zi zC + il ldc
+  int32_t bnzi;
+  int64_t zC, zCo, zoff, bzR;
   Dim bM, bN;
 };
 
@@ -1009,15 +1016,18 @@ __global__ void __launch_bounds__(256) reconstruct_words_kernel(ReconParams p, i
   const int32_t* EB = p.blk ? p.EB + (i - il) : p.EB;
   int64_t Nv = N;
   bool row_ok = i < M;
+  int64_t coff = zb * p.zC;
   if (p.bdims) {
+    const int64_t zo = zb / p.bnzi, zi = zb - zo * p.bnzi;
     Dim bm = p.bM, bn = p.bN;
-    bm.off += zb * p.zoff;
-    bn.off += zb * p.zoff;
-    row_ok = row_ok && il < eval_dim(bm, p.rdev);
-    Nv = eval_dim(bn, p.rdev);
+    bm.off += zi * p.zoff;
+    bn.off += zi * p.zoff;
+    row_ok = row_ok && il < eval_dim(bm, p.rdev + zo * p.bzR);
+    Nv = eval_dim(bn, p.rdev + zo * p.bzR);
+    coff = zo * p.zCo + zi * p.zC;
   }
   if (!row_ok || j0 >= Nv || (p.lower && j0 > il)) return;
-  double* crow = p.C + (p.blk ? zb * p.zC + il * p.ldc : i * p.ldc);
+  double* crow = p.C + (p.blk ? coff + il * p.ldc : i * p.ldc);
   const size_t plane = (size_t)p.Mpad * (size_t)p.Npad;
   const uint32_t* r = reinterpret_cast<const uint32_t*>(p.R + i * p.Npad + j0);
   uint64_t acc[4][NL];
@@ -1288,18 +1298,20 @@ cudaError_t crt_row_exponents(const double* X, int64_t ld, int tview, Dim rows, 
 cudaError_t crt_row_exponents_batched(const double* X, int64_t ld, int tview, Dim rows, Dim K,
                                       const int64_t* rdev, int64_t rows_max, int32_t* E,
                                       DevState* st, int nz, int64_t zX, int64_t zR, int64_t zE,
-                                      cudaStream_t s, KernelTimer* timer, int64_t zoff) {
+                                      cudaStream_t s, KernelTimer* timer, const ZNest* znp) {
   if (nz < 1 || nz > 65535) return cudaErrorInvalidValue;
   // operands of separate problems have their own states; the nodes of one
   // matrix (zR = 0) share its state
   const int64_t zSt = (nz > 1 && zR != 0) ? 1 : 0;
+  const ZNest zn = znp ? *znp : ZNest{1, 0, 0};
+  if (zn.nzi < 1) return cudaErrorInvalidValue;
   return timer->run(KT_SPLIT, s, [&] {
     if (!tview)
       row_expo_kernel<<<dim3((unsigned)((rows_max * 32 + 255) / 256), 1, (unsigned)nz), 256, 0,
-                        s>>>(X, ld, 0, rows, K, rdev, E, st, zX, zR, zE, zSt, zoff);
+                        s>>>(X, ld, 0, rows, K, rdev, E, st, zX, zR, zE, zSt, zn);
     else
       row_expo_kernel<<<dim3((unsigned)((rows_max + 31) / 32), 16, (unsigned)nz), 256, 0, s>>>(
-          X, ld, 1, rows, K, rdev, E, st, zX, zR, zE, zSt, zoff);
+          X, ld, 1, rows, K, rdev, E, st, zX, zR, zE, zSt, zn);
     return cudaGetLastError();
   });
 }
@@ -1308,20 +1320,22 @@ cudaError_t crt_split(const double* X, int64_t ld, int tview, Dim rows, Dim K, c
                       int64_t rows_max, int64_t kpad, const int32_t* E, int n_mod, int beta,
                       void* out, cudaStream_t s, KernelTimer* timer, bool trim_k) {
   return crt_split_batched(X, ld, tview, rows, K, rdev, rows_max, kpad, E, n_mod, beta, out, 1, 0,
-                           0, s, timer, 0, trim_k);
+                           0, s, timer, nullptr, trim_k);
 }
 
 cudaError_t crt_split_batched(const double* X, int64_t ld, int tview, Dim rows, Dim K,
                               const int64_t* rdev, int64_t rows_max, int64_t kpad,
                               const int32_t* E, int n_mod, int beta, void* out, int nz,
                               int64_t zX, int64_t zR, cudaStream_t s, KernelTimer* timer,
-                              int64_t zoff, bool trim_k) {
+                              const ZNest* znp, bool trim_k) {
   if (nz < 1 || nz > 65535 || rows_max % 32) return cudaErrorInvalidValue;
+  const ZNest zn = znp ? *znp : ZNest{1, 0, 0};
+  if (zn.nzi < 1) return cudaErrorInvalidValue;
   dim3 grid((unsigned)(kpad / 64), (unsigned)((rows_max + 31) / 32), (unsigned)nz);
   const int64_t zrow = nz > 1 ? rows_max : 0;
   return timer->run(KT_SPLIT, s, [&] {
     split_kernel<<<grid, 256, 0, s>>>(X, ld, tview, rows, K, rows_max, kpad, rdev, E, n_mod, beta,
-                                      (bf16*)out, zX, zR, zrow, rows_max * nz, zoff,
+                                      (bf16*)out, zX, zR, zrow, rows_max * nz, zn,
                                       trim_k ? 1 : 0);
     return cudaGetLastError();
   });
@@ -1358,7 +1372,10 @@ cudaError_t crt_mma(const void* SA, int64_t a_rows, int a_row0, const void* SB, 
   mp.lower = lower;
   mp.blk = blk;
   if (blk && bplace) {
+    if (bplace->nzi < 1) return cudaErrorInvalidValue;
     mp.bdims = 1;
+    mp.bnzi = bplace->nzi;
+    mp.bzR = bplace->zR;
     mp.bzoff = bplace->zoff;
     mp.bM = bplace->M;
     mp.bN = bplace->N;
@@ -1426,11 +1443,18 @@ cudaError_t crt_reconstruct(const uint8_t* R, int64_t Mpad, int64_t Npad, Dim M,
   rp.lower = lower;
   rp.blk = blk;
   rp.bdims = 0;
+  rp.bnzi = 1;
   rp.zC = (int64_t)blk * ldc;
+  rp.zCo = 0;
   rp.zoff = 0;
+  rp.bzR = 0;
   rp.bM = rp.bN = hdim(0);
   if (blk && bplace) {
+    if (bplace->nzi < 1) return cudaErrorInvalidValue;
     rp.bdims = 1;
+    rp.bnzi = bplace->nzi;
+    rp.bzR = bplace->zR;
+    rp.zCo = bplace->zCo;
     rp.zC = bplace->zC;
     rp.zoff = bplace->zoff;
     rp.bM = bplace->M;

@@ -91,12 +91,15 @@ cudaError_t crt_split(const double* X, int64_t ld, int tview, Dim rows, Dim K, c
 // Largest moduli count of a block-diagonal reconstruction (crt_reconstruct
 // with blk > 0).
 constexpr int kRecBlockMaxMod = 22;
-// Placement of the blocks of a block-diagonal output: block z keeps its rows
-// i < M and columns j < N (each with z zoff added to its offset) and writes
-// them to C + z zC + i ldc + j.
+// Placement of the blocks of a block-diagonal output, block z = zo nzi + zi
+// (zo: the problem, zi: a block inside it): block z keeps its rows i < M and
+// columns j < N (each with zi zoff added to its offset, the rank read at
+// rdev + zo zR) and writes them to C + zo zCo + zi zC + i ldc + j.
 struct BlockPlace {
   Dim M, N;
   int64_t zoff, zC;
+  int32_t nzi = 1;
+  int64_t zR = 0, zCo = 0;
 };
 // blk > 0: block-diagonal product (the Gram matrices of a batch stacked
 // along M = N): only the tiles inside the blk x blk diagonal blocks, R holds
@@ -118,20 +121,22 @@ cudaError_t crt_reconstruct(const uint8_t* R, int64_t Mpad, int64_t Npad, Dim M,
                             int betaB, double alpha, double beta, double* C, int64_t ldc,
                             int lower, int n_mod, cudaStream_t s, KernelTimer* timer,
                             int blk = 0, const BlockPlace* bplace = nullptr);
-// Batches of nz operands (z-major): operand z at X + z zX with its dims
-// read at rdev + z zR and z zoff added to their offsets; its exponents and
-// residue rows follow one another (rows z rows_max .. in E and in the planes,
-// plane rows = nz rows_max).  zR = 0: the operands are blocks of one matrix
-// and share its state.
+// Batches of nz operands (z-major), z = zo nzi + zi (zn; default nzi = 1):
+// operand z at X + zo zX + zi zXi with its dims read at rdev + zo zR and
+// zi zoff added to their offsets; its exponents and residue rows follow one
+// another (rows z rows_max .. in E and in the planes, plane rows =
+// nz rows_max).  zR = 0: the operands are blocks of one matrix and share its
+// state.
 cudaError_t crt_row_exponents_batched(const double* X, int64_t ld, int tview, Dim rows, Dim K,
                                       const int64_t* rdev, int64_t rows_max, int32_t* E,
                                       DevState* st, int nz, int64_t zX, int64_t zR, int64_t zE,
-                                      cudaStream_t s, KernelTimer* timer, int64_t zoff = 0);
+                                      cudaStream_t s, KernelTimer* timer,
+                                      const ZNest* zn = nullptr);
 cudaError_t crt_split_batched(const double* X, int64_t ld, int tview, Dim rows, Dim K,
                               const int64_t* rdev, int64_t rows_max, int64_t kpad,
                               const int32_t* E, int n_mod, int beta, void* out, int nz,
                               int64_t zX, int64_t zR, cudaStream_t s, KernelTimer* timer,
-                              int64_t zoff = 0, bool trim_k = false);
+                              const ZNest* zn = nullptr, bool trim_k = false);
 
 // chol_queue.cu: the factorisations of a batch in one persistent launch
 // fed by a device task queue (tasks on 32 x 32 tiles, listed in dependency
