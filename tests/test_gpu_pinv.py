@@ -209,3 +209,21 @@ def test_split_mode_reduced_accuracy_tier(cp):
     W, rk = cp.lstsq(to_dev(G), to_dev(F), mode="bf16x3")
     torch.cuda.synchronize()
     assert rk == 150 and rel(W.cpu().numpy(), oracle.lstsq(G, F)) < 1e-3
+
+
+# Orders and ranks around the triangular inverse's levels: in the exact mode
+# the levels of order 512 and 1024 here are block-diagonal residue products
+# whose node rows are clipped by the rank on the device -- a node with six
+# rows (r = 1030 of 1100), a node with none (r = 1000), ragged last nodes
+# (r = 1200 and r = 650).
+LEVEL_SHAPES = [(1400, 1100, 1030), (1400, 1100, 1000), (1300, 1200, 1200), (900, 700, 650)]
+
+
+@pytest.mark.parametrize("shape", LEVEL_SHAPES)
+def test_triangular_inverse_levels_exact(cp, shape):
+    m, n, r = shape
+    G = inputs.rank_deficient(m, n, r, seed=m + 3 * n + r)
+    Yo, fac = oracle.geninv(G, return_factors=True)
+    Y, rk = _pinv(cp, G, "exact")
+    assert rk == fac["rank"] == r
+    assert rel(Y, Yo) <= tol_for("exact", G, r)
