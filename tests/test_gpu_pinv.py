@@ -215,7 +215,12 @@ def test_split_mode_reduced_accuracy_tier(cp):
 # the levels of order 512 and 1024 here are block-diagonal residue products
 # whose node rows are clipped by the rank on the device -- a node with six
 # rows (r = 1030 of 1100), a node with none (r = 1000), ragged last nodes
-# (r = 1200 and r = 650).
+# (r = 1200 and r = 650).  The kept columns of these inputs are much worse
+# conditioned than G itself (kappa(G_S) up to 7e4 against kappa(G) ~ 100),
+# and the method amplifies the Gram's rounding through them (Sec. 2): the
+# bar is widened to 8x the oracle's own change between a correctly rounded
+# and an FP64 Gram, as for the paper family.  A clipping mistake would move
+# G+ by O(1).
 LEVEL_SHAPES = [(1400, 1100, 1030), (1400, 1100, 1000), (1300, 1200, 1200), (900, 700, 650)]
 
 
@@ -224,6 +229,7 @@ def test_triangular_inverse_levels_exact(cp, shape):
     m, n, r = shape
     G = inputs.rank_deficient(m, n, r, seed=m + 3 * n + r)
     Yo, fac = oracle.geninv(G, return_factors=True)
+    sens = rel(oracle.geninv(G, exact_gram=False), Yo)
     Y, rk = _pinv(cp, G, "exact")
     assert rk == fac["rank"] == r
-    assert rel(Y, Yo) <= tol_for("exact", G, r)
+    assert rel(Y, Yo) <= max(tol_for("exact", G, r), 8.0 * sens), (rel(Y, Yo), sens)
