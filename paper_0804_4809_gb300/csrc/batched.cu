@@ -30,6 +30,7 @@
 
 #include "../../include/cpinv.h"
 #include "common.cuh"
+#include "crt_device.cuh"
 #include "kernels.h"
 
 namespace cpinv {
@@ -233,9 +234,12 @@ struct Bucket {
   int nmod_g, nmod_l;      // moduli of the Gram (62-bit G) and of L'L (53-bit L)
   int64_t kpad_g, kpad_l;  // K of those products, padded to the planes' block
   size_t off_EG, off_EL, off_S, off_R;
-  // the factorisations as one persistent launch fed by a device task queue
-  // (chol_queue.cu), chosen by the tuner against one launch per panel step
-  bool queue;
+  // the factorisations' form, chosen by the tuner: 0 one launch per panel
+  // step (FP64 right-looking updates), 1 one persistent launch fed by a
+  // device task queue (chol_queue.cu), 2 (exact mode) left-looking with each
+  // panel's update an exact residue product rounded once
+  int queue;
+  int nmod_c;  // form 2: moduli of the factor's residue planes (60-bit L)
   int32_t nb_q, ntasks;
   size_t off_tasks, off_qflags, off_qhead, off_qdinv;
 };
@@ -277,6 +281,7 @@ struct Layout {
 constexpr int kGramBits = 62;  // integer width of G in the exact Gram (as the single problem)
 constexpr int kProdBits = 53;  // ... of L in L'L
 constexpr int kLevelBits = 62;  // ... of the triangular-inverse level products' operands
+constexpr int kCholBits = 60;   // ... of L in the left-looking exact factorisation's planes
 constexpr int64_t kExactMaxM = 4096;  // one exact residue product: K <= 4096
 
 Layout make_layout(int P, const cpinv_problem* probs, bool exact) {
@@ -301,7 +306,7 @@ Layout make_layout(int P, const cpinv_problem* probs, bool exact) {
     Bucket& b = L.buckets[it->second];
     b.exact = exact;
     b.bn = 128;
-    b.queue = false;
+    b.queue = 0;
     b.ids.push_back(i);
     b.mp = std::max<int64_t>(b.mp, probs[i].m);
     b.kp = std::max<int64_t>(b.kp, probs[i].k);
@@ -346,13 +351,15 @@ Layout make_layout(int P, const cpinv_problem* probs, bool exact) {
       b.kpad_l = round_up(b.np, bk);
       b.nmod_g = crt_moduli_for(b.mp, kGramBits, kGramBits);
       b.nmod_l = crt_moduli_for(b.np, kProdBits, kProdBits);
+      b.nmod_c = crt_moduli_for(b.np, kCholBits, kCholBits);
       const size_t rows = nz * np;
       const size_t sg = 2 * (size_t)b.nmod_g * rows * (size_t)b.kpad_g;
       const size_t sl = 2 * (size_t)b.nmod_l * rows * (size_t)b.kpad_l;
-      const int nmax = b.nmod_g > b.nmod_l ? b.nmod_g : b.nmod_l;
+      const size_t sc = 2 * (size_t)b.nmod_c * rows * (size_t)b.kpad_l;  // factor planes
+      const int nmax = std::max(b.nmod_g, std::max(b.nmod_l, b.nmod_c));
       b.off_EG = take(4 * rows);
       b.off_EL = take(4 * rows);
-      b.off_S = take(sg > sl ? sg : sl);
+      b.off_S = take(std::max(sg, std::max(sl, sc)));
       b.off_R = take((size_t)nmax * rows * np);
     }
   }
@@ -460,8 +467,11 @@ int bucket_factor_queue(cudaStream_t s, const Bucket& bk, char* ws, int spd) {
   return CPINV_OK;
 }
 
+int bucket_factor_exact(cudaStream_t s, const Bucket& bk, char* ws, int spd);
+
 int bucket_factor(cudaStream_t s, const Bucket& bk, char* ws, int spd, int b) {
-  if (bk.queue) return bucket_factor_queue(s, bk, ws, spd);
+  if (bk.queue == 1) return bucket_factor_queue(s, bk, ws, spd);
+  if (bk.queue == 2) return bucket_factor_exact(s, bk, ws, spd);
   const int nz = (int)bk.ids.size();
   const int64_t np = bk.np, nb = (np + b - 1) / b;
   double* A = (double*)(ws + bk.off_A);
@@ -516,6 +526,153 @@ int bucket_factor(cudaStream_t s, const Bucket& bk, char* ws, int spd, int b) {
       return launch_tri_block_inverse_batched(A, np, zz, np, &st->rank,
                                               (int64_t)(sizeof(DevState) / sizeof(int64_t)), b, T,
                                               nb * b * b, nz, s);
+    }));
+  return CPINV_OK;
+}
+
+// E_z[i] = biased exponent of sqrt(A_z(i, i)), plus one (0 for a
+// non-positive or non-finite entry): the row scales of the factor's residue
+// planes, |L_z(i, j)| < 2^(E_z[i] - 1022).  Grid: x over rows, y problems.
+__global__ void rowscale_batched_kernel(const double* A, int64_t np, Dim nd, const DevState* st,
+                                        int32_t* E) {
+  const int64_t z = blockIdx.y;
+  const int64_t n = eval_dim(nd, &st[z].rank);
+  const double* a = A + z * np * np;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int e = 0;
+    if (i < n) {
+      const double d = a[i * np + i];
+      if (d > 0.0 && isfinite(d)) {
+        const uint64_t bits = (uint64_t)__double_as_longlong(sqrt(d));
+        e = (int)((bits >> 52) & 0x7FF) + 1;
+      }
+    }
+    E[z * np + i] = e;
+  }
+}
+
+// Residues of the finished panel k0 (columns k0 .. k0 + 31 of L, rows k0 ..
+// n_z of each problem; the diagonal block's lower triangle only) into the
+// factor's planes RL[j][z np + i][k0 + c] (row pitch kpad, plane pitch
+// `plane` elements).  Grid: x over the panel's entries, y problems.
+__global__ void rl_panel_split_kernel(const double* A, int64_t np, Dim nd, const DevState* st,
+                                      int64_t k0, const int32_t* E, int n_mod, int beta,
+                                      __nv_bfloat16* RL, int64_t kpad, size_t plane) {
+  const int64_t z = blockIdx.y;
+  const int64_t n = eval_dim(nd, &st[z].rank);
+  const double* a = A + z * np * np;
+  const int64_t total = (np - k0) * 32;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t il = e >> 5, c = e & 31, i = k0 + il, col = k0 + c;
+    if (i >= n || col >= n) continue;
+    const double v = (il >= 32 || c <= il) ? a[i * np + col] : 0.0;
+    const uint64_t bits = (uint64_t)__double_as_longlong(v);
+    const uint64_t q = crt::integerize(bits, E[z * np + i], beta);
+    crt::store_residues(q, (bits >> 63) != 0, n_mod, RL + (size_t)(z * np + i) * kpad + col, plane);
+  }
+}
+
+// The factorisations of a bucket, left-looking in the exact-slice arithmetic
+// (the single problem's rounding: every entry of L from its exactly summed
+// update, rounded once): per panel k0 of 32 columns, one block-diagonal
+// residue product over the problems forms L(k0.., 0..k0) L(k0..k0+31, 0..k0)'
+// from the factor's persistent residue planes, one reconstruction subtracts
+// it from the panel (the exact sum rounded once, then the difference), then
+// the diagonal blocks are factored (one CTA per problem, the pivot test as
+// everywhere), the rows below solved against them, and the finished panel is
+// cut into residues once.
+int bucket_factor_exact(cudaStream_t s, const Bucket& bk, char* ws, int spd) {
+  const int nz = (int)bk.ids.size();
+  const int64_t np = bk.np, zz = np * np, rows = (int64_t)nz * np, kpad = bk.kpad_l;
+  constexpr int b = 32;
+  const int nm = bk.nmod_c;
+  if (nm < 1 || nm > kRecBlockMaxMod || np % 128) return CPINV_ERR_UNSUPPORTED;
+  double* A = (double*)(ws + bk.off_A);
+  DevState* st = (DevState*)(ws + bk.off_st);
+  double* dinv = (double*)(ws + bk.off_Z);
+  uint8_t* acc = (uint8_t*)(ws + bk.off_acc);
+  int32_t* E = (int32_t*)(ws + bk.off_EG);
+  __nv_bfloat16* RL = (__nv_bfloat16*)(ws + bk.off_S);
+  uint8_t* R = (uint8_t*)(ws + bk.off_R);
+  const size_t plane = (size_t)rows * (size_t)kpad;
+  const int32_t sel = spd ? SEL_RANK : SEL_N;
+  const Dim nd{0, np, sel, 0};
+  const int64_t zR = (int64_t)(sizeof(DevState) / sizeof(int64_t));
+  KernelTimer t;
+  BK_CHECK(t.run(KT_AUX, s, [&] {
+    rowscale_batched_kernel<<<dim3(g1(np, 256, 4), (unsigned)nz), 256, 0, s>>>(A, np, nd, st, E);
+    return cudaGetLastError();
+  }));
+  BK_CHECK(cudaMemsetAsync(RL, 0, sizeof(__nv_bfloat16) * (size_t)nm * plane, s));
+  for (int64_t k0 = 0; k0 < np; k0 += b) {
+    if (k0 > 0) {
+      // panel k0's update: block z holds rows k0 .. n_z of problem z against
+      // the panel's own rows, columns 0 .. k0 (tiles past the panel's 32
+      // columns or past the problem's rows skipped)
+      BlockPlace place;
+      place.M = Dim{-k0, np - k0, sel, 0};
+      place.N = Dim{-k0, b, sel, 0};
+      place.zoff = 0;
+      place.zC = 0;
+      place.nzi = 1;
+      place.zR = zR;
+      place.zCo = zz;
+      GemmParams fl;  // traced work: each problem's (n - k0) x 32 x k0 product
+      std::memset(&fl, 0, sizeof(fl));
+      fl.M = hdim(np - k0);
+      fl.N = hdim(b);
+      fl.K = hdim(k0 * nz);
+      BK_CHECK(crt_mma(RL, rows, (int)k0, RL, rows, (int)k0, kpad, k0, nm, hdim(rows), hdim(rows),
+                       &st->rank, 0, R, rows, np, &st->status, s, &t, &fl, 0, (int)np, 128,
+                       &place));
+      // A(k0.., k0..k0+31) -= the exact sum, rounded once (lower triangle of
+      // the diagonal block)
+      BK_CHECK(crt_reconstruct(R, rows, np, hdim(rows), hdim(b), &st->rank, E + k0, E + k0,
+                               kCholBits, kCholBits, -1.0, 1.0, A + k0 * np + k0, np, 1, nm, s,
+                               &t, (int)np, &place));
+    }
+    DiagBatch d;
+    std::memset(&d, 0, sizeof(d));
+    d.A = A;
+    d.lda = np;
+    d.zA = zz;
+    d.nd = nd;
+    d.k0 = k0;
+    d.b = b;
+    d.spd = spd;
+    d.st = st;
+    d.accepted = spd ? nullptr : acc;
+    d.zAcc = np;
+    d.dinv = dinv;
+    d.zDinv = 32;
+    BK_CHECK(KernelTimer().run(KT_DIAG, s, [&] { return launch_diag_batched(d, nz, s); }));
+    if (k0 + b < np) {
+      PanelBatch pb;
+      std::memset(&pb, 0, sizeof(pb));
+      pb.A = A;
+      pb.lda = np;
+      pb.zA = zz;
+      pb.nd = nd;
+      pb.k0 = k0;
+      pb.b = b;
+      pb.dinv = dinv;
+      pb.zDinv = 32;
+      pb.st = st;
+      BK_CHECK(KernelTimer().run(KT_AUX, s, [&] { return launch_panel_solve_batched(pb, nz, s); }));
+      // the finished panel's residues (read by the later panels' products)
+      BK_CHECK(t.run(KT_SPLIT, s, [&] {
+        rl_panel_split_kernel<<<dim3(g1((np - k0) * 32, 256, 64), (unsigned)nz), 256, 0, s>>>(
+            A, np, nd, st, k0, E, nm, kCholBits, RL, kpad, plane);
+        return cudaGetLastError();
+      }));
+    }
+  }
+  if (spd)
+    BK_CHECK(KernelTimer().run(KT_AUX, s, [&] {
+      return launch_tri_block_inverse_batched(A, np, zz, np, &st->rank, zR, b,
+                                              (double*)(ws + bk.off_T), bk.nb_q * 32 * 32, nz, s);
     }));
   return CPINV_OK;
 }
@@ -789,7 +946,7 @@ int run_bucket(cudaStream_t s, const Bucket& bk, char* ws, double rel_tol, int b
 struct Tuned {
   int panel;
   int bn;
-  int queue;  // 1: the factorisations as one queue-fed persistent launch (panel 32)
+  int queue;  // the factorisations' form (Bucket::queue): 0 panels, 1 queue, 2 exact
 };
 struct Tuner {
   std::mutex mu;
@@ -805,7 +962,7 @@ struct Tuner {
     std::snprintf(buf, sizeof(buf), "%s|sm%d%d|%s|n%lld|m%lld|k%lld|p%zu%s", prop.name, prop.major,
                   prop.minor, b.exact ? "exact" : "fp64", (long long)b.np, (long long)b.mp,
                   (long long)b.kp, b.ids.size(),
-                  force == 1 ? "|queue" : force == 0 ? "|panels" : "");
+                  force == 2 ? "|exact" : force == 1 ? "|queue" : force == 0 ? "|panels" : "");
     return buf;
   }
   void load() {
@@ -829,7 +986,7 @@ struct Tuner {
       const int b = std::atoi(pn + 9);
       const int t = bn ? std::atoi(bn + 6) : 128;
       const int u = qu ? std::atoi(qu + 9) : 0;
-      if ((b == 16 || b == 32) && (t == 128 || t == 256) && (u == 0 || (u == 1 && b == 32)))
+      if ((b == 16 || b == 32) && (t == 128 || t == 256) && (u == 0 || ((u == 1 || u == 2) && b == 32)))
         best[std::string(k, e)] = Tuned{b, t, u};
     }
     std::fclose(fp);
@@ -889,35 +1046,41 @@ int choose_panels(Layout& L, char* ws, double rel_tol, int panel, bool measure, 
   g_tuner.load();
   int64_t* ranks_dev = (int64_t*)(ws + L.off_ranks);
   int32_t* status_dev = (int32_t*)(ws + L.off_status);
-  // CPINV_BATCH_FACTOR=queue / panels restricts the factorisation's form
-  // (tests use it to cover both); unset, the tuner picks
+  // CPINV_BATCH_FACTOR=queue / panels / exact restricts the factorisation's
+  // form (tests use it to cover each); unset, the tuner picks
   int force = -1;
   if (const char* fe = std::getenv("CPINV_BATCH_FACTOR")) {
     if (std::strcmp(fe, "queue") == 0) force = 1;
     else if (std::strcmp(fe, "panels") == 0) force = 0;
+    else if (std::strcmp(fe, "exact") == 0) force = 2;
   }
   for (auto& bk : L.buckets) {
     bk.b = panel ? panel : 32;
     bk.bn = 128;
-    bk.queue = force == 1 && (!panel || panel == 32);
-    const std::string k = Tuner::key(bk, device, force);
+    // the exact form exists in the exact mode only (the FP64 mode falls back
+    // to the tuner's choice)
+    const int fb = (force == 2 && !bk.exact) ? -1 : force;
+    bk.queue = (fb >= 1 && (!panel || panel == 32)) ? fb : 0;
+    const std::string k = Tuner::key(bk, device, fb);
     auto it = g_tuner.best.find(k);
-    if (it != g_tuner.best.end() && (!panel || it->second.panel == panel)) {
+    if (it != g_tuner.best.end() && (!panel || it->second.panel == panel) &&
+        (it->second.queue != 2 || bk.exact)) {
       bk.b = it->second.panel;
       bk.bn = it->second.bn;
-      bk.queue = it->second.queue != 0;
+      bk.queue = it->second.queue;
       continue;
     }
     if (!measure) continue;
     // candidates: the factorisations as one launch per panel step with panel
-    // width 16 or 32 (unless given), or as the queue-fed persistent launch
-    // (panel 32); x, in the exact mode, the residue products' tile width
-    // 128 / 256 (256 when it divides n_pad)
+    // width 16 or 32 (unless given), as the queue-fed persistent launch
+    // (panel 32), or, in the exact mode, left-looking with exact residue
+    // updates (panel 32); x, in the exact mode, the residue products' tile
+    // width 128 / 256 (256 when it divides n_pad)
     std::vector<Tuned> cands;
     for (int pb : {16, 32}) {
       if (panel && pb != panel) continue;
-      for (int qu = 0; qu <= (pb == 32 ? 1 : 0); ++qu) {
-        if ((force == 1 && !qu) || (force == 0 && qu)) continue;
+      for (int qu = 0; qu <= (pb == 32 ? (bk.exact ? 2 : 1) : 0); ++qu) {
+        if (fb >= 0 && qu != fb) continue;
         cands.push_back(Tuned{pb, 128, qu});
         if (bk.exact && bk.np % 256 == 0) cands.push_back(Tuned{pb, 256, qu});
       }
@@ -926,7 +1089,7 @@ int choose_panels(Layout& L, char* ws, double rel_tol, int panel, bool measure, 
     if (cands.size() == 1) {
       bk.b = cands[0].panel;
       bk.bn = cands[0].bn;
-      bk.queue = cands[0].queue != 0;
+      bk.queue = cands[0].queue;
       continue;
     }
     cudaEvent_t e0, e1;
@@ -936,7 +1099,7 @@ int choose_panels(Layout& L, char* ws, double rel_tol, int panel, bool measure, 
     Tuned best = cands[0];
     for (size_t ci = 0; ci < cands.size(); ++ci) {
       bk.bn = cands[ci].bn;
-      bk.queue = cands[ci].queue != 0;
+      bk.queue = cands[ci].queue;
       const int cand = cands[ci].panel;
       // one untimed run (first launches load modules), one timed
       if (int rc = run_bucket(s, bk, ws, rel_tol, cand, ranks_dev, status_dev)) return rc;
@@ -955,7 +1118,7 @@ int choose_panels(Layout& L, char* ws, double rel_tol, int panel, bool measure, 
     cudaEventDestroy(e1);
     bk.b = best.panel;
     bk.bn = best.bn;
-    bk.queue = best.queue != 0;
+    bk.queue = best.queue;
     g_tuner.store(k, best);
   }
   return CPINV_OK;

@@ -15,6 +15,8 @@
 // Every spin-wait on an mbarrier has an iteration limit; on expiry the CTA
 // records ST_TIMEOUT in the call's status word, stops issuing work, waits (with
 // a limit) for the copies it has in flight, frees its tensor memory and exits.
+#include <algorithm>
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -1215,8 +1217,14 @@ bool make_map(CUtensorMap* map, const bf16* base, int64_t kpad, int64_t rows, in
 template <int BN, int STAGES, bool S3>
 cudaError_t launch_mma(const CUtensorMap& ta, CUtensorMap const& tb, MmaParams& mp,
                        int64_t Mmax, int64_t Nmax, int64_t wave, cudaStream_t s) {
-  // block-diagonal mode: the tiles of one blk x blk block, times the blocks
-  const int64_t bm = mp.blk ? mp.blk : Mmax, bn = mp.blk ? mp.blk : Nmax;
+  // block-diagonal mode: the tiles of one blk x blk block (of its kept rows
+  // and columns when they are bounded), times the blocks
+  int64_t bm = mp.blk ? mp.blk : Mmax, bn = mp.blk ? mp.blk : Nmax;
+  if (mp.blk && mp.bdims) {
+    bm = std::min<int64_t>(bm, mp.bM.max);
+    bn = std::min<int64_t>(bn, mp.bN.max);
+    if (bm < 1 || bn < 1) return cudaSuccess;
+  }
   mp.tiles_m = (int32_t)((bm + BM - 1) / BM);
   mp.tiles_n = (int32_t)((bn + BN - 1) / BN);
   int64_t tiles = 0;
@@ -1350,7 +1358,11 @@ cudaError_t crt_mma(const void* SA, int64_t a_rows, int a_row0, const void* SB, 
   const int64_t Mmax = M.max, Nmax = N.max;
   if (Mmax <= 0 || Nmax <= 0) return cudaSuccess;
   int BN = (Nmax >= 2048) ? 256 : (Nmax <= 32 ? 32 : 128);
-  if (blk) BN = (bn == 256 && blk % 256 == 0) ? 256 : 128;  // a tile never leaves its block
+  if (blk) {
+    BN = (bn == 256 && blk % 256 == 0) ? 256 : 128;  // a tile never leaves its block
+    // blocks that keep at most 32 columns (bplace) take 32-wide tiles
+    if (bplace && bplace->N.max <= 32) BN = 32;
+  }
   else if (bn == 128 || bn == 256) BN = bn;
   CUtensorMap ta, tb;
   if (!make_map(&ta, (const bf16*)SA, kpad, a_rows, n_mod, BM)) return cudaErrorInvalidValue;

@@ -313,3 +313,43 @@ def test_batched_queue_full_workload(factor_form):
     assert ranks == [p.r for p in probs]
     sample = np.random.default_rng(2).choice(512, size=16, replace=False)
     _check_against_oracle(probs, Ws, ranks, st, idx=sorted(int(i) for i in sample))
+
+
+# --------------------------------------------------------------------------
+# the exact mode's left-looking factorisation (CPINV_BATCH_FACTOR=exact):
+# every panel's update one block-diagonal residue product over the problems,
+# each entry the exact sum rounded once, as in the single-problem path
+# --------------------------------------------------------------------------
+
+def test_batched_exact_factor_small_uneven(factor_form):
+    probs = _problems(24, 11, k=3, m_range=(16, 300), n_lo=4, n_hi=160)
+    cp = _cp()
+    factor_form("exact")
+    Ws, ranks, st = cp.lstsq_batched([to_dev(p.G) for p in probs], [to_dev(p.F) for p in probs],
+                                     mode="exact")
+    _check_against_oracle(probs, Ws, ranks, st)
+    assert ranks == [p.r for p in probs]
+
+
+def test_batched_exact_factor_wide_buckets(factor_form):
+    """n_pad 256 and 512 groups, ragged n and m up to 4096."""
+    probs = _problems(9, 13, k=2, m_range=(300, 4096), n_lo=130, n_hi=512)
+    cp = _cp()
+    factor_form("exact")
+    Ws, ranks, st = cp.lstsq_batched([to_dev(p.G) for p in probs], [to_dev(p.F) for p in probs],
+                                     mode="exact")
+    _check_against_oracle(probs, Ws, ranks, st)
+
+
+def test_batched_exact_factor_full_workload(factor_form):
+    probs = inputs.batched_problems(512, 4, k=4, attempts=gap.load())
+    cp = _cp()
+    factor_form("exact")
+    plan = cp.BatchedLstsq([to_dev(p.G) for p in probs], [to_dev(p.F) for p in probs],
+                           mode="exact")
+    plan()
+    Ws, ranks, st = plan()
+    assert all(s == 0 for s in st)
+    assert ranks == [p.r for p in probs]
+    sample = np.random.default_rng(3).choice(512, size=24, replace=False)
+    _check_against_oracle(probs, Ws, ranks, st, idx=sorted(int(i) for i in sample))
