@@ -728,9 +728,10 @@ def batched_bench(args, device, flush, loop_steps: int = 2) -> dict:
         "max_rel_diff_fp64_batch_vs_loop": max(
             float(np.linalg.norm(a - b.cpu().numpy()) / max(np.linalg.norm(a), 1e-300))
             for a, b in zip(Wmodes["fp64"], Wl)),
-        "note": "exact: the Gram, L'L and W'W of every problem on the tensor cores (one "
-                "block-diagonal residue product each per n group), the rest FP64; fp64: every product FP64; loop: one "
-                "cpinv_lstsq FP64 call per problem",
+        "note": "exact: the Gram, L'L, W'W and the large triangular-inverse levels of every "
+                "problem on the tensor cores (one block-diagonal residue product each per n group), "
+                "the factorisations' panel updates too where the tuner picks the exact form, the "
+                "rest FP64; fp64: every product FP64; loop: one cpinv_lstsq FP64 call per problem",
     })
     return out
 

@@ -899,8 +899,9 @@ __global__ void __launch_bounds__(256, 2) reconstruct_kernel(ReconParams p, int 
 // Gram's and the factorisation's wider products).  The CRT sum S (< n P)
 // lives in three 64-bit words; the reduction mod P uses a quotient estimate
 // from FP32, the centring and the rounding work word-wise.  Four adjacent
-// columns per thread (one 32-bit load per modulus), eight rows x 128
-// columns per block.
+// columns per thread (one 32-bit load per modulus), LW threads per row:
+// eight rows x 128 columns per block, or (LW = 8, outputs of at most 32
+// columns) 32 rows x 32 columns.
 constexpr int kRecWordsMaxMod = 22;
 constexpr int kRecWords4MaxMod = 19;
 static_assert(kRecWordsMaxMod == kRecBlockMaxMod, "block-diagonal reconstruction limit");
@@ -985,7 +986,7 @@ __device__ __forceinline__ bool gt192(uint64_t x2, uint64_t x1, uint64_t x0, uin
   return x2 != y2 ? x2 > y2 : (x1 != y1 ? x1 > y1 : x0 > y0);
 }
 
-template <int NL>
+template <int NL, int LW>
 __global__ void __launch_bounds__(256) reconstruct_words_kernel(ReconParams p, int n_mod) {
   const crt::Consts& c = g_crt_consts[n_mod];
   __shared__ RecWShared sh;
@@ -1011,8 +1012,8 @@ __global__ void __launch_bounds__(256) reconstruct_words_kernel(ReconParams p, i
   const float inv_ptop = 1.0f / (float)(uint32_t)shr192(P2, P1, P0, qs);
 
   const int64_t M = eval_dim(p.M, p.rdev), N = eval_dim(p.N, p.rdev);
-  const int64_t i = (int64_t)blockIdx.y * kRecWRows + (threadIdx.x >> 5);
-  const int64_t j0 = (int64_t)blockIdx.x * kRecWCols + 4 * (threadIdx.x & 31);
+  const int64_t i = (int64_t)blockIdx.y * (256 / LW) + (threadIdx.x / LW);
+  const int64_t j0 = (int64_t)blockIdx.x * (4 * LW) + 4 * (threadIdx.x % LW);
   const int64_t il = p.blk ? i % p.blk : i;       // row within its block
   const int64_t zb = p.blk ? i / p.blk : 0;
   const int32_t* EB = p.blk ? p.EB + (i - il) : p.EB;
@@ -1475,17 +1476,23 @@ cudaError_t crt_reconstruct(const uint8_t* R, int64_t Mpad, int64_t Npad, Dim M,
   // small outputs (factorisation panels): latency-bound, four lanes per output
   // (block-diagonal outputs always take the word-wise kernel)
   const bool small = !blk && M.max * N.max <= ((int64_t)1 << 16);
+  // outputs of at most 32 columns (the batched factorisation's panels): eight
+  // threads per row, so that no lane idles
+  const bool narrow = N.max <= 32;
+  const dim3 gw((unsigned)((N.max + kRecWCols - 1) / kRecWCols),
+                (unsigned)((M.max + kRecWRows - 1) / kRecWRows));
+  const dim3 gn(1, (unsigned)((M.max + 31) / 32));
   return timer->run(KT_RECON, s, [&] {
     if (small)
       reconstruct_split_kernel<<<grid1d(M.max * N.max * kRecLanes, 256), 256, 0, s>>>(rp, n_mod);
+    else if (n_mod <= kRecWords4MaxMod && narrow)
+      reconstruct_words_kernel<4, 8><<<gn, 256, 0, s>>>(rp, n_mod);
     else if (n_mod <= kRecWords4MaxMod)
-      reconstruct_words_kernel<4><<<dim3((unsigned)((N.max + kRecWCols - 1) / kRecWCols),
-                                         (unsigned)((M.max + kRecWRows - 1) / kRecWRows)),
-                                    256, 0, s>>>(rp, n_mod);
+      reconstruct_words_kernel<4, 32><<<gw, 256, 0, s>>>(rp, n_mod);
+    else if (n_mod <= kRecWordsMaxMod && narrow)
+      reconstruct_words_kernel<5, 8><<<gn, 256, 0, s>>>(rp, n_mod);
     else if (n_mod <= kRecWordsMaxMod)
-      reconstruct_words_kernel<5><<<dim3((unsigned)((N.max + kRecWCols - 1) / kRecWCols),
-                                         (unsigned)((M.max + kRecWRows - 1) / kRecWRows)),
-                                    256, 0, s>>>(rp, n_mod);
+      reconstruct_words_kernel<5, 32><<<gw, 256, 0, s>>>(rp, n_mod);
     else
       reconstruct_kernel<<<grid1d(M.max * ((N.max + kRecW - 1) / kRecW), 256), 256, 0, s>>>(
           rp, n_mod);
