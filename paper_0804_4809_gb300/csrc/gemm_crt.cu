@@ -1414,6 +1414,10 @@ cudaError_t crt_mma(const void* SA, int64_t a_rows, int a_row0, const void* SB, 
 // The CRT tables of every moduli count, uploaded once per device (outside
 // any stream capture: the first call of an argument set always runs
 // directly); returns their device address, indexed by the moduli count.
+// The address is kept for the life of the process, like the library's
+// streams, events and graphs: it belongs to the device's primary context,
+// so a reset of that context (cudaDeviceReset) between calls is not
+// supported.
 const crt::Consts* crt_consts_device() {
   static std::mutex mu;
   static std::vector<std::pair<int, const crt::Consts*>> done;
