@@ -32,6 +32,10 @@
  *   - m = 0 or n = 0 gives an empty result and r = 0.  A G with no positive
  *     diagonal entry in its Gram matrix (e.g. G = 0) gives G+ = 0 and r = 0,
  *     like the Appendix listing (min over an empty set makes every test false).
+ *   - The library keeps per-device state for the life of the process (its
+ *     streams, events, captured CUDA graphs and constant tables), all in the
+ *     device's primary context: do not reset the device (cudaDeviceReset)
+ *     between calls.
  */
 #ifndef CPINV_H
 #define CPINV_H
